@@ -1,0 +1,508 @@
+"""Benchmark of the GB300 positional population count.
+
+Default workload (the large-array sweep, one GPU): an 8 GiB array of
+Bernoulli(0.5) bits (seed 0) resident in HBM; one step counts it for
+w = 8, 16, 32 and 64 (four launches of the single-array kernel).  The value
+is input GB/s over the timed steps (device time, CUDA events), and the line
+also carries:
+
+* per_w: GB/s and fraction of measured HBM peak for each w;
+* roofline: the counting kernel's achieved GB/s per launch against the
+  measured HBM peak, plus the DRAM traffic per launch from the committed
+  ncu summary (null when the kernel source changed since it was taken);
+* read_roofline: the roofline read kernel (Section 5's "dummy" kernel) on the
+  same array;
+* e2e: the same metric through the host-memory entry point (pinned host
+  input, every step's input crosses the CPU-GPU link, counts read back);
+* batched: the ragged one-hot batch (200000 uint8 arrays, log-uniform
+  1 B .. 4 MiB, about 55 GB), one batched call vs one launch per array;
+* short: microseconds per call for short unaligned arrays, one launch each,
+  plain and graph-replayed;
+* cpu_baseline: the CPU oracle on the host cores on a bounded sample;
+* clocks: SM clocks and throttle reasons sampled during the timed region.
+
+``--impl reference`` times the CPU oracle on the same workload instead.
+Under torchrun each rank runs an independent replica (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+GIB = 1 << 30
+WIDTHS = (8, 16, 32, 64)
+METRIC = "pospopcnt input GB/s and % of HBM peak per w; batched vs per-array; p99 us"
+WORKLOAD = ("large-array sweep: 8 GiB array of Bernoulli(0.5) bits (seed 0) resident in HBM, "
+            "w in {8,16,32,64} per step")
+
+
+def _measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks/throttle sampling in the background (read-only)."""
+
+    FIELDS = ("timestamp", "index", "clocks.sm", "clocks.max.sm", "power.draw",
+              "clocks_event_reasons.active", "clocks_event_reasons.hw_slowdown",
+              "clocks_event_reasons.hw_thermal_slowdown",
+              "clocks_event_reasons.sw_thermal_slowdown", "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int, period_ms: int = 50):
+        self.samples = []
+        self.proc = None
+        self.index = index
+        self.period_ms = period_ms
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + ",".join(self.FIELDS),
+                 "--format=csv,noheader,nounits", "-lms", str(self.period_ms)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.samples.append((time.time(), [x.strip() for x in line.split(",")]))
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        if self.thread is not None:
+            self.thread.join(timeout=2)
+
+    def summary(self, t0: float, t1: float) -> dict:
+        win = [s for (t, s) in self.samples if t0 - 0.06 <= t <= t1 + 0.06]
+        if not win and self.samples:
+            mid = 0.5 * (t0 + t1)
+            win = [min(self.samples, key=lambda x: abs(x[0] - mid))[1]]
+        if not win:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"],
+                    "samples": 0}
+        sm = [float(s[2]) for s in win if s[2].replace(".", "").isdigit()]
+        smax = [float(s[3]) for s in win if s[3].replace(".", "").isdigit()]
+        reasons = set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for s in win:
+            for name, val in zip(names, s[6:10]):
+                if val.strip().lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(win)}
+
+
+def _kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2412_16370_gb300", "csrc")
+    for f in ("pospop_device.cuh", "pospop_stream.cu"):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def _profile_traffic(nbytes: int):
+    """DRAM bytes per launch of the counting kernel from the committed ncu summary."""
+    path = os.path.join(ROOT, "profiles", "stream_kernel_traffic.json")
+    try:
+        with open(path) as f:
+            prof = json.load(f)
+    except (OSError, ValueError):
+        return None, "no committed ncu summary"
+    if prof.get("kernel_source_sha256_16") != _kernel_source_hash():
+        return None, "kernel changed since the ncu capture"
+    per_byte = prof["dram_bytes_per_launch"] / prof["input_bytes_per_launch"]
+    return per_byte * nbytes, prof.get("note", "")
+
+
+def _cpu_baseline(data_dev, budget_s: float = 4.0):
+    """The oracle as it stands, all host cores, on a bounded sample of the array."""
+    import torch
+    import oracle
+    orc = oracle.load()
+    cores = os.cpu_count() or 1
+    probe = 16 << 20
+    host = data_dev[:probe].cpu().numpy()
+    t0 = time.perf_counter()
+    orc.bytes_mt(16, host, cores)
+    rate = probe / max(time.perf_counter() - t0, 1e-6)
+    sample = int(min(GIB, max(probe, rate * budget_s / len(WIDTHS))))
+    sample -= sample % 64
+    host = data_dev[:sample].cpu().numpy()
+    t0 = time.perf_counter()
+    for w in WIDTHS:
+        orc.bytes_mt(w, host, cores)
+    dt = time.perf_counter() - t0
+    del torch
+    return {"value": round(sample * len(WIDTHS) / dt / 1e9, 4), "unit": "GB/s", "cores": cores,
+            "kind": "oracle",
+            "sample": f"first {sample >> 20} MiB of the 8 GiB array, counted once per w in "
+                      f"{{8,16,32,64}} with {cores} threads (Fig. 2 loop, -O2 -fno-tree-vectorize)"}
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2412_16370_gb300 import binding as pp
+    from paper_2412_16370_gb300 import build as pkg_build
+    from paper_2412_16370_gb300 import synth, synth_device
+
+    world, rank, local = _dist()
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo",
+                                device_id=torch.device(f"cuda:{local}"))
+    torch.cuda.set_device(local)
+    dev = torch.device(f"cuda:{local}")
+    if rank == 0 or world == 1:
+        pkg_build.build()
+    if world > 1:
+        dist.barrier()
+    pp.init(local)
+    peaks, peak_kind = _measured_peaks()
+    hbm_peak = float(peaks["hbm_gbs"])
+
+    nbytes = args.gib * GIB
+    data = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    synth_device.bernoulli_(data, 0.5, seed=0 + rank)
+    counts = torch.zeros((len(WIDTHS), 64), dtype=torch.int64, device=dev)
+    stream = torch.cuda.current_stream()
+    torch.cuda.synchronize()
+
+    def step(ev=None):
+        for k, w in enumerate(WIDTHS):
+            if ev is not None:
+                ev[k][0].record(stream)
+            pp.pospopcnt_async(w, counts[k], data, nbytes, stream)
+            if ev is not None:
+                ev[k][1].record(stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    evs = [[[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in WIDTHS]
+           for _ in range(args.steps)]
+    start_ev = torch.cuda.Event(enable_timing=True)
+    end_ev = torch.cuda.Event(enable_timing=True)
+    launches0 = pp.pospopcnt_launch_count()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.time()
+    start_ev.record(stream)
+    for i in range(args.steps):
+        step(evs[i])
+    end_ev.record(stream)
+    torch.cuda.synchronize()
+    t1 = time.time()
+    if world > 1:
+        dist.barrier()
+    launches = pp.pospopcnt_launch_count() - launches0
+    time.sleep(0.1)
+    sampler.stop()
+    clocks = sampler.summary(t0, t1)
+
+    total_ms = start_ev.elapsed_time(end_ev)
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_step = total_ms / args.steps
+    bytes_step = nbytes * len(WIDTHS)
+    value = world * bytes_step * args.steps / (total_ms / 1e3) / 1e9
+
+    per_w = {}
+    launch_ms_all = []
+    for k, w in enumerate(WIDTHS):
+        ms = [evs[i][k][0].elapsed_time(evs[i][k][1]) for i in range(args.steps)]
+        launch_ms_all += ms
+        gbs = nbytes / (float(np.mean(ms)) / 1e3) / 1e9
+        per_w[str(w)] = {"GBps": round(gbs, 1), "frac_of_hbm_peak": round(gbs / hbm_peak, 4),
+                         "ms_per_launch": round(float(np.mean(ms)), 4)}
+    avg_launch_ms = float(np.mean(launch_ms_all))
+    achieved = nbytes / (avg_launch_ms / 1e3) / 1e9
+    traffic, traffic_note = _profile_traffic(nbytes)
+
+    # correctness spot check of the timed counts: every w's counts add up to the
+    # same total (the array's popcount), times the number of launches
+    tot = counts.sum(dim=1).cpu().numpy()
+    consistent = bool(np.all(tot == tot[0]))
+
+    # roofline read kernel on the same array
+    rsum = torch.zeros(1, dtype=torch.int64, device=dev)
+    for _ in range(3):
+        pp.pospopcnt_roofline_read(data, rsum, nbytes, stream)
+    torch.cuda.synchronize()
+    r0 = torch.cuda.Event(enable_timing=True)
+    r1 = torch.cuda.Event(enable_timing=True)
+    reps = 20
+    r0.record(stream)
+    for _ in range(reps):
+        pp.pospopcnt_roofline_read(data, rsum, nbytes, stream)
+    r1.record(stream)
+    torch.cuda.synchronize()
+    read_gbs = nbytes / (r0.elapsed_time(r1) / reps / 1e3) / 1e9
+
+    extra = {}
+    if not args.quick:
+        extra["e2e"] = _e2e(args, pp, data, nbytes, world, dist)
+        if rank == 0:
+            extra["batched"] = _batched(pp, synth, synth_device, dev, stream, achieved, hbm_peak)
+            extra["short"] = _short(pp, synth, dev, stream)
+            extra["cpu_baseline"] = _cpu_baseline(data)
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+
+    line = {
+        "metric": METRIC,
+        "value": round(value, 1),
+        "unit": "GB/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(ms_step, 4),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "u32",
+        "data": "synthetic (seeded SplitMix64 Bernoulli(0.5) bits, generated on the device)",
+        "config": {"workload": WORKLOAD, "bytes_per_step_per_gpu": bytes_step,
+                   "array_bytes": nbytes, "widths": list(WIDTHS),
+                   "l2": "inputs (8 GiB) far larger than L2 (126 MB): no flush between steps",
+                   "parallelism": f"replicas x{world}",
+                   "tune": pp.pospopcnt_tune_describe().splitlines()[0]},
+        "per_w": per_w,
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak,
+                     "unit": "GB/s", "frac": round(achieved / hbm_peak, 4),
+                     "traffic": traffic, "peak_kind": f"{peak_kind} hbm_gbs (copy, burst)",
+                     "kernel": "pospop::stream_kernel (single-array count)",
+                     "traffic_note": traffic_note},
+        "read_roofline": {"GBps": round(read_gbs, 1), "frac_of_hbm_peak": round(read_gbs / hbm_peak, 4),
+                          "kernel": "pospop::roofline_kernel (sum of the input)"},
+        "gpu_launches": int(launches),
+        "counts_consistent_across_w": consistent,
+        "clocks": clocks,
+    }
+    line.update(extra)
+    if "e2e" not in line:
+        line["e2e"] = None
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def _e2e(args, pp, data, nbytes, world, dist):
+    """Same metric through pospopcnt_host: pinned host input, counts read back to the host."""
+    import torch
+    host = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
+    host.copy_(data)
+    hc = np.zeros(64, dtype=np.uint64)
+    steps = max(1, min(args.steps, args.e2e_steps))
+    for w in WIDTHS:
+        pp.pospopcnt_host(w, hc, host)
+    if world > 1:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        for w in WIDTHS:
+            pp.pospopcnt_host(w, hc, host)
+    dt = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([dt], dtype=torch.float64, device=data.device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dt = float(t.item())
+    del host
+    return {"value": round(world * nbytes * len(WIDTHS) * steps / dt / 1e9, 2), "unit": "GB/s",
+            "h2d_bytes_per_step": nbytes * len(WIDTHS),
+            "d2h_bytes_per_step": 8 * sum(WIDTHS), "steps": steps,
+            "path": "pospopcnt_host on pinned host memory (read in place over NVLink-C2C)"}
+
+
+def _batched(pp, synth, synth_device, dev, stream, large_gbs, hbm_peak, m=200000):
+    import torch
+    sizes = synth.log_uniform_sizes(m, 1, 4 << 20, seed=3)
+    offs = synth.csr_offsets(sizes)
+    total = int(offs[-1])
+    base = torch.empty(total + 64, dtype=torch.uint8, device=dev)
+    synth_device.one_hot_(base, 4, nbytes=total)
+    offs_d = torch.from_numpy(offs.view(np.int64)).to(dev)
+    c = torch.zeros((m, 8), dtype=torch.int64, device=dev)
+    for _ in range(3):
+        pp.pospopcnt_batch(8, c, base, offs_d, m, stream)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    reps = 10
+    e0.record(stream)
+    for _ in range(reps):
+        pp.pospopcnt_batch(8, c, base, offs_d, m, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    ok = bool(np.array_equal(c.sum(dim=1).cpu().numpy(), (reps + 3) * sizes))
+    # one launch per array
+    c.zero_()
+    basep = base.data_ptr()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e0.record(stream)
+    for a in range(m):
+        if sizes[a]:
+            pp.pospopcnt_async(8, c[a], basep + int(offs[a]), int(sizes[a]), stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    ms_per = e0.elapsed_time(e1)
+    gbs = total / (ms / 1e3) / 1e9
+    del base
+    torch.cuda.empty_cache()
+    return {"workload": f"{m} one-hot uint8 arrays (Zipf(1.1) over 8 classes), sizes log-uniform "
+                        "1 B..4 MiB, back to back (unaligned starts), w=8",
+            "bytes": total, "GBps": round(gbs, 1), "ms": round(ms, 3),
+            "frac_of_large_array": round(gbs / large_gbs, 4),
+            "frac_of_hbm_peak": round(gbs / hbm_peak, 4),
+            "per_array_launches": {"GBps": round(total / (ms_per / 1e3) / 1e9, 1),
+                                   "ms": round(ms_per, 1), "host_wall_s": round(wall, 2)},
+            "speedup_vs_per_array": round(ms_per / ms, 1),
+            "one_hot_sums_ok": ok}
+
+
+def _short(pp, synth, dev, stream, n=2000):
+    """Short unaligned arrays (log-uniform 1 B .. 64 KiB), one launch per array."""
+    import torch
+    sizes = synth.log_uniform_sizes(n, 1, 65536, seed=21)
+    slot = 65536 + 32
+    buf = torch.empty(slot * 64, dtype=torch.uint8, device=dev)
+    buf.random_(0, 256)
+    c = torch.zeros(64, dtype=torch.int64, device=dev)
+    basep = buf.data_ptr()
+    calls = [(WIDTHS[k % 4], basep + (k % 64) * slot + (k % 16), int(sizes[k])) for k in range(n)]
+    for w, p, s in calls[:50]:
+        pp.pospopcnt_async(w, c, p, s, stream)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    t0 = time.perf_counter()
+    e0.record(stream)
+    for w, p, s in calls:
+        pp.pospopcnt_async(w, c, p, s, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    dev_us = e0.elapsed_time(e1) * 1e3 / n
+    # graph-replayed: the same launches captured once
+    g = torch.cuda.CUDAGraph()
+    s2 = torch.cuda.Stream()
+    with torch.cuda.stream(s2):
+        g.capture_begin()
+        for w, p, s in calls:
+            pp.pospopcnt_async(w, c, p, s, s2)
+        g.capture_end()
+    torch.cuda.synchronize()
+    g.replay()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    g.replay()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    graph_us = e0.elapsed_time(e1) * 1e3 / n
+    return {"workload": f"{n} arrays, sizes log-uniform 1 B..64 KiB, start offsets 0..15, "
+                        "w cycling 8/16/32/64, one launch each",
+            "device_us_per_call": round(dev_us, 2), "host_us_per_call": round(wall * 1e6 / n, 2),
+            "graph_us_per_call": round(graph_us, 2)}
+
+
+def run_reference(args):
+    """The CPU oracle (the reference arm of this tier) on the same workload."""
+    world, rank, _ = _dist()
+    if rank != 0:
+        return
+    import oracle
+    from paper_2412_16370_gb300 import synth
+    orc = oracle.load()
+    cores = os.cpu_count() or 1
+    sample = args.ref_sample_mib << 20
+    host = synth.bernoulli_bytes(sample, 0.5, seed=0)
+    for _ in range(args.warmup):
+        orc.bytes_mt(16, host[:1 << 20], cores)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        for w in WIDTHS:
+            orc.bytes_mt(w, host, cores)
+    dt = time.perf_counter() - t0
+    value = sample * len(WIDTHS) * args.steps / dt / 1e9
+    desc = (f"first {args.ref_sample_mib} MiB of the 8 GiB Bernoulli(0.5) array (seed 0), "
+            f"counted for w in {{8,16,32,64}} per step with {cores} threads")
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": "GB/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(dt * 1e3 / args.steps, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+            "data": "synthetic (seeded SplitMix64 Bernoulli(0.5) bits)",
+            "config": {"workload": WORKLOAD, "parallelism": "host cores",
+                       "sample_bytes_per_step": sample * len(WIDTHS)},
+            "cpu_baseline": {"value": round(value, 4), "unit": "GB/s", "cores": cores,
+                             "kind": "oracle", "sample": desc},
+            "e2e": {"value": round(value, 4), "unit": "GB/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--gib", type=int, default=8, help="array size in GiB (8 = the workload)")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--ref-sample-mib", type=int, default=16)
+    ap.add_argument("--quick", action="store_true", help="skip e2e, batched, short, cpu baseline")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be at least 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

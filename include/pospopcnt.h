@@ -1,0 +1,171 @@
+/*
+ * pospopcnt.h -- C ABI of libpospopcnt.so, the GB300 (sm_103a) positional
+ * population count.
+ *
+ * The operation (arXiv 2412.16370, Fig. 2 and Section 1): for an array of
+ * n words of w bits, count for every bit position j < w how many words have
+ * bit j set.  Equivalently the input bit stream is read as w interleaved
+ * streams and the bits at stream positions j, j+w, j+2w, ... are summed.
+ *
+ * Conventions shared by every entry point below:
+ *
+ *   - Byte order.  Words are little-endian, so bit j of a word lives in byte
+ *     j/8 of that word; for the byte-length forms bit b of byte k is stream
+ *     bit 8k+b and is counted in counter (8k+b) mod w.  A trailing partial
+ *     word counts as if zero-padded.  The start address may have any byte
+ *     alignment.
+ *   - Add-into.  Counts are ADDED to the uint64_t counters the caller passes
+ *     (Section 4, step 1 and its footnote: clearing the counters is
+ *     optional, which lets streamed or non-contiguous input be counted into
+ *     one counter array).  Zero them first for a fresh count.
+ *   - Widths.  w is 8, 16, 32 or 64 (the paper's f_8 .. f_64, Section 5).
+ *     The byte-length and batch forms also accept w = 1, 2, 4 (w = 1 is the
+ *     ordinary population count).
+ *   - Memory.  Unless a function says otherwise, pointers are DEVICE
+ *     pointers of the current CUDA device (cudaMalloc, PyTorch tensors,
+ *     cudaMallocManaged or pinned host memory that the device can address).
+ *     A plain pageable host pointer returns POSPOP_EPTR.  The caller owns
+ *     inputs and counters; the library owns its workspace.
+ *   - Streams.  `stream` is a cudaStream_t passed as void* (NULL = the
+ *     legacy default stream).  *_async and batch calls only enqueue work:
+ *     they neither allocate nor synchronise once the workspace is large
+ *     enough, so they may be captured into a CUDA graph (see
+ *     pospopcnt_reserve).
+ *   - Errors.  Functions return POSPOP_OK (0) or a negative POSPOP_E* code;
+ *     n == 0 (or m == 0) is a no-op that returns POSPOP_OK.  A failed call
+ *     leaves the counters untouched unless it says otherwise.
+ */
+#ifndef POSPOPCNT_H
+#define POSPOPCNT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define POSPOP_OK 0
+#define POSPOP_EINVAL (-1)    /* bad argument: NULL with n > 0, bad w, decreasing offsets */
+#define POSPOP_EPTR (-2)      /* pointer not addressable by the device (or wrong kind) */
+#define POSPOP_ECUDA (-3)     /* a CUDA runtime call or a kernel launch failed */
+#define POSPOP_ENOMEM (-4)    /* workspace or staging memory could not be allocated */
+#define POSPOP_ETIMEDOUT (-5) /* a bounded wait expired */
+#define POSPOP_EBUSY (-6)     /* no free slot / budget (serving) */
+#define POSPOP_ERANGE (-7)    /* size beyond a documented maximum */
+
+/* Message for a status code (static storage, never NULL). */
+const char *pospopcnt_strerror(int code);
+
+/* Set up the library for `device` (workspace, launch table, tune table) and
+ * make it the current device of the calling thread.  Idempotent.  Other
+ * entry points set up the current device on first use, so calling this is
+ * optional; call it before capturing a CUDA graph. */
+int pospopcnt_init(int device);
+
+/* Release every device's workspace and staging buffers.  Later calls set
+ * the library up again. */
+void pospopcnt_shutdown(void);
+
+/*
+ * Fig. 2's pospop_w(counts, words, n) for w = 8, 16, 32, 64: counts[j] +=
+ * number of the n words with bit j set.  `counts` and `words` are either
+ * both device-addressable pointers (the count runs on the legacy default
+ * stream) or both plain host pointers (the input is streamed to the device
+ * through the library's staging buffers, as pospopcnt_host).  Mixed kinds
+ * return POSPOP_EPTR.  These calls return when the counts are final, and
+ * report kernel errors.
+ */
+int pospopcnt_u8(uint64_t counts[8], const uint8_t *words, size_t n);
+int pospopcnt_u16(uint64_t counts[16], const uint16_t *words, size_t n);
+int pospopcnt_u32(uint64_t counts[32], const uint32_t *words, size_t n);
+int pospopcnt_u64(uint64_t counts[64], const uint64_t *words, size_t n);
+
+/*
+ * Byte-length form, asynchronous (Fig. 2 / Section 1): counts[0..w-1] +=
+ * the width-w positional population count of the nbytes bytes at `bytes`
+ * (any alignment; a trailing partial word is zero-padded).  Enqueued on
+ * `stream`; the counts are final once the stream reaches this point.
+ * Device pointers only.
+ */
+int pospopcnt_async(int w, uint64_t *counts, const void *bytes, size_t nbytes, void *stream);
+
+/*
+ * Batched form: m arrays stored at base + offsets[a] .. base + offsets[a+1]
+ * (offsets: m+1 uint64_t byte offsets, non-decreasing, in DEVICE memory).
+ * counts is an m x w row-major uint64_t array: counts[a*w + j] += count of
+ * position j in array a.  One planning pass and one persistent counting
+ * launch on `stream` (Section 4's algorithm per work item; the batching is
+ * this library's own).  Decreasing offsets are detected on the device: no
+ * counter is changed and the stream's batch status becomes POSPOP_EINVAL
+ * (read it with pospopcnt_batch_status).  Zero-length arrays are allowed.
+ */
+int pospopcnt_batch(int w, uint64_t *counts, const void *base, const uint64_t *offsets,
+                    size_t m, void *stream);
+
+/* Synchronise `stream` and return (then clear) the device-side status of
+ * the last pospopcnt_batch call on it: POSPOP_OK or POSPOP_EINVAL. */
+int pospopcnt_batch_status(void *stream);
+
+/* Grow the workspace of `stream` so that batch calls with up to m_max
+ * arrays need no allocation (required before capturing such calls into a
+ * CUDA graph; a capture that needs more returns POSPOP_ENOMEM). */
+int pospopcnt_reserve(size_t m_max, void *stream);
+
+/*
+ * Host-memory form: counts (host, w entries) += the count of the nbytes
+ * host bytes at `bytes`.  Pinned host memory is read by the counting kernel
+ * directly over the CPU-GPU link; pageable memory is copied through the
+ * library's double-buffered device staging area, copies overlapping the
+ * counting.  Synchronous.
+ */
+int pospopcnt_host(int w, uint64_t *counts, const void *bytes, size_t nbytes);
+
+/*
+ * Roofline read kernel (the paper's "dummy" kernel of Section 5: it sums
+ * the input and adds the sum to an output).  *sum (device, one uint64_t) +=
+ * the sum of the 32-bit little-endian words of the 16-byte-aligned interior
+ * of [bytes, bytes + nbytes).  It reads the input exactly like the counting
+ * kernel and is the achievable-bandwidth reference for it.
+ */
+int pospopcnt_roofline_read(const void *bytes, size_t nbytes, uint64_t *sum, void *stream);
+
+/*
+ * Launch plan of the single-array count for (w, nbytes) on the current
+ * device, as chosen from the tune table.  Writes 8 values to plan:
+ * [0] grid blocks, [1] threads per block, [2] CSA flush depth (16 or 32
+ * words per a16 flush), [3] load variant, [4] size class, [5] rows of 512 B,
+ * [6] launches, [7] resident blocks per SM.  For tests and benchmarks.
+ */
+int pospopcnt_plan(int w, size_t nbytes, uint32_t plan[8]);
+
+/*
+ * Tune table.  pospopcnt_autotune times every launch candidate for each
+ * size class on the current device (allocating a scratch buffer of up to
+ * max_bytes), installs the fastest, and, if path is not NULL, writes the
+ * table there.  pospopcnt_tune_load installs a table written earlier;
+ * pospopcnt_tune_describe writes a one-line-per-class summary into buf.
+ */
+int pospopcnt_autotune(size_t max_bytes, const char *path);
+int pospopcnt_tune_load(const char *path);
+int pospopcnt_tune_describe(char *buf, size_t len);
+
+/*
+ * CUDA graph of one batched call (planning + counting), captured on
+ * `stream` and replayed with pospopcnt_graph_launch.  The graph keeps the
+ * pointers and m it was made with.  *graph receives an opaque handle.
+ */
+int pospopcnt_batch_graph_create(int w, uint64_t *counts, const void *base,
+                                 const uint64_t *offsets, size_t m, void *stream,
+                                 void **graph);
+int pospopcnt_graph_launch(void *graph, void *stream);
+int pospopcnt_graph_destroy(void *graph);
+
+/* Number of library kernel launches enqueued by this process so far. */
+uint64_t pospopcnt_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* POSPOPCNT_H */

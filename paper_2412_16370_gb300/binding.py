@@ -1,0 +1,231 @@
+"""Thin ctypes binding of ``libpospopcnt.so`` (C ABI: ``include/pospopcnt.h``).
+
+Argument marshalling only: every function forwards to the entry point of the
+same name, passing raw pointers (``tensor.data_ptr()`` for torch tensors,
+``array.ctypes.data`` for numpy arrays), sizes and the CUDA stream handle, and
+raises ``PospopError`` on a nonzero status.  There is no CPU fallback: if the
+library is missing, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libpospopcnt.so")
+
+POSPOP_OK = 0
+POSPOP_EINVAL = -1
+POSPOP_EPTR = -2
+POSPOP_ECUDA = -3
+POSPOP_ENOMEM = -4
+POSPOP_ETIMEDOUT = -5
+POSPOP_EBUSY = -6
+POSPOP_ERANGE = -7
+
+_lock = threading.Lock()
+_lib = None
+
+
+class PospopError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"pospopcnt error {code}: {msg}")
+        self.code = code
+
+
+_u64p = ctypes.POINTER(ctypes.c_uint64)
+_vp = ctypes.c_void_p
+_sz = ctypes.c_size_t
+_int = ctypes.c_int
+
+_SIGNATURES = {
+    "pospopcnt_strerror": ([_int], ctypes.c_char_p),
+    "pospopcnt_init": ([_int], _int),
+    "pospopcnt_shutdown": ([], None),
+    "pospopcnt_u8": ([_vp, _vp, _sz], _int),
+    "pospopcnt_u16": ([_vp, _vp, _sz], _int),
+    "pospopcnt_u32": ([_vp, _vp, _sz], _int),
+    "pospopcnt_u64": ([_vp, _vp, _sz], _int),
+    "pospopcnt_async": ([_int, _vp, _vp, _sz, _vp], _int),
+    "pospopcnt_batch": ([_int, _vp, _vp, _vp, _sz, _vp], _int),
+    "pospopcnt_batch_status": ([_vp], _int),
+    "pospopcnt_reserve": ([_sz, _vp], _int),
+    "pospopcnt_host": ([_int, _vp, _vp, _sz], _int),
+    "pospopcnt_roofline_read": ([_vp, _sz, _vp, _vp], _int),
+    "pospopcnt_plan": ([_int, _sz, ctypes.POINTER(ctypes.c_uint32)], _int),
+    "pospopcnt_autotune": ([_sz, ctypes.c_char_p], _int),
+    "pospopcnt_tune_load": ([ctypes.c_char_p], _int),
+    "pospopcnt_tune_describe": ([ctypes.c_char_p, _sz], _int),
+    "pospopcnt_batch_graph_create": ([_int, _vp, _vp, _vp, _sz, _vp, ctypes.POINTER(_vp)], _int),
+    "pospopcnt_graph_launch": ([_vp, _vp], _int),
+    "pospopcnt_graph_destroy": ([_vp], _int),
+    "pospopcnt_launch_count": ([], ctypes.c_uint64),
+}
+
+
+def lib():
+    """The loaded library (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(
+                    f"{LIB_PATH} is missing: build it with "
+                    "`python -m paper_2412_16370_gb300.build` (there is no CPU fallback)")
+            L = ctypes.CDLL(LIB_PATH)
+            for name, (args, res) in _SIGNATURES.items():
+                fn = getattr(L, name)
+                fn.argtypes = args
+                fn.restype = res
+            _lib = L
+        return _lib
+
+
+def strerror(code: int) -> str:
+    return lib().pospopcnt_strerror(code).decode()
+
+
+def _check(rc: int) -> int:
+    if rc != POSPOP_OK:
+        raise PospopError(rc, strerror(rc))
+    return rc
+
+
+def _ptr(x) -> int | None:
+    """Raw address of a torch tensor, numpy array, int or None."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if hasattr(x, "ctypes"):
+        return x.ctypes.data
+    raise TypeError(f"cannot take the address of {type(x).__name__}")
+
+
+def _nbytes(x) -> int:
+    if hasattr(x, "element_size"):
+        return x.numel() * x.element_size()
+    return int(x.nbytes)
+
+
+def _stream(stream) -> int | None:
+    """A cudaStream_t handle: None means torch's current stream on the current device."""
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream or None
+    if isinstance(stream, int):
+        return stream or None
+    return stream.cuda_stream or None
+
+
+def init(device: int = 0) -> None:
+    _check(lib().pospopcnt_init(device))
+
+
+def shutdown() -> None:
+    lib().pospopcnt_shutdown()
+
+
+def _typed(w: int, counts, words, n):
+    if n is None:
+        n = _nbytes(words) // (w // 8)
+    fn = getattr(lib(), f"pospopcnt_u{w}")
+    return _check(fn(_ptr(counts), _ptr(words), n))
+
+
+def pospopcnt_u8(counts, words, n=None):
+    return _typed(8, counts, words, n)
+
+
+def pospopcnt_u16(counts, words, n=None):
+    return _typed(16, counts, words, n)
+
+
+def pospopcnt_u32(counts, words, n=None):
+    return _typed(32, counts, words, n)
+
+
+def pospopcnt_u64(counts, words, n=None):
+    return _typed(64, counts, words, n)
+
+
+def pospopcnt_async(w: int, counts, data, nbytes=None, stream=None):
+    if nbytes is None:
+        nbytes = _nbytes(data)
+    return _check(lib().pospopcnt_async(w, _ptr(counts), _ptr(data), nbytes, _stream(stream)))
+
+
+def pospopcnt_batch(w: int, counts, base, offsets, m=None, stream=None):
+    if m is None:
+        m = offsets.numel() - 1 if hasattr(offsets, "numel") else len(offsets) - 1
+    return _check(lib().pospopcnt_batch(w, _ptr(counts), _ptr(base), _ptr(offsets), m,
+                                        _stream(stream)))
+
+
+def pospopcnt_batch_status(stream=None) -> int:
+    """Status of the last batch call on ``stream`` (0 or a negative code; does not raise)."""
+    return lib().pospopcnt_batch_status(_stream(stream))
+
+
+def pospopcnt_reserve(m_max: int, stream=None):
+    return _check(lib().pospopcnt_reserve(m_max, _stream(stream)))
+
+
+def pospopcnt_host(w: int, counts, data, nbytes=None):
+    if nbytes is None:
+        nbytes = _nbytes(data)
+    return _check(lib().pospopcnt_host(w, _ptr(counts), _ptr(data), nbytes))
+
+
+def pospopcnt_roofline_read(data, sum_out, nbytes=None, stream=None):
+    if nbytes is None:
+        nbytes = _nbytes(data)
+    return _check(lib().pospopcnt_roofline_read(_ptr(data), nbytes, _ptr(sum_out),
+                                                _stream(stream)))
+
+
+PLAN_FIELDS = ("grid", "block", "depth", "hint", "size_class", "rows", "launches", "ctas_per_sm")
+
+
+def pospopcnt_plan(w: int, nbytes: int) -> dict:
+    out = (ctypes.c_uint32 * 8)()
+    _check(lib().pospopcnt_plan(w, nbytes, out))
+    return dict(zip(PLAN_FIELDS, list(out)))
+
+
+def pospopcnt_autotune(max_bytes: int = 0, path: str | None = None):
+    return _check(lib().pospopcnt_autotune(max_bytes, path.encode() if path else None))
+
+
+def pospopcnt_tune_load(path: str):
+    return _check(lib().pospopcnt_tune_load(path.encode()))
+
+
+def pospopcnt_tune_describe() -> str:
+    buf = ctypes.create_string_buffer(8192)
+    _check(lib().pospopcnt_tune_describe(buf, len(buf)))
+    return buf.value.decode()
+
+
+def pospopcnt_batch_graph_create(w: int, counts, base, offsets, m=None, stream=None) -> int:
+    if m is None:
+        m = offsets.numel() - 1 if hasattr(offsets, "numel") else len(offsets) - 1
+    h = _vp()
+    _check(lib().pospopcnt_batch_graph_create(w, _ptr(counts), _ptr(base), _ptr(offsets), m,
+                                              _stream(stream), ctypes.byref(h)))
+    return h.value
+
+
+def pospopcnt_graph_launch(graph: int, stream=None):
+    return _check(lib().pospopcnt_graph_launch(graph, _stream(stream)))
+
+
+def pospopcnt_graph_destroy(graph: int):
+    return _check(lib().pospopcnt_graph_destroy(graph))
+
+
+def pospopcnt_launch_count() -> int:
+    return int(lib().pospopcnt_launch_count())

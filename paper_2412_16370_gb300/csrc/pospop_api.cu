@@ -1,0 +1,907 @@
+// pospop_api.cu -- the C ABI of libpospopcnt.so (declared in
+// include/pospopcnt.h): argument checks, per-device contexts, workspaces,
+// launch planning, the host-memory path and CUDA graphs.
+//
+// Every count runs in the sm_103a kernels of pospop_stream.cu and
+// pospop_batch.cu; this file only validates, plans and enqueues.
+#include <dlfcn.h>
+
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "pospopcnt.h"
+#include "pospop_runtime.h"
+
+namespace pospop {
+
+static std::mutex g_mu;
+static DevCtx *g_ctx[kMaxDevices] = {nullptr};
+static std::atomic<uint64_t> g_launches{0};
+
+void note_launches(uint64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+static bool valid_w(int w) {
+  return w == 1 || w == 2 || w == 4 || w == 8 || w == 16 || w == 32 || w == 64;
+}
+
+// ---------------------------------------------------------------------------
+// Tune table.
+// ---------------------------------------------------------------------------
+int size_class(uint64_t rows) {
+  if (rows <= 64) return 0;          // <= 32 KiB
+  if (rows <= 2048) return 1;        // <= 1 MiB
+  if (rows <= 65536) return 2;       // <= 32 MiB
+  if (rows <= (1u << 21)) return 3;  // <= 1 GiB
+  return 4;
+}
+
+int find_variant(bool batch, int bs, int minb, int depth, int hint) {
+  const int n = batch ? batch_variant_count() : stream_variant_count();
+  for (int i = 0; i < n; i++) {
+    const Variant &v = batch ? batch_variant(i) : stream_variant(i);
+    if (v.bs == bs && v.minb == minb && v.depth == depth && v.hint == hint) return i;
+  }
+  return -1;
+}
+
+static int find_roof_variant(int bs, int hint) {
+  for (int i = 0; i < roofline_variant_count(); i++)
+    if (roofline_variant(i).bs == bs && roofline_variant(i).hint == hint) return i;
+  return -1;
+}
+
+TuneTable default_tune() {
+  TuneTable t;
+  const int sv = find_variant(false, 512, 1, 16, 1);
+  const uint32_t minrows[kClasses] = {2, 4, 8, 16, 16};
+  for (int c = 0; c < kClasses; c++) t.stream[c] = StreamTune{sv, 1, minrows[c]};
+  t.batch = BatchTune{find_variant(true, 256, 2, 16, 1), 2, 511, 1};
+  t.roof = RoofTune{find_roof_variant(512, 1), 4};
+  t.source = "built-in defaults";
+  return t;
+}
+
+// Text format, one entry per line ('#' starts a comment):
+//   stream <class> <bs> <minb> <depth> <hint> <ctas_per_sm> <min_rows>
+//   batch <bs> <minb> <depth> <hint> <ctas_per_sm> <item_rows> <grab>
+//   roofline <bs> <hint> <ctas_per_sm>
+int parse_tune(const char *text, TuneTable *out) {
+  TuneTable t = default_tune();
+  std::string s(text);
+  size_t pos = 0;
+  int lineno = 0;
+  while (pos < s.size()) {
+    size_t nl = s.find('\n', pos);
+    if (nl == std::string::npos) nl = s.size();
+    std::string line = s.substr(pos, nl - pos);
+    pos = nl + 1;
+    lineno++;
+    const size_t hash = line.find('#');
+    if (hash != std::string::npos) line.resize(hash);
+    char kind[16] = {0};
+    if (sscanf(line.c_str(), "%15s", kind) != 1) continue;
+    if (strcmp(kind, "stream") == 0) {
+      int c, bs, minb, d, h, cps;
+      unsigned mr;
+      if (sscanf(line.c_str(), "%*s %d %d %d %d %d %d %u", &c, &bs, &minb, &d, &h, &cps, &mr) != 7)
+        return POSPOP_EINVAL;
+      const int v = find_variant(false, bs, minb, d, h);
+      if (c < 0 || c >= kClasses || v < 0 || cps < 1 || mr < 1) return POSPOP_EINVAL;
+      t.stream[c] = StreamTune{v, cps, mr};
+    } else if (strcmp(kind, "batch") == 0) {
+      int bs, minb, d, h, cps;
+      unsigned ir, grab;
+      if (sscanf(line.c_str(), "%*s %d %d %d %d %d %u %u", &bs, &minb, &d, &h, &cps, &ir, &grab) !=
+          7)
+        return POSPOP_EINVAL;
+      const int v = find_variant(true, bs, minb, d, h);
+      if (v < 0 || cps < 1 || ir < 1 || ir > (1u << 20) || grab < 1 || grab > 64)
+        return POSPOP_EINVAL;
+      t.batch = BatchTune{v, cps, ir, grab};
+    } else if (strcmp(kind, "roofline") == 0) {
+      int bs, h, cps;
+      if (sscanf(line.c_str(), "%*s %d %d %d", &bs, &h, &cps) != 3) return POSPOP_EINVAL;
+      const int v = find_roof_variant(bs, h);
+      if (v < 0 || cps < 1) return POSPOP_EINVAL;
+      t.roof = RoofTune{v, cps};
+    } else {
+      return POSPOP_EINVAL;
+    }
+  }
+  *out = t;
+  return POSPOP_OK;
+}
+
+std::string format_tune(const DevCtx &ctx, const TuneTable &t) {
+  std::string s;
+  char line[256];
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, ctx.device) != cudaSuccess) {
+    cudaGetLastError();
+    snprintf(prop.name, sizeof(prop.name), "unknown");
+  }
+  snprintf(line, sizeof line, "# pospopcnt tune table: %s, %d SMs (%s)\n", prop.name, ctx.sms,
+           t.source.c_str());
+  s += line;
+  s += "# stream <class> <bs> <minb> <depth> <hint> <ctas_per_sm> <min_rows>\n";
+  for (int c = 0; c < kClasses; c++) {
+    const Variant &v = stream_variant(t.stream[c].variant);
+    snprintf(line, sizeof line, "stream %d %d %d %d %d %d %u\n", c, v.bs, v.minb, v.depth, v.hint,
+             t.stream[c].ctas_per_sm, t.stream[c].min_rows);
+    s += line;
+  }
+  {
+    const Variant &v = batch_variant(t.batch.variant);
+    s += "# batch <bs> <minb> <depth> <hint> <ctas_per_sm> <item_rows> <grab>\n";
+    snprintf(line, sizeof line, "batch %d %d %d %d %d %u %u\n", v.bs, v.minb, v.depth, v.hint,
+             t.batch.ctas_per_sm, t.batch.item_rows, t.batch.grab);
+    s += line;
+  }
+  {
+    const Variant &v = roofline_variant(t.roof.variant);
+    s += "# roofline <bs> <hint> <ctas_per_sm>\n";
+    snprintf(line, sizeof line, "roofline %d %d %d\n", v.bs, v.hint, t.roof.ctas_per_sm);
+    s += line;
+  }
+  return s;
+}
+
+static bool read_file(const std::string &path, std::string *out) {
+  FILE *f = fopen(path.c_str(), "rb");
+  if (!f) return false;
+  std::string s;
+  char buf[4096];
+  size_t n;
+  while ((n = fread(buf, 1, sizeof buf, f)) > 0) s.append(buf, n);
+  fclose(f);
+  *out = s;
+  return true;
+}
+
+// The tune table installed at set-up: $POSPOP_TUNE_FILE, else
+// pospopcnt_tune.txt next to this shared library, else the defaults.
+static TuneTable initial_tune() {
+  std::string path;
+  if (const char *env = getenv("POSPOP_TUNE_FILE")) {
+    path = env;
+  } else {
+    Dl_info info;
+    if (dladdr(reinterpret_cast<void *>(&initial_tune), &info) && info.dli_fname) {
+      std::string so = info.dli_fname;
+      const size_t slash = so.rfind('/');
+      path = (slash == std::string::npos ? std::string(".") : so.substr(0, slash)) +
+             "/pospopcnt_tune.txt";
+    }
+  }
+  std::string text;
+  TuneTable t;
+  if (!path.empty() && read_file(path, &text) && parse_tune(text.c_str(), &t) == POSPOP_OK) {
+    t.source = path;
+    return t;
+  }
+  return default_tune();
+}
+
+// ---------------------------------------------------------------------------
+// Device contexts.
+// ---------------------------------------------------------------------------
+static int init_ctx(DevCtx &c, int device) {
+  if (cudaSetDevice(device) != cudaSuccess) { cudaGetLastError(); return POSPOP_ECUDA; }
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
+    cudaGetLastError();
+    return POSPOP_ECUDA;
+  }
+  for (int i = 0; i < stream_variant_count(); i++) {
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, stream_variant(i).fn,
+                                                      stream_variant(i).bs, 0) != cudaSuccess) {
+      cudaGetLastError();
+      return POSPOP_ECUDA;
+    }
+    c.occ_stream[i] = n > 0 ? n : 1;
+  }
+  for (int i = 0; i < batch_variant_count(); i++) {
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_variant(i).fn,
+                                                      batch_variant(i).bs, 0) != cudaSuccess) {
+      cudaGetLastError();
+      return POSPOP_ECUDA;
+    }
+    c.occ_batch[i] = n > 0 ? n : 1;
+  }
+  for (int i = 0; i < roofline_variant_count(); i++) {
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, roofline_variant(i).fn,
+                                                      roofline_variant(i).bs, 0) != cudaSuccess) {
+      cudaGetLastError();
+      return POSPOP_ECUDA;
+    }
+    c.occ_roof[i] = n > 0 ? n : 1;
+  }
+  c.device = device;
+  c.sms = sms;
+  c.tune = initial_tune();
+  c.ready = true;
+  return POSPOP_OK;
+}
+
+DevCtx *ctx_for_device(int device, int *rc) {
+  if (device < 0 || device >= kMaxDevices) { *rc = POSPOP_EINVAL; return nullptr; }
+  std::lock_guard<std::mutex> g(g_mu);
+  if (!g_ctx[device]) g_ctx[device] = new DevCtx();
+  DevCtx *c = g_ctx[device];
+  if (!c->ready) {
+    *rc = init_ctx(*c, device);
+    if (*rc != POSPOP_OK) return nullptr;
+  }
+  *rc = POSPOP_OK;
+  return c;
+}
+
+DevCtx *current_ctx(int *rc) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    *rc = POSPOP_ECUDA;
+    return nullptr;
+  }
+  return ctx_for_device(dev, rc);
+}
+
+static void free_staging(Staging &st) {
+  for (int b = 0; b < kStageBufs; b++) {
+    if (st.buf[b]) cudaFree(st.buf[b]);
+    if (st.copied[b]) cudaEventDestroy(st.copied[b]);
+    if (st.consumed[b]) cudaEventDestroy(st.consumed[b]);
+  }
+  if (st.dcounts) cudaFree(st.dcounts);
+  if (st.hcounts) cudaFreeHost(st.hcounts);
+  if (st.copy) cudaStreamDestroy(st.copy);
+  if (st.comp) cudaStreamDestroy(st.comp);
+  st = Staging();
+  cudaGetLastError();
+}
+
+static void free_ctx(DevCtx &c) {
+  int prev = -1;
+  cudaGetDevice(&prev);
+  cudaSetDevice(c.device);
+  cudaDeviceSynchronize();
+  for (auto &kv : c.ws)
+    if (kv.second.buf) cudaFree(kv.second.buf);
+  c.ws.clear();
+  free_staging(c.st);
+  c.ready = false;
+  cudaGetLastError();
+  if (prev >= 0) cudaSetDevice(prev);
+}
+
+// ---------------------------------------------------------------------------
+// Pointer kinds.
+// ---------------------------------------------------------------------------
+enum PtrKind { kDev, kPinned, kPageable, kBadPtr };
+
+static PtrKind classify(const void *p, int device, const void **devptr) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return kBadPtr;
+  }
+  switch (a.type) {
+    case cudaMemoryTypeDevice:
+      if (a.device != device) return kBadPtr;
+      if (devptr) *devptr = p;
+      return kDev;
+    case cudaMemoryTypeManaged:
+      if (devptr) *devptr = p;
+      return kDev;
+    case cudaMemoryTypeHost:
+      if (!a.devicePointer) return kBadPtr;
+      if (devptr) *devptr = a.devicePointer;
+      return kPinned;
+    default:
+      return kPageable;
+  }
+}
+
+static bool device_addressable(const void *p, int device, const void **devptr) {
+  const PtrKind k = classify(p, device, devptr);
+  return k == kDev || k == kPinned;
+}
+
+// ---------------------------------------------------------------------------
+// Single-array launches.
+// ---------------------------------------------------------------------------
+StreamPlan plan_stream(const DevCtx &ctx, const TuneTable &t, uint64_t rows) {
+  StreamPlan p;
+  p.cls = size_class(rows);
+  const StreamTune &st = t.stream[p.cls];
+  p.variant = st.variant;
+  const Variant &v = stream_variant(st.variant);
+  int cps = st.ctas_per_sm < ctx.occ_stream[st.variant] ? st.ctas_per_sm : ctx.occ_stream[st.variant];
+  if (cps < 1) cps = 1;
+  p.cps = cps;
+  const uint64_t wpb = (uint64_t)v.bs / 32;
+  const uint64_t max_grid = (uint64_t)ctx.sms * (uint64_t)cps;
+  const uint64_t want_warps = (rows + st.min_rows - 1) / st.min_rows;
+  uint64_t grid = (want_warps + wpb - 1) / wpb;
+  if (grid < 1) grid = 1;
+  if (grid > max_grid) grid = max_grid;
+  p.grid = (unsigned)grid;
+  p.block = (unsigned)v.bs;
+  p.rows = rows;
+  p.rows_per_launch = grid * wpb * kMaxRowsPerWarp;
+  p.launches = rows == 0 ? 0 : (int)((rows + p.rows_per_launch - 1) / p.rows_per_launch);
+  return p;
+}
+
+int launch_stream_with(const DevCtx &ctx, const TuneTable &t, int w, unsigned long long *counts,
+                       const void *bytes, size_t nbytes, cudaStream_t stream) {
+  if (nbytes == 0) return POSPOP_OK;
+  const uint64_t p0 = (uint64_t)bytes, e = p0 + nbytes;
+  StreamParams P;
+  const uint64_t A = p0 & ~15ull;
+  P.s.A = reinterpret_cast<const uint8_t *>(A);
+  P.s.head = (uint32_t)(p0 - A);
+  P.s.G = (((e + 15u) & ~15ull) - A) >> 4;
+  P.s.tail = (uint32_t)(e - (A + 16u * (P.s.G - 1)));
+  P.counts = counts;
+  P.w = w;
+  P.rot = (8u * P.s.head) & (uint32_t)(w - 1);
+  const uint64_t R = (P.s.G + 31) >> 5;
+  const StreamPlan pl = plan_stream(ctx, t, R);
+  const Variant &v = stream_variant(pl.variant);
+  for (uint64_t rb = 0; rb < R; rb += pl.rows_per_launch) {
+    P.row_begin = rb;
+    P.row_end = (R - rb > pl.rows_per_launch) ? rb + pl.rows_per_launch : R;
+    void *args[] = {&P};
+    if (cudaLaunchKernel(v.fn, dim3(pl.grid), dim3(pl.block), args, 0, stream) != cudaSuccess) {
+      cudaGetLastError();
+      return POSPOP_ECUDA;
+    }
+    note_launches(1);
+  }
+  return POSPOP_OK;
+}
+
+int launch_stream(DevCtx &ctx, int w, unsigned long long *counts, const void *bytes, size_t nbytes,
+                  cudaStream_t stream) {
+  TuneTable t;
+  {
+    std::lock_guard<std::mutex> g(ctx.mu);
+    t = ctx.tune;
+  }
+  return launch_stream_with(ctx, t, w, counts, bytes, nbytes, stream);
+}
+
+int launch_roofline_with(const DevCtx &ctx, const RoofTune &rt, const void *bytes, size_t nbytes,
+                         unsigned long long *sum, cudaStream_t stream) {
+  const uint64_t p0 = (uint64_t)bytes;
+  const uint64_t A = (p0 + 15u) & ~15ull, E = (p0 + nbytes) & ~15ull;
+  if (E <= A) return POSPOP_OK;
+  RooflineParams P;
+  P.A = reinterpret_cast<const uint8_t *>(A);
+  P.G = (E - A) >> 4;
+  P.sum = sum;
+  const Variant &v = roofline_variant(rt.variant);
+  int cps = rt.ctas_per_sm < ctx.occ_roof[rt.variant] ? rt.ctas_per_sm : ctx.occ_roof[rt.variant];
+  if (cps < 1) cps = 1;
+  const uint64_t rows = (P.G + 31) >> 5;
+  uint64_t grid = (rows + (v.bs / 32) - 1) / (v.bs / 32);
+  const uint64_t max_grid = (uint64_t)ctx.sms * cps;
+  if (grid > max_grid) grid = max_grid;
+  if (grid < 1) grid = 1;
+  void *args[] = {&P};
+  if (cudaLaunchKernel(v.fn, dim3((unsigned)grid), dim3(v.bs), args, 0, stream) != cudaSuccess) {
+    cudaGetLastError();
+    return POSPOP_ECUDA;
+  }
+  note_launches(1);
+  return POSPOP_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Batched launches and their workspace.
+// ---------------------------------------------------------------------------
+static size_t ws_bytes(size_t m_cap) {
+  const size_t nb = (m_cap + kPlanChunk - 1) / kPlanChunk + 1;
+  return 8 * (m_cap + 1) + 8 * nb + 16;
+}
+
+static int is_capturing(cudaStream_t s, bool *cap) {
+  cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &st) != cudaSuccess) {
+    cudaGetLastError();
+    return POSPOP_ECUDA;
+  }
+  *cap = st != cudaStreamCaptureStatusNone;
+  return POSPOP_OK;
+}
+
+// Workspace of `stream` with room for m arrays (grown if needed).  Caller
+// holds ctx.mu.
+static int get_ws(DevCtx &ctx, cudaStream_t stream, size_t m, Workspace **out) {
+  Workspace &w = ctx.ws[stream];
+  if (w.buf && w.m_cap >= m) {
+    *out = &w;
+    return POSPOP_OK;
+  }
+  bool cap = false;
+  int rc = is_capturing(stream, &cap);
+  if (rc != POSPOP_OK) return rc;
+  if (cap) return POSPOP_ENOMEM;   // no allocation inside a capture: call pospopcnt_reserve first
+  size_t cap_m = w.m_cap ? w.m_cap : 65536;
+  while (cap_m < m) cap_m *= 2;
+  void *buf = nullptr;
+  if (cudaMalloc(&buf, ws_bytes(cap_m)) != cudaSuccess) {
+    cudaGetLastError();
+    return POSPOP_ENOMEM;
+  }
+  if (w.buf) {
+    // the old buffer may still be in use by work queued on this stream
+    if (cudaStreamSynchronize(stream) != cudaSuccess) { cudaGetLastError(); }
+    cudaFree(w.buf);
+  }
+  const size_t nb = (cap_m + kPlanChunk - 1) / kPlanChunk + 1;
+  uint8_t *b = static_cast<uint8_t *>(buf);
+  w.buf = buf;
+  w.m_cap = cap_m;
+  w.item_start = reinterpret_cast<uint64_t *>(b);
+  w.block_sum = reinterpret_cast<uint64_t *>(b + 8 * (cap_m + 1));
+  w.next = reinterpret_cast<unsigned long long *>(b + 8 * (cap_m + 1) + 8 * nb);
+  w.status = reinterpret_cast<int *>(b + 8 * (cap_m + 1) + 8 * nb + 8);
+  if (cudaMemsetAsync(w.status, 0, sizeof(int), stream) != cudaSuccess) {
+    cudaGetLastError();
+    return POSPOP_ECUDA;
+  }
+  *out = &w;
+  return POSPOP_OK;
+}
+
+static int launch_plan(const DevCtx &ctx, const PlanParams &pp, cudaStream_t stream) {
+  (void)ctx;
+  PlanParams P = pp;
+  void *args[] = {&P};
+  if (cudaLaunchKernel(plan_items_fn(), dim3(P.nblocks), dim3(kPlanThreads), args, 0, stream) !=
+          cudaSuccess ||
+      cudaLaunchKernel(plan_scan_fn(), dim3(1), dim3(kPlanThreads), args, 0, stream) !=
+          cudaSuccess ||
+      cudaLaunchKernel(plan_apply_fn(), dim3(P.nblocks), dim3(kPlanThreads), args, 0, stream) !=
+          cudaSuccess) {
+    cudaGetLastError();
+    return POSPOP_ECUDA;
+  }
+  note_launches(3);
+  return POSPOP_OK;
+}
+
+int launch_batch_with(DevCtx &ctx, const TuneTable &t, int w, unsigned long long *counts,
+                      const void *base, const uint64_t *offsets, size_t m, cudaStream_t stream) {
+  Workspace *ws = nullptr;
+  {
+    std::lock_guard<std::mutex> g(ctx.mu);
+    const int rc = get_ws(ctx, stream, m, &ws);
+    if (rc != POSPOP_OK) return rc;
+  }
+  if (cudaMemsetAsync(ws->status, 0, sizeof(int), stream) != cudaSuccess) {
+    cudaGetLastError();
+    return POSPOP_ECUDA;
+  }
+  PlanParams pp;
+  pp.offsets = offsets;
+  pp.m = m;
+  pp.base_addr = (uint64_t)base;
+  pp.item_start = ws->item_start;
+  pp.block_sum = ws->block_sum;
+  pp.next = ws->next;
+  pp.status = ws->status;
+  pp.item_rows = t.batch.item_rows;
+  pp.nblocks = (uint32_t)((m + kPlanChunk - 1) / kPlanChunk);
+  int rc = launch_plan(ctx, pp, stream);
+  if (rc != POSPOP_OK) return rc;
+
+  BatchParams bp;
+  bp.base = static_cast<const uint8_t *>(base);
+  bp.offsets = offsets;
+  bp.m = m;
+  bp.counts = counts;
+  bp.w = w;
+  bp.item_start = ws->item_start;
+  bp.next = ws->next;
+  bp.status = ws->status;
+  bp.item_rows = t.batch.item_rows;
+  bp.grab = t.batch.grab;
+  const Variant &v = batch_variant(t.batch.variant);
+  int cps = t.batch.ctas_per_sm < ctx.occ_batch[t.batch.variant] ? t.batch.ctas_per_sm
+                                                                 : ctx.occ_batch[t.batch.variant];
+  if (cps < 1) cps = 1;
+  void *args[] = {&bp};
+  if (cudaLaunchKernel(v.fn, dim3((unsigned)(ctx.sms * cps)), dim3(v.bs), args, 0, stream) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    return POSPOP_ECUDA;
+  }
+  note_launches(1);
+  return POSPOP_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Host-memory path.
+// ---------------------------------------------------------------------------
+static int ensure_staging(DevCtx &ctx) {
+  Staging &st = ctx.st;
+  if (st.ready) return POSPOP_OK;
+  bool ok = cudaStreamCreateWithFlags(&st.copy, cudaStreamNonBlocking) == cudaSuccess &&
+            cudaStreamCreateWithFlags(&st.comp, cudaStreamNonBlocking) == cudaSuccess &&
+            cudaMalloc(&st.dcounts, 64 * sizeof(unsigned long long)) == cudaSuccess &&
+            cudaMallocHost(&st.hcounts, 64 * sizeof(unsigned long long)) == cudaSuccess;
+  for (int b = 0; ok && b < kStageBufs; b++)
+    ok = cudaMalloc(&st.buf[b], kStageChunk) == cudaSuccess &&
+         cudaEventCreateWithFlags(&st.copied[b], cudaEventDisableTiming) == cudaSuccess &&
+         cudaEventCreateWithFlags(&st.consumed[b], cudaEventDisableTiming) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    free_staging(st);
+    return POSPOP_ENOMEM;
+  }
+  st.ready = true;
+  return POSPOP_OK;
+}
+
+static int host_count(DevCtx &ctx, int w, uint64_t *counts, const void *bytes, size_t nbytes) {
+  const void *dev_bytes = nullptr;
+  const PtrKind kc = classify(counts, ctx.device, nullptr);
+  const PtrKind kb = classify(bytes, ctx.device, &dev_bytes);
+  if ((kc != kPinned && kc != kPageable) || (kb != kPinned && kb != kPageable)) return POSPOP_EPTR;
+  std::lock_guard<std::mutex> g(ctx.host_mu);
+  int rc = ensure_staging(ctx);
+  if (rc != POSPOP_OK) return rc;
+  Staging &st = ctx.st;
+  TuneTable t;
+  {
+    std::lock_guard<std::mutex> g2(ctx.mu);
+    t = ctx.tune;
+  }
+  if (cudaMemsetAsync(st.dcounts, 0, 64 * sizeof(unsigned long long), st.comp) != cudaSuccess) {
+    cudaGetLastError();
+    return POSPOP_ECUDA;
+  }
+  const bool staged = kb == kPageable || getenv("POSPOP_HOST_STAGED") != nullptr;
+  if (!staged) {
+    // Pinned memory: the kernel reads it in place over the CPU-GPU link.
+    rc = launch_stream_with(ctx, t, w, st.dcounts, dev_bytes, nbytes, st.comp);
+    if (rc != POSPOP_OK) return rc;
+  } else {
+    const uint8_t *src = static_cast<const uint8_t *>(bytes);
+    size_t chunk = 0;
+    for (size_t off = 0; off < nbytes; off += kStageChunk, chunk++) {
+      const int b = (int)(chunk % kStageBufs);
+      const size_t len = nbytes - off < kStageChunk ? nbytes - off : kStageChunk;
+      // chunk starts are multiples of 64 MiB from the start, so every chunk
+      // starts on a word boundary and its counters line up with the whole's
+      if (cudaStreamWaitEvent(st.copy, st.consumed[b], 0) != cudaSuccess ||
+          cudaMemcpyAsync(st.buf[b], src + off, len, cudaMemcpyHostToDevice, st.copy) !=
+              cudaSuccess ||
+          cudaEventRecord(st.copied[b], st.copy) != cudaSuccess ||
+          cudaStreamWaitEvent(st.comp, st.copied[b], 0) != cudaSuccess) {
+        cudaGetLastError();
+        return POSPOP_ECUDA;
+      }
+      rc = launch_stream_with(ctx, t, w, st.dcounts, st.buf[b], len, st.comp);
+      if (rc != POSPOP_OK) return rc;
+      if (cudaEventRecord(st.consumed[b], st.comp) != cudaSuccess) {
+        cudaGetLastError();
+        return POSPOP_ECUDA;
+      }
+    }
+  }
+  if (cudaMemcpyAsync(st.hcounts, st.dcounts, (size_t)w * sizeof(unsigned long long),
+                      cudaMemcpyDeviceToHost, st.comp) != cudaSuccess ||
+      cudaStreamSynchronize(st.comp) != cudaSuccess) {
+    cudaGetLastError();
+    return POSPOP_ECUDA;
+  }
+  for (int j = 0; j < w; j++) counts[j] += st.hcounts[j];
+  return POSPOP_OK;
+}
+
+}  // namespace pospop
+
+using namespace pospop;
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+const char *pospopcnt_strerror(int code) {
+  switch (code) {
+    case POSPOP_OK: return "success";
+    case POSPOP_EINVAL: return "invalid argument (NULL pointer with nonzero size, bad width, or decreasing offsets)";
+    case POSPOP_EPTR: return "pointer is not addressable by the current device (or of the wrong kind)";
+    case POSPOP_ECUDA: return "CUDA runtime error or kernel launch failure";
+    case POSPOP_ENOMEM: return "out of device or pinned memory (or allocation needed during graph capture)";
+    case POSPOP_ETIMEDOUT: return "timed out";
+    case POSPOP_EBUSY: return "busy: no free slot or memory budget";
+    case POSPOP_ERANGE: return "size beyond the supported maximum";
+    default: return "unknown status code";
+  }
+}
+
+int pospopcnt_init(int device) {
+  int rc = POSPOP_OK;
+  DevCtx *c = ctx_for_device(device, &rc);
+  if (!c) return rc;
+  if (cudaSetDevice(device) != cudaSuccess) {
+    cudaGetLastError();
+    return POSPOP_ECUDA;
+  }
+  return POSPOP_OK;
+}
+
+void pospopcnt_shutdown(void) {
+  std::lock_guard<std::mutex> g(g_mu);
+  for (int d = 0; d < kMaxDevices; d++) {
+    if (g_ctx[d] && g_ctx[d]->ready) {
+      std::lock_guard<std::mutex> g1(g_ctx[d]->mu);
+      std::lock_guard<std::mutex> g2(g_ctx[d]->host_mu);
+      free_ctx(*g_ctx[d]);
+    }
+  }
+}
+
+int pospopcnt_async(int w, uint64_t *counts, const void *bytes, size_t nbytes, void *stream) {
+  if (!valid_w(w)) return POSPOP_EINVAL;
+  if (nbytes == 0) return POSPOP_OK;
+  if (!counts || !bytes) return POSPOP_EINVAL;
+  int rc = POSPOP_OK;
+  DevCtx *c = current_ctx(&rc);
+  if (!c) return rc;
+  const void *dc = nullptr, *db = nullptr;
+  if (!device_addressable(counts, c->device, &dc) || !device_addressable(bytes, c->device, &db))
+    return POSPOP_EPTR;
+  return launch_stream(*c, w, (unsigned long long *)const_cast<void *>(dc), db, nbytes,
+                       static_cast<cudaStream_t>(stream));
+}
+
+static int typed_count(int w, uint64_t *counts, const void *words, size_t n) {
+  if (n == 0) return POSPOP_OK;
+  if (!counts || !words) return POSPOP_EINVAL;
+  const size_t W = (size_t)w / 8;
+  if (n > SIZE_MAX / W) return POSPOP_ERANGE;
+  int rc = POSPOP_OK;
+  DevCtx *c = current_ctx(&rc);
+  if (!c) return rc;
+  const void *dc = nullptr, *dw = nullptr;
+  const PtrKind kc = classify(counts, c->device, &dc);
+  const PtrKind kw = classify(words, c->device, &dw);
+  if (kc == kBadPtr || kw == kBadPtr) return POSPOP_EPTR;
+  const bool dev_c = kc == kDev, dev_w = kw == kDev;
+  if (dev_c != dev_w) return POSPOP_EPTR;
+  if (!dev_c) return host_count(*c, w, counts, words, n * W);
+  rc = launch_stream(*c, w, (unsigned long long *)const_cast<void *>(dc), dw, n * W, nullptr);
+  if (rc != POSPOP_OK) return rc;
+  if (cudaStreamSynchronize(nullptr) != cudaSuccess) {
+    cudaGetLastError();
+    return POSPOP_ECUDA;
+  }
+  return POSPOP_OK;
+}
+
+int pospopcnt_u8(uint64_t counts[8], const uint8_t *words, size_t n) {
+  return typed_count(8, counts, words, n);
+}
+int pospopcnt_u16(uint64_t counts[16], const uint16_t *words, size_t n) {
+  return typed_count(16, counts, words, n);
+}
+int pospopcnt_u32(uint64_t counts[32], const uint32_t *words, size_t n) {
+  return typed_count(32, counts, words, n);
+}
+int pospopcnt_u64(uint64_t counts[64], const uint64_t *words, size_t n) {
+  return typed_count(64, counts, words, n);
+}
+
+int pospopcnt_batch(int w, uint64_t *counts, const void *base, const uint64_t *offsets, size_t m,
+                    void *stream) {
+  if (!valid_w(w)) return POSPOP_EINVAL;
+  if (m == 0) return POSPOP_OK;
+  if (!counts || !base || !offsets) return POSPOP_EINVAL;
+  if (m > (SIZE_MAX / 8) / 64 - 1) return POSPOP_ERANGE;
+  int rc = POSPOP_OK;
+  DevCtx *c = current_ctx(&rc);
+  if (!c) return rc;
+  const void *dc = nullptr, *db = nullptr, *doff = nullptr;
+  if (!device_addressable(counts, c->device, &dc) || !device_addressable(base, c->device, &db) ||
+      !device_addressable(offsets, c->device, &doff))
+    return POSPOP_EPTR;
+  TuneTable t;
+  {
+    std::lock_guard<std::mutex> g(c->mu);
+    t = c->tune;
+  }
+  return launch_batch_with(*c, t, w, (unsigned long long *)const_cast<void *>(dc), db,
+                           static_cast<const uint64_t *>(doff), m,
+                           static_cast<cudaStream_t>(stream));
+}
+
+int pospopcnt_batch_status(void *stream) {
+  int rc = POSPOP_OK;
+  DevCtx *c = current_ctx(&rc);
+  if (!c) return rc;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (cudaStreamSynchronize(s) != cudaSuccess) {
+    cudaGetLastError();
+    return POSPOP_ECUDA;
+  }
+  int *status = nullptr;
+  {
+    std::lock_guard<std::mutex> g(c->mu);
+    auto it = c->ws.find(s);
+    if (it == c->ws.end() || !it->second.buf) return POSPOP_OK;
+    status = it->second.status;
+  }
+  int h = 0;
+  if (cudaMemcpy(&h, status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemset(status, 0, sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    return POSPOP_ECUDA;
+  }
+  return h == 0 ? POSPOP_OK : POSPOP_EINVAL;
+}
+
+int pospopcnt_reserve(size_t m_max, void *stream) {
+  int rc = POSPOP_OK;
+  DevCtx *c = current_ctx(&rc);
+  if (!c) return rc;
+  std::lock_guard<std::mutex> g(c->mu);
+  Workspace *ws = nullptr;
+  return get_ws(*c, static_cast<cudaStream_t>(stream), m_max ? m_max : 1, &ws);
+}
+
+int pospopcnt_host(int w, uint64_t *counts, const void *bytes, size_t nbytes) {
+  if (!valid_w(w)) return POSPOP_EINVAL;
+  if (nbytes == 0) return POSPOP_OK;
+  if (!counts || !bytes) return POSPOP_EINVAL;
+  int rc = POSPOP_OK;
+  DevCtx *c = current_ctx(&rc);
+  if (!c) return rc;
+  return host_count(*c, w, counts, bytes, nbytes);
+}
+
+int pospopcnt_roofline_read(const void *bytes, size_t nbytes, uint64_t *sum, void *stream) {
+  if (nbytes == 0) return POSPOP_OK;
+  if (!bytes || !sum) return POSPOP_EINVAL;
+  int rc = POSPOP_OK;
+  DevCtx *c = current_ctx(&rc);
+  if (!c) return rc;
+  const void *db = nullptr, *ds = nullptr;
+  if (!device_addressable(bytes, c->device, &db) || !device_addressable(sum, c->device, &ds))
+    return POSPOP_EPTR;
+  RoofTune rt;
+  {
+    std::lock_guard<std::mutex> g(c->mu);
+    rt = c->tune.roof;
+  }
+  return launch_roofline_with(*c, rt, db, nbytes, (unsigned long long *)const_cast<void *>(ds),
+                              static_cast<cudaStream_t>(stream));
+}
+
+int pospopcnt_plan(int w, size_t nbytes, uint32_t plan[8]) {
+  if (!valid_w(w) || !plan) return POSPOP_EINVAL;
+  int rc = POSPOP_OK;
+  DevCtx *c = current_ctx(&rc);
+  if (!c) return rc;
+  TuneTable t;
+  {
+    std::lock_guard<std::mutex> g(c->mu);
+    t = c->tune;
+  }
+  const uint64_t G = (nbytes + 15) / 16;
+  const uint64_t R = (G + 31) / 32;
+  const StreamPlan p = plan_stream(*c, t, R);
+  const Variant &v = stream_variant(p.variant);
+  plan[0] = p.grid;
+  plan[1] = p.block;
+  plan[2] = (uint32_t)v.depth;
+  plan[3] = (uint32_t)v.hint;
+  plan[4] = (uint32_t)p.cls;
+  plan[5] = (uint32_t)(R > 0xffffffffu ? 0xffffffffu : R);
+  plan[6] = (uint32_t)p.launches;
+  plan[7] = (uint32_t)p.cps;
+  return POSPOP_OK;
+}
+
+int pospopcnt_tune_load(const char *path) {
+  if (!path) return POSPOP_EINVAL;
+  int rc = POSPOP_OK;
+  DevCtx *c = current_ctx(&rc);
+  if (!c) return rc;
+  std::string text;
+  if (!read_file(path, &text)) return POSPOP_EINVAL;
+  TuneTable t;
+  rc = parse_tune(text.c_str(), &t);
+  if (rc != POSPOP_OK) return rc;
+  t.source = path;
+  std::lock_guard<std::mutex> g(c->mu);
+  c->tune = t;
+  return POSPOP_OK;
+}
+
+int pospopcnt_tune_describe(char *buf, size_t len) {
+  if (!buf || len == 0) return POSPOP_EINVAL;
+  int rc = POSPOP_OK;
+  DevCtx *c = current_ctx(&rc);
+  if (!c) return rc;
+  std::string s;
+  {
+    std::lock_guard<std::mutex> g(c->mu);
+    s = format_tune(*c, c->tune);
+  }
+  snprintf(buf, len, "%s", s.c_str());
+  return s.size() < len ? POSPOP_OK : POSPOP_ERANGE;
+}
+
+struct pospop_graph {
+  cudaGraph_t graph;
+  cudaGraphExec_t exec;
+};
+
+int pospopcnt_batch_graph_create(int w, uint64_t *counts, const void *base,
+                                 const uint64_t *offsets, size_t m, void *stream, void **graph) {
+  if (!graph || !stream) return POSPOP_EINVAL;   // the legacy stream cannot be captured
+  *graph = nullptr;
+  int rc = pospopcnt_reserve(m, stream);
+  if (rc != POSPOP_OK) return rc;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaGetLastError();
+    return POSPOP_ECUDA;
+  }
+  rc = pospopcnt_batch(w, counts, base, offsets, m, stream);
+  cudaGraph_t g = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(s, &g);
+  if (rc == POSPOP_OK && e != cudaSuccess) rc = POSPOP_ECUDA;
+  if (rc != POSPOP_OK) {
+    cudaGetLastError();
+    if (g) cudaGraphDestroy(g);
+    return rc;
+  }
+  cudaGraphExec_t x = nullptr;
+  if (cudaGraphInstantiate(&x, g, 0) != cudaSuccess) {
+    cudaGetLastError();
+    cudaGraphDestroy(g);
+    return POSPOP_ECUDA;
+  }
+  pospop_graph *h = new pospop_graph{g, x};
+  *graph = h;
+  return POSPOP_OK;
+}
+
+int pospopcnt_graph_launch(void *graph, void *stream) {
+  if (!graph) return POSPOP_EINVAL;
+  pospop_graph *h = static_cast<pospop_graph *>(graph);
+  if (cudaGraphLaunch(h->exec, static_cast<cudaStream_t>(stream)) != cudaSuccess) {
+    cudaGetLastError();
+    return POSPOP_ECUDA;
+  }
+  note_launches(4);
+  return POSPOP_OK;
+}
+
+int pospopcnt_graph_destroy(void *graph) {
+  if (!graph) return POSPOP_EINVAL;
+  pospop_graph *h = static_cast<pospop_graph *>(graph);
+  cudaGraphExecDestroy(h->exec);
+  cudaGraphDestroy(h->graph);
+  delete h;
+  return POSPOP_OK;
+}
+
+uint64_t pospopcnt_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+
+}  // extern "C"

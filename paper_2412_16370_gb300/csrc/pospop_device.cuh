@@ -1,0 +1,359 @@
+// pospop_device.cuh -- device building blocks of the sm_103a positional
+// population count (arXiv 2412.16370, Sections 3-4), shared by the
+// single-array, batched and serving kernels.
+//
+// Data layout.  The input byte stream is cut into 16-byte granules aligned
+// to 16 bytes (the first granule starts at the start address rounded down).
+// One granule is four 32-bit lanes: lane r holds granule bit positions
+// 32r .. 32r+31, and granule bit position k = 8 * (byte in granule) + bit.
+// A "row" is 32 consecutive granules (512 bytes); lane l of a warp always
+// handles granule l of a row, so every warp-wide load is one coalesced
+// 512-byte row.  Because 16-byte granules are aligned and w divides 128,
+// granule bit position k always belongs to counter (k - 8*head) mod w, where
+// head is the start's offset past the 16-byte boundary.
+//
+// Per thread, the granules of the rows a thread visits are reduced in
+// registers with the paper's carry-save-adder (CSA) networks: CSA_15 for the
+// first 15 vectors (Section 4.2, 11 full adders), then CSA_16+4 for every
+// further 16 (15 full adders), each full adder being two lop3 instructions
+// (Section 3.1.1, Eq. 3: parity 0x96 for the sum, majority 0xe8 for the
+// carry).  The a16 bit vector skimmed off every 16 vectors (Section 4.3,
+// Eq. 4) is counted with a 32x32 bit transpose across the warp followed by
+// one popcount per lane, which yields the warp-wide count of one bit
+// position per lane; the final (a8, a4, a2, a1) vectors are counted the same
+// way with weights 8, 4, 2, 1 (Section 4.5).  Counters are u32 per lane and
+// position; the host bounds the rows per warp so they cannot overflow (the
+// role of Eq. 5, Section 4.4).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace pospop {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kGranule = 16;               // bytes per granule (one uint4 per lane)
+constexpr int kRowBytes = 32 * kGranule;   // 512 bytes per warp row
+
+// ---------------------------------------------------------------------------
+// Bit-parallel full adder (Section 3.1.1, Eq. 3): one lop3 per output.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t lop3_parity(uint32_t a, uint32_t b, uint32_t c) {
+  uint32_t r;
+  asm("lop3.b32 %0, %1, %2, %3, 0x96;" : "=r"(r) : "r"(a), "r"(b), "r"(c));
+  return r;
+}
+__device__ __forceinline__ uint32_t lop3_majority(uint32_t a, uint32_t b, uint32_t c) {
+  uint32_t r;
+  asm("lop3.b32 %0, %1, %2, %3, 0xe8;" : "=r"(r) : "r"(a), "r"(b), "r"(c));
+  return r;
+}
+
+struct V4 {
+  uint32_t x[4];
+};
+
+__device__ __forceinline__ V4 v4_zero() { return V4{{0u, 0u, 0u, 0u}}; }
+
+// (carry, sum) = FA(a, b, c) on all 128 bits of a granule.
+__device__ __forceinline__ void fa(V4 &sum, V4 &carry, const V4 &a, const V4 &b, const V4 &c) {
+  V4 s, k;
+#pragma unroll
+  for (int r = 0; r < 4; r++) {
+    s.x[r] = lop3_parity(a.x[r], b.x[r], c.x[r]);
+    k.x[r] = lop3_majority(a.x[r], b.x[r], c.x[r]);
+  }
+  sum = s;
+  carry = k;
+}
+
+// Half adder, used only to merge a16 vectors into the deeper a16 plane.
+__device__ __forceinline__ void ha(V4 &sum, V4 &carry, const V4 &a, const V4 &b) {
+  V4 s, k;
+#pragma unroll
+  for (int r = 0; r < 4; r++) {
+    s.x[r] = a.x[r] ^ b.x[r];
+    k.x[r] = a.x[r] & b.x[r];
+  }
+  sum = s;
+  carry = k;
+}
+
+// Bit-sliced per-thread accumulator: weights 1, 2, 4, 8 (and 16 when the
+// flush depth is 32 vectors).
+struct Planes {
+  V4 a1, a2, a4, a8, a16;
+};
+
+// CSA_15 (Section 4.2): 15 vectors of weight 1 -> (a8, a4, a2, a1) with 11
+// full adders and a critical path of 5.
+__device__ __forceinline__ void csa15(Planes &p, const V4 *v) {
+  V4 s0, s1, s2, s3, s4, c0, c1, c2, c3, c4;
+  fa(s0, c0, v[0], v[1], v[2]);
+  fa(s1, c1, v[3], v[4], v[5]);
+  fa(s2, c2, v[6], v[7], v[8]);
+  fa(s3, c3, v[9], v[10], v[11]);
+  fa(s4, c4, v[12], v[13], v[14]);
+  V4 t0, d0, d1;
+  fa(t0, d0, s0, s1, s2);
+  fa(p.a1, d1, t0, s3, s4);          // weight 1 done
+  V4 u0, u1, e0, e1, e2;
+  fa(u0, e0, c0, c1, c2);
+  fa(u1, e1, c3, c4, d0);
+  fa(p.a2, e2, u0, u1, d1);          // weight 2 done
+  fa(p.a4, p.a8, e0, e1, e2);        // weights 4 and 8
+}
+
+// CSA_16+4 (Section 4.2): 16 vectors of weight 1 plus (a8, a4, a2, a1) ->
+// (a16, a8, a4, a2, a1) with 15 full adders.  Returns a16.
+__device__ __forceinline__ V4 csa16(Planes &p, const V4 *v) {
+  V4 s0, s1, s2, s3, s4, c0, c1, c2, c3, c4;
+  fa(s0, c0, p.a1, v[0], v[1]);
+  fa(s1, c1, v[2], v[3], v[4]);
+  fa(s2, c2, v[5], v[6], v[7]);
+  fa(s3, c3, v[8], v[9], v[10]);
+  fa(s4, c4, v[11], v[12], v[13]);
+  V4 t0, t1, d0, d1, d2;
+  fa(t0, d0, s0, s1, s2);
+  fa(t1, d1, s3, s4, v[14]);
+  fa(p.a1, d2, t0, t1, v[15]);       // weight 1: 8 full adders
+  V4 u0, u1, u2, e0, e1, e2, e3;
+  fa(u0, e0, p.a2, c0, c1);
+  fa(u1, e1, c2, c3, c4);
+  fa(u2, e2, d0, d1, d2);
+  fa(p.a2, e3, u0, u1, u2);          // weight 2: 4 full adders
+  V4 x0, f0, f1;
+  fa(x0, f0, p.a4, e0, e1);
+  fa(p.a4, f1, x0, e2, e3);          // weight 4: 2 full adders
+  V4 a16;
+  fa(p.a8, a16, p.a8, f0, f1);       // weight 8: 1 full adder
+  return a16;
+}
+
+// ---------------------------------------------------------------------------
+// Warp-wide 32x32 bit transpose + popcount.
+//
+// Lane t holds row t (a 32-bit register).  Five exchange stages (distance
+// 16, 8, 4, 2, 1) each swap bit j of the row index with bit j of the column
+// index; afterwards lane l holds column l, i.e. bit l of every lane's
+// register, and its popcount is the warp-wide count of bit position l.
+// Per stage: one funnel-shift rotate, one shuffle, one lop3 select.
+// ---------------------------------------------------------------------------
+struct Xpose {
+  uint32_t amt[5];
+  uint32_t keep[5];
+};
+
+__device__ __forceinline__ Xpose make_xpose(unsigned lane) {
+  const uint32_t low[5] = {0x0000ffffu, 0x00ff00ffu, 0x0f0f0f0fu, 0x33333333u, 0x55555555u};
+  Xpose k;
+#pragma unroll
+  for (int s = 0; s < 5; s++) {
+    const unsigned j = 16u >> s;
+    const bool lower = (lane & j) == 0;
+    k.amt[s] = lower ? j : 32u - j;     // lower lanes send rotr(x, j), upper lanes rotl(x, j)
+    k.keep[s] = lower ? low[s] : ~low[s];
+  }
+  return k;
+}
+
+__device__ __forceinline__ uint32_t xpose_popc(uint32_t x, const Xpose &k) {
+#pragma unroll
+  for (int s = 0; s < 5; s++) {
+    const unsigned j = 16u >> s;
+    const uint32_t send = __funnelshift_r(x, x, k.amt[s]);
+    const uint32_t y = __shfl_xor_sync(kFull, send, j);
+    x = (x & k.keep[s]) | (y & ~k.keep[s]);
+  }
+  return (uint32_t)__popc(x);
+}
+
+// cnt[r] += weight * (warp-wide count of granule position 32r + lane in v).
+template <int SHIFT>
+__device__ __forceinline__ void flush_plane(uint32_t cnt[4], const V4 &v, const Xpose &k) {
+#pragma unroll
+  for (int r = 0; r < 4; r++) cnt[r] += xpose_popc(v.x[r], k) << SHIFT;
+}
+
+// ---------------------------------------------------------------------------
+// Loads.
+// ---------------------------------------------------------------------------
+// HINT 0: ld.global.nc with L1 no-allocate; HINT 1: additionally asks L2 to
+// fetch 256-byte sectors (streaming prefetch).
+template <int HINT>
+__device__ __forceinline__ V4 ldg_granule(const uint8_t *p) {
+  V4 v;
+  if (HINT == 1) {
+    asm("ld.global.nc.L1::no_allocate.L2::256B.v4.u32 {%0,%1,%2,%3}, [%4];"
+        : "=r"(v.x[0]), "=r"(v.x[1]), "=r"(v.x[2]), "=r"(v.x[3])
+        : "l"(p));
+  } else {
+    asm("ld.global.nc.L1::no_allocate.v4.u32 {%0,%1,%2,%3}, [%4];"
+        : "=r"(v.x[0]), "=r"(v.x[1]), "=r"(v.x[2]), "=r"(v.x[3])
+        : "l"(p));
+  }
+  return v;
+}
+
+// One array (or a piece of one) in granule coordinates.
+struct Span {
+  const uint8_t *A;   // 16-byte aligned address of granule 0
+  uint64_t G;         // granules (>= 1)
+  uint32_t head;      // bytes of granule 0 before the first counted byte (0..15)
+  uint32_t tail;      // counted bytes of granule G-1 (1..16)
+};
+
+__host__ __device__ __forceinline__ uint64_t span_rows(const Span &s) { return (s.G + 31) >> 5; }
+
+// Granule g with everything outside the span zeroed.  Bytes outside
+// [start, end) are never read: the partial first and last granules are read
+// byte by byte.
+template <int HINT>
+__device__ __forceinline__ V4 load_granule_masked(const Span &s, uint64_t g) {
+  if (g >= s.G) return v4_zero();
+  const uint32_t lo = (g == 0) ? s.head : 0u;
+  const uint32_t hi = (g == s.G - 1) ? s.tail : 16u;
+  const uint8_t *p = s.A + g * kGranule;
+  if (lo == 0u && hi == 16u) return ldg_granule<HINT>(p);
+  V4 v = v4_zero();
+  for (uint32_t b = lo; b < hi; b++) {
+    const uint32_t byte = __ldg(p + b);
+    v.x[b >> 2] |= byte << (8u * (b & 3u));
+  }
+  return v;
+}
+
+// ---------------------------------------------------------------------------
+// The per-thread algorithm (Section 4, steps 2-7) over a sequence of rows
+// row0, row0 + stride, ..., nrows of them.  Lane `lane` handles granule
+// 32 * row + lane of each row.  Adds the warp-wide counts of granule bit
+// positions 32r + lane (r = 0..3) into cnt[r].  Warp-uniform control flow.
+// ---------------------------------------------------------------------------
+template <int DEPTH, int HINT>
+__device__ __forceinline__ void count_rows(const Span &s, uint64_t row0, uint64_t stride,
+                                           uint64_t nrows, unsigned lane, const Xpose &xk,
+                                           uint32_t cnt[4]) {
+  if (nrows == 0) return;
+  const uint64_t R = span_rows(s);
+  const uint64_t gstride = stride * 32u;          // granules between consecutive rows
+  uint64_t g = row0 * 32u + lane;                 // this lane's granule in the current row
+
+  if (nrows <= 3) {
+    // Short sequence (Section 4.6): too few vectors for a CSA network to pay;
+    // count every vector directly.
+    for (uint64_t i = 0; i < nrows; i++, g += gstride) {
+      const V4 v = load_granule_masked<HINT>(s, g);
+      flush_plane<0>(cnt, v, xk);
+    }
+    return;
+  }
+
+  Planes p;
+  {
+    // Head (Section 4.1) and initial CSA_15 reduction (Section 4.2).  The
+    // masked loader zeroes bytes before the start and after the end.
+    V4 v[15];
+#pragma unroll
+    for (int i = 0; i < 15; i++)
+      v[i] = ((uint64_t)i < nrows) ? load_granule_masked<HINT>(s, g + (uint64_t)i * gstride)
+                                   : v4_zero();
+    csa15(p, v);
+  }
+  p.a16 = v4_zero();
+  uint64_t i = 15;
+  g += 15u * gstride;
+
+  // Main loop (Section 4, step 5): 16 vectors per CSA_16+4, a16 skimmed off
+  // and counted.  Groups whose rows are all interior (not the first row,
+  // not the last row of the span) load without masking.
+  const uint8_t *ptr = s.A + g * kGranule;
+  const uint64_t pstep = gstride * kGranule;
+  if (DEPTH == 32) {
+    for (; i + 32 <= nrows; i += 32, g += 32u * gstride, ptr += 32u * pstep) {
+      const uint64_t first_row = row0 + i * stride, last_row = row0 + (i + 31) * stride;
+      const bool interior = first_row >= 1 && last_row + 1 < R;
+      V4 x, y;
+      {
+        V4 v[16];
+        if (interior) {
+#pragma unroll
+          for (int k = 0; k < 16; k++) v[k] = ldg_granule<HINT>(ptr + (uint64_t)k * pstep);
+        } else {
+#pragma unroll
+          for (int k = 0; k < 16; k++) v[k] = load_granule_masked<HINT>(s, g + (uint64_t)k * gstride);
+        }
+        x = csa16(p, v);
+      }
+      {
+        V4 v[16];
+        if (interior) {
+#pragma unroll
+          for (int k = 0; k < 16; k++) v[k] = ldg_granule<HINT>(ptr + (uint64_t)(16 + k) * pstep);
+        } else {
+#pragma unroll
+          for (int k = 0; k < 16; k++)
+            v[k] = load_granule_masked<HINT>(s, g + (uint64_t)(16 + k) * gstride);
+        }
+        y = csa16(p, v);
+      }
+      V4 a32;
+      fa(p.a16, a32, p.a16, x, y);
+      flush_plane<5>(cnt, a32, xk);
+    }
+  }
+  for (; i < nrows; i += 16, g += 16u * gstride, ptr += 16u * pstep) {
+    const uint64_t first_row = row0 + i * stride;
+    const bool full = i + 16 <= nrows;
+    const bool interior = full && first_row >= 1 && row0 + (i + 15) * stride + 1 < R;
+    V4 v[16];
+    if (interior) {
+#pragma unroll
+      for (int k = 0; k < 16; k++) v[k] = ldg_granule<HINT>(ptr + (uint64_t)k * pstep);
+    } else {
+      // Tail (Section 4.6): rows past the sequence and bytes past the end are zero.
+#pragma unroll
+      for (int k = 0; k < 16; k++)
+        v[k] = (i + (uint64_t)k < nrows) ? load_granule_masked<HINT>(s, g + (uint64_t)k * gstride)
+                                         : v4_zero();
+    }
+    const V4 a16 = csa16(p, v);
+    if (DEPTH == 32) {
+      V4 a32;
+      ha(p.a16, a32, p.a16, a16);
+      flush_plane<5>(cnt, a32, xk);
+    } else {
+      flush_plane<4>(cnt, a16, xk);
+    }
+  }
+
+  // Final accumulation (Section 4.5): the carried planes with weights 8, 4, 2, 1.
+  if (DEPTH == 32) flush_plane<4>(cnt, p.a16, xk);
+  flush_plane<3>(cnt, p.a8, xk);
+  flush_plane<2>(cnt, p.a4, xk);
+  flush_plane<1>(cnt, p.a2, xk);
+  flush_plane<0>(cnt, p.a1, xk);
+}
+
+// ---------------------------------------------------------------------------
+// Fold (f_w, Section 4.4) with the phase rotation for unaligned starts: the
+// lane's counts of granule positions 32r + lane become counter
+// (32r + lane - rot) mod w.  For w <= 32 all four lanes r share one counter,
+// and lanes l, l + w, l + 2w, ... are summed with shuffles first.
+// emit(j, value) is called by the lanes that own a finished counter.
+// ---------------------------------------------------------------------------
+template <typename Emit>
+__device__ __forceinline__ void fold_counts(const uint32_t cnt[4], int w, uint32_t rot,
+                                            unsigned lane, Emit emit) {
+  if (w == 64) {
+    const unsigned long long v0 = (unsigned long long)cnt[0] + cnt[2];
+    const unsigned long long v1 = (unsigned long long)cnt[1] + cnt[3];
+    emit((lane - rot) & 63u, v0);
+    emit((lane + 32u - rot) & 63u, v1);
+  } else {
+    unsigned long long v = (unsigned long long)cnt[0] + cnt[1] + cnt[2] + cnt[3];
+    for (int off = 16; off >= w; off >>= 1) v += __shfl_xor_sync(kFull, v, off);
+    if ((int)lane < w) emit((lane - rot) & (uint32_t)(w - 1), v);
+  }
+}
+
+}  // namespace pospop

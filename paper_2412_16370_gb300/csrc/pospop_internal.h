@@ -1,0 +1,85 @@
+// pospop_internal.h -- declarations shared by the library's translation
+// units (kernel tables, launch parameters).  Not part of the public ABI.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace pospop {
+
+// One array (or a piece of one) in 16-byte granule coordinates; see
+// pospop_device.cuh for the layout.
+struct SpanH {
+  const uint8_t *A;
+  uint64_t G;
+  uint32_t head;
+  uint32_t tail;
+};
+
+struct StreamParams {
+  SpanH s;
+  uint64_t row_begin;           // rows [row_begin, row_end) of the span in this launch
+  uint64_t row_end;
+  unsigned long long *counts;   // w counters (device)
+  int w;
+  uint32_t rot;                 // (8 * head) mod w
+};
+
+struct BatchParams {
+  const uint8_t *base;
+  const uint64_t *offsets;      // m + 1 byte offsets (device)
+  uint64_t m;
+  unsigned long long *counts;   // m * w counters (device)
+  int w;
+  const uint64_t *item_start;   // m + 1 exclusive prefix sums of work items (workspace)
+  unsigned long long *next;     // dynamic work counter (workspace)
+  const int *status;            // planning status (workspace)
+  uint32_t item_rows;           // rows of 512 B per work item
+  uint32_t grab;                // work items taken per atomic
+};
+
+struct PlanParams {
+  const uint64_t *offsets;
+  uint64_t m;
+  uint64_t base_addr;           // (uint64_t)base, for granule alignment
+  uint64_t *item_start;         // m + 1
+  uint64_t *block_sum;          // one per planning block
+  unsigned long long *next;
+  int *status;
+  uint32_t item_rows;
+  uint32_t nblocks;
+};
+
+struct RooflineParams {
+  const uint8_t *A;             // 16-byte aligned
+  uint64_t G;                   // whole granules
+  unsigned long long *sum;
+};
+
+// Kernel variant descriptor.  `fn` is the __global__ function to launch
+// with a single by-value parameter struct.
+struct Variant {
+  const void *fn;
+  int bs;       // threads per block
+  int minb;     // __launch_bounds__ min blocks per SM
+  int depth;    // 16 or 32 vectors per flush
+  int hint;     // load variant
+};
+
+constexpr int kPlanThreads = 1024;
+constexpr int kPlanPerThread = 4;
+constexpr int kPlanChunk = kPlanThreads * kPlanPerThread;
+
+int stream_variant_count();
+const Variant &stream_variant(int i);
+int batch_variant_count();
+const Variant &batch_variant(int i);
+int roofline_variant_count();
+const Variant &roofline_variant(int i);
+
+const void *plan_items_fn();
+const void *plan_scan_fn();
+const void *plan_apply_fn();
+
+}  // namespace pospop

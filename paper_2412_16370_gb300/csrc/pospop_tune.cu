@@ -1,0 +1,207 @@
+// pospop_tune.cu -- the autotuner behind pospopcnt_autotune: times every
+// launch candidate of the single-array kernel per size class, of the
+// batched kernel on a ragged batch, and of the roofline read kernel, and
+// installs the fastest of each.  Timing is with CUDA events on the tuning
+// stream; counting kernels do not depend on the data values, so the scratch
+// buffer holds a fixed byte pattern.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <functional>
+#include <string>
+#include <vector>
+
+#include "pospopcnt.h"
+#include "pospop_runtime.h"
+
+namespace pospop {
+namespace {
+
+struct Timer {
+  cudaStream_t s = nullptr;
+  cudaEvent_t a = nullptr, b = nullptr;
+  bool ok = false;
+  Timer() {
+    ok = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) == cudaSuccess &&
+         cudaEventCreate(&a) == cudaSuccess && cudaEventCreate(&b) == cudaSuccess;
+  }
+  ~Timer() {
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+    if (s) cudaStreamDestroy(s);
+  }
+  // Mean milliseconds per call of fn (which enqueues on s); < 0 on error.
+  double time(const std::function<int()> &fn, double budget_ms = 15.0) {
+    if (fn() != POSPOP_OK || cudaStreamSynchronize(s) != cudaSuccess) return -1.0;
+    float ms = 0.f;
+    if (cudaEventRecord(a, s) != cudaSuccess || fn() != POSPOP_OK ||
+        cudaEventRecord(b, s) != cudaSuccess || cudaEventSynchronize(b) != cudaSuccess ||
+        cudaEventElapsedTime(&ms, a, b) != cudaSuccess)
+      return -1.0;
+    int reps = (int)std::min(200.0, std::max(3.0, budget_ms / std::max(ms, 1e-3f)));
+    if (cudaEventRecord(a, s) != cudaSuccess) return -1.0;
+    for (int i = 0; i < reps; i++)
+      if (fn() != POSPOP_OK) return -1.0;
+    if (cudaEventRecord(b, s) != cudaSuccess || cudaEventSynchronize(b) != cudaSuccess ||
+        cudaEventElapsedTime(&ms, a, b) != cudaSuccess)
+      return -1.0;
+    return (double)ms / reps;
+  }
+};
+
+// xorshift64* for the tuning batch's sizes (tuning input only).
+struct Rng {
+  uint64_t x;
+  uint64_t next() {
+    x ^= x >> 12;
+    x ^= x << 25;
+    x ^= x >> 27;
+    return x * 0x2545F4914F6CDD1Dull;
+  }
+  double uniform() { return (double)(next() >> 11) * (1.0 / 9007199254740992.0); }
+};
+
+}  // namespace
+}  // namespace pospop
+
+using namespace pospop;
+
+extern "C" int pospopcnt_autotune(size_t max_bytes, const char *path) {
+  int rc = POSPOP_OK;
+  DevCtx *c = current_ctx(&rc);
+  if (!c) return rc;
+  if (max_bytes == 0) max_bytes = size_t(1) << 30;
+  if (max_bytes < (size_t(1) << 24)) max_bytes = size_t(1) << 24;
+
+  uint8_t *buf = nullptr;
+  unsigned long long *counts = nullptr;
+  uint64_t *doff = nullptr;
+  if (cudaMalloc(&buf, max_bytes + 64) != cudaSuccess ||
+      cudaMalloc(&counts, 20000 * 64 * sizeof(unsigned long long)) != cudaSuccess) {
+    cudaGetLastError();
+    if (buf) cudaFree(buf);
+    return POSPOP_ENOMEM;
+  }
+  cudaMemset(buf, 0xA5, max_bytes + 64);
+  cudaMemset(counts, 0, 20000 * 64 * sizeof(unsigned long long));
+  Timer tm;
+  if (!tm.ok) {
+    cudaGetLastError();
+    cudaFree(buf);
+    cudaFree(counts);
+    return POSPOP_ECUDA;
+  }
+
+  TuneTable best;
+  {
+    std::lock_guard<std::mutex> g(c->mu);
+    best = c->tune;
+  }
+  TuneTable cand = best;
+
+  // --- single-array kernel, per size class -----------------------------------
+  const size_t rep_bytes[kClasses] = {size_t(16) << 10, size_t(512) << 10, size_t(16) << 20,
+                                      size_t(512) << 20, max_bytes};
+  const uint32_t minrows_set[] = {1, 2, 4, 8, 16, 32, 64, 128};
+  for (int cls = 0; cls < kClasses; cls++) {
+    const size_t nbytes = std::min(rep_bytes[cls], max_bytes);
+    const uint64_t rows = (nbytes / 16 + 31) / 32;
+    if (size_class(rows) != cls) {   // scratch too small for this class: inherit
+      if (cls > 0) best.stream[cls] = best.stream[cls - 1];
+      continue;
+    }
+    double best_ms = 1e30;
+    for (int v = 0; v < stream_variant_count(); v++) {
+      for (int cps = 1; cps <= std::min(c->occ_stream[v], 4); cps++) {
+        unsigned last_grid = 0;
+        for (uint32_t mr : minrows_set) {
+          cand = best;
+          cand.stream[cls] = StreamTune{v, cps, mr};
+          const StreamPlan pl = plan_stream(*c, cand, rows);
+          if (pl.grid == last_grid) continue;   // same launch as the previous min_rows
+          last_grid = pl.grid;
+          const double ms = tm.time([&] {
+            return launch_stream_with(*c, cand, 16, counts, buf, nbytes, tm.s);
+          });
+          if (ms > 0 && ms < best_ms) {
+            best_ms = ms;
+            best.stream[cls] = cand.stream[cls];
+          }
+        }
+      }
+    }
+  }
+
+  // --- batched kernel on a ragged batch (log-uniform sizes, 1 B .. 4 MiB) ----
+  {
+    Rng rng{0x9E3779B97F4A7C15ull};
+    std::vector<uint64_t> off(1, 0);
+    const double lo = 0.0, hi = std::log(4.0 * 1048576.0 + 1.0);
+    while (off.size() <= 20000) {
+      const uint64_t sz = (uint64_t)std::floor(std::exp(lo + rng.uniform() * (hi - lo)));
+      if (off.back() + sz > max_bytes) break;
+      off.push_back(off.back() + sz);
+    }
+    const size_t m = off.size() - 1;
+    if (m > 0 && cudaMalloc(&doff, off.size() * sizeof(uint64_t)) == cudaSuccess &&
+        cudaMemcpy(doff, off.data(), off.size() * sizeof(uint64_t), cudaMemcpyHostToDevice) ==
+            cudaSuccess) {
+      double best_ms = 1e30;
+      const uint32_t item_rows_set[] = {63, 127, 255, 511, 1023, 2047};
+      const uint32_t grab_set[] = {1, 2, 4};
+      for (int v = 0; v < batch_variant_count(); v++)
+        for (int cps = 1; cps <= std::min(c->occ_batch[v], 4); cps++)
+          for (uint32_t ir : item_rows_set)
+            for (uint32_t gr : grab_set) {
+              cand = best;
+              cand.batch = BatchTune{v, cps, ir, gr};
+              const double ms = tm.time([&] {
+                return launch_batch_with(*c, cand, 8, counts, buf + 3, doff, m, tm.s);
+              });
+              if (ms > 0 && ms < best_ms) {
+                best_ms = ms;
+                best.batch = cand.batch;
+              }
+            }
+    }
+    cudaGetLastError();
+  }
+
+  // --- roofline read kernel -------------------------------------------------
+  {
+    double best_ms = 1e30;
+    for (int v = 0; v < roofline_variant_count(); v++)
+      for (int cps = 1; cps <= std::min(c->occ_roof[v], 8); cps++) {
+        const RoofTune rt{v, cps};
+        const double ms = tm.time([&] {
+          return launch_roofline_with(*c, rt, buf, max_bytes, counts, tm.s);
+        });
+        if (ms > 0 && ms < best_ms) {
+          best_ms = ms;
+          best.roof = rt;
+        }
+      }
+  }
+
+  cudaStreamSynchronize(tm.s);
+  if (doff) cudaFree(doff);
+  cudaFree(counts);
+  cudaFree(buf);
+  cudaGetLastError();
+
+  best.source = "autotuned";
+  std::string text;
+  {
+    std::lock_guard<std::mutex> g(c->mu);
+    c->tune = best;
+    text = format_tune(*c, best);
+  }
+  if (path) {
+    FILE *f = fopen(path, "wb");
+    if (!f) return POSPOP_EINVAL;
+    fwrite(text.data(), 1, text.size(), f);
+    fclose(f);
+  }
+  return POSPOP_OK;
+}

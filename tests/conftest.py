@@ -8,3 +8,25 @@ if ROOT not in sys.path:
 
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (runs the sm_103a kernels)")
+
+
+import pytest  # noqa: E402
+
+
+@pytest.fixture(scope="session")
+def orc():
+    import oracle
+    return oracle.load()
+
+
+@pytest.fixture(scope="session")
+def gpu():
+    """cuda:0 with the package's libraries built and set up (GPU tests only)."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("GPU test run without a CUDA device")
+    from paper_2412_16370_gb300 import build, binding
+    build.build()
+    torch.cuda.set_device(0)
+    binding.init(0)
+    return torch.device("cuda:0")

@@ -1,0 +1,190 @@
+"""Batched pospopcnt (CSR offsets, one persistent launch) vs the CPU oracle.
+
+The ragged one-hot workload: uint8 arrays, each byte with exactly one of 8
+bits set (Zipf(1.1) categories), sizes log-uniform on 1 B .. 4 MiB,
+concatenated back to back (so starts are unaligned).  A 20000-array subset is
+checked exactly against the oracle for every array; the full 200000-array
+batch (about 55 GB) is checked on every array through the one-hot property
+(counts of an array add up to its length) and exactly against the oracle on
+sampled arrays.  Also: every kernel variant and work-item size, zero-length
+arrays, decreasing offsets, and CUDA-graph replay.
+"""
+import numpy as np
+import pytest
+import torch
+
+from paper_2412_16370_gb300 import binding as pp
+from paper_2412_16370_gb300 import synth, synth_device
+
+from _gpu import WORD_W, counts_np, oracle_batch_parallel
+
+pytestmark = pytest.mark.gpu
+
+ONE_HOT_SEED = 4
+SIZE_SEED = 3
+
+
+def _one_hot_batch(dev, m):
+    sizes = synth.log_uniform_sizes(m, 1, 4 << 20, seed=SIZE_SEED)
+    offs = synth.csr_offsets(sizes)
+    total = int(offs[-1])
+    base = torch.empty(total + 64, dtype=torch.uint8, device=dev)
+    synth_device.one_hot_(base, ONE_HOT_SEED, nbytes=total)
+    offs_d = torch.from_numpy(offs.view(np.int64)).to(dev)
+    return sizes, offs, base, offs_d
+
+
+@pytest.fixture
+def tune_override(gpu, tmp_path):
+    saved = tmp_path / "saved_tune.txt"
+    saved.write_text(pp.pospopcnt_tune_describe())
+
+    def install(text):
+        f = tmp_path / "tune.txt"
+        f.write_text(text)
+        pp.pospopcnt_tune_load(str(f))
+
+    yield install
+    pp.pospopcnt_tune_load(str(saved))
+
+
+def test_subset_every_array_exact(gpu, orc):
+    m = 20000
+    sizes, offs, base, offs_d = _one_hot_batch(gpu, m)
+    host = base[:int(offs[-1])].cpu().numpy()
+    # the device generator made exactly the numpy recipe's bytes (sampled windows)
+    for s0 in (0, 12345, int(offs[-1]) - 4096):
+        assert np.array_equal(host[s0:s0 + 4096], synth.one_hot_bytes(4096, ONE_HOT_SEED, start=s0))
+    for w in WORD_W:
+        counts = torch.zeros((m, w), dtype=torch.int64, device=gpu)
+        pp.pospopcnt_batch(w, counts, base, offs_d, m)
+        assert pp.pospopcnt_batch_status() == pp.POSPOP_OK
+        got = counts_np(counts)
+        exp = oracle_batch_parallel(orc, w, host, offs)
+        bad = np.nonzero((got != exp).any(axis=1))[0]
+        assert bad.size == 0, (w, bad[:5].tolist())
+        if w == 8:
+            assert np.array_equal(got.sum(axis=1), sizes.astype(np.uint64))
+
+
+def test_full_batch_one_hot_and_sampled(gpu, orc):
+    m = 200000
+    sizes, offs, base, offs_d = _one_hot_batch(gpu, m)
+    counts = torch.zeros((m, 8), dtype=torch.int64, device=gpu)
+    pp.pospopcnt_batch(8, counts, base, offs_d, m)
+    assert pp.pospopcnt_batch_status() == pp.POSPOP_OK
+    got = counts_np(counts)
+    # every byte has exactly one bit set: an array's counts add up to its length
+    assert np.array_equal(got.sum(axis=1), sizes.astype(np.uint64))
+    rng = np.random.default_rng(0)
+    sample = set(rng.choice(m, 1500, replace=False).tolist())
+    sample.update(np.argsort(sizes)[-40:].tolist())
+    sample.update([0, 1, m - 2, m - 1])
+    for a in sorted(sample):
+        lo, hi = int(offs[a]), int(offs[a + 1])
+        seg = base[lo:hi].cpu().numpy()
+        assert np.array_equal(got[a], orc.bytes(8, seg)), a
+    # w = 16 over the same batch: folding pairs of bytes
+    c16 = torch.zeros((m, 16), dtype=torch.int64, device=gpu)
+    pp.pospopcnt_batch(16, c16, base, offs_d, m)
+    g16 = counts_np(c16)
+    assert np.array_equal(g16.sum(axis=1), sizes.astype(np.uint64))
+    for a in sorted(sample)[:300]:
+        seg = base[int(offs[a]):int(offs[a + 1])].cpu().numpy()
+        assert np.array_equal(g16[a], orc.bytes(16, seg)), a
+
+
+def test_every_variant_and_item_size(gpu, orc, tune_override):
+    sizes = synth.log_uniform_sizes(700, 1, 300000, seed=77)
+    sizes[::37] = 0   # zero-length arrays in between
+    offs = synth.csr_offsets(sizes)
+    host = synth.random_bytes(int(offs[-1]), seed=78)
+    base = torch.empty(host.size + 32, dtype=torch.uint8, device=gpu)[5:5 + host.size]
+    base.copy_(torch.from_numpy(host))
+    offs_d = torch.from_numpy(offs.view(np.int64)).to(gpu)
+    exp = {w: orc.batch(w, host, offs) for w in WORD_W}
+    for bs, minb in ((256, 2), (512, 1), (128, 4)):
+        for depth in (16, 32):
+            for hint in (0, 1):
+                for item_rows, grab in ((1, 1), (3, 2), (15, 1), (31, 3), (47, 1), (511, 4)):
+                    tune_override(f"batch {bs} {minb} {depth} {hint} 1 {item_rows} {grab}\n")
+                    for w in WORD_W:
+                        c = torch.zeros((len(sizes), w), dtype=torch.int64, device=gpu)
+                        pp.pospopcnt_batch(w, c, base, offs_d)
+                        assert pp.pospopcnt_batch_status() == pp.POSPOP_OK
+                        assert np.array_equal(counts_np(c), exp[w]), (bs, depth, hint, item_rows, w)
+
+
+def test_short_sweep_back_to_back(gpu, orc):
+    """The short/unaligned sweep's arrays laid back to back in one batch."""
+    for w in WORD_W:
+        lens = synth.short_sweep_lengths()
+        arrays = [synth.random_bytes(n, synth.case_seed(w, n, off))
+                  for n in lens for off in (0, 7, 15)]
+        sizes = np.array([a.size for a in arrays], dtype=np.int64)
+        offs = synth.csr_offsets(sizes)
+        host = np.concatenate(arrays)
+        base = torch.from_numpy(host).to(gpu)
+        c = torch.zeros((len(arrays), w), dtype=torch.int64, device=gpu)
+        pp.pospopcnt_batch(w, c, base, torch.from_numpy(offs.view(np.int64)).to(gpu))
+        assert np.array_equal(counts_np(c), orc.batch(w, host, offs)), w
+
+
+def test_sub_byte_widths(gpu, orc):
+    sizes = synth.log_uniform_sizes(500, 1, 100000, seed=5)
+    offs = synth.csr_offsets(sizes)
+    host = synth.random_bytes(int(offs[-1]), seed=6)
+    base = torch.from_numpy(host).to(gpu)
+    offs_d = torch.from_numpy(offs.view(np.int64)).to(gpu)
+    for w in (1, 2, 4):
+        c = torch.zeros((len(sizes), w), dtype=torch.int64, device=gpu)
+        pp.pospopcnt_batch(w, c, base, offs_d)
+        assert np.array_equal(counts_np(c), orc.batch(w, host, offs)), w
+
+
+def test_decreasing_offsets_rejected(gpu):
+    offs = np.array([0, 10, 30, 20, 40], dtype=np.int64)
+    base = torch.ones(64, dtype=torch.uint8, device=gpu)
+    c = torch.full((4, 8), 7, dtype=torch.int64, device=gpu)
+    pp.pospopcnt_batch(8, c, base, torch.from_numpy(offs).to(gpu))
+    assert pp.pospopcnt_batch_status() == pp.POSPOP_EINVAL
+    assert (c == 7).all()
+    # the status is cleared once read, and a good batch afterwards works
+    offs[3] = 30
+    pp.pospopcnt_batch(8, c, base, torch.from_numpy(offs).to(gpu))
+    assert pp.pospopcnt_batch_status() == pp.POSPOP_OK
+    assert c.sum().item() == 4 * 8 * 7 + 40
+
+
+def test_graph_replay_matches_direct(gpu, orc):
+    sizes = synth.log_uniform_sizes(3000, 1, 1 << 20, seed=12)
+    offs = synth.csr_offsets(sizes)
+    host = synth.random_bytes(int(offs[-1]), seed=13)
+    base = torch.from_numpy(host).to(gpu)
+    offs_d = torch.from_numpy(offs.view(np.int64)).to(gpu)
+    exp = orc.batch(32, host, offs)
+    s = torch.cuda.Stream()
+    c = torch.zeros((len(sizes), 32), dtype=torch.int64, device=gpu)
+    g = pp.pospopcnt_batch_graph_create(32, c, base, offs_d, stream=s)
+    try:
+        s.synchronize()
+        c.zero_()
+        torch.cuda.synchronize()
+        for _ in range(3):
+            pp.pospopcnt_graph_launch(g, s)
+        s.synchronize()
+        assert np.array_equal(counts_np(c), 3 * exp)
+    finally:
+        pp.pospopcnt_graph_destroy(g)
+
+
+def test_argument_errors(gpu):
+    L = pp.lib()
+    c = torch.zeros(64, dtype=torch.int64, device=gpu)
+    base = torch.zeros(64, dtype=torch.uint8, device=gpu)
+    offs = torch.zeros(3, dtype=torch.int64, device=gpu)
+    assert L.pospopcnt_batch(8, c.data_ptr(), base.data_ptr(), offs.data_ptr(), 0, None) == 0
+    assert L.pospopcnt_batch(8, None, base.data_ptr(), offs.data_ptr(), 2, None) == pp.POSPOP_EINVAL
+    assert L.pospopcnt_batch(9, c.data_ptr(), base.data_ptr(), offs.data_ptr(), 2, None) == pp.POSPOP_EINVAL
+    hoffs = np.zeros(3, dtype=np.uint64)
+    assert L.pospopcnt_batch(8, c.data_ptr(), base.data_ptr(), hoffs.ctypes.data, 2, None) == pp.POSPOP_EPTR
