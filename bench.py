@@ -284,13 +284,19 @@ def run_ours(args):
     read_gbs = nbytes / (r0.elapsed_time(r1) / reps / 1e3) / 1e9
 
     extra = {}
+    sections = set(args.sections.split(",")) if args.sections else None
+    want = (lambda k: sections is None or k in sections)
     if not args.quick:
-        extra["e2e"] = _e2e(args, pp, data, nbytes, world, dist)
+        if want("e2e"):
+            extra["e2e"] = _e2e(args, pp, data, nbytes, world, dist)
         if rank == 0:
             for key, fn in (("batched", lambda: _batched(pp, synth, synth_device, dev, stream,
                                                          achieved, hbm_peak)),
                             ("short", lambda: _short(pp, synth, dev, stream)),
+                            ("serving", lambda: _serving(pp, synth, data, nbytes, achieved, dev)),
                             ("cpu_baseline", lambda: _cpu_baseline(data))):
+                if not want(key):
+                    continue
                 try:
                     extra[key] = fn()
                 except Exception as e:  # report, keep the line
@@ -459,6 +465,51 @@ def _short(pp, synth, dev, stream, n=2000):
             "graph_us_per_call": round(graph_us, 2)}
 
 
+def _serving(pp, synth, pool, pool_bytes, large_gbs, dev, loads=(0.3, 0.6, 0.9),
+             duration_s=0.3, budget=32 << 30):
+    """Poisson request streams at fractions of the large-array rate, served by
+    the continuous-batching loop over the resident 8 GiB pool."""
+    import math
+    import torch
+    lo, hi = 64, 256 << 20
+    mean = (hi - lo) / math.log((hi + 1) / lo)      # mean of the log-uniform size
+    out = {"workload": "Poisson arrivals; w uniform in {8,16,32,64}; sizes log-uniform "
+                       "64 B..256 MiB at uniform offsets of the resident 8 GiB array",
+           "mem_budget_bytes": budget, "max_inflight": 4096, "batch_streams": 4, "loads": []}
+    for k, load in enumerate(loads):
+        rate = load * large_gbs * 1e9 / mean
+        n = max(100, int(rate * duration_s))
+        r = synth.poisson_requests(n, rate, seed=500 + k, lo=lo, hi=hi, pool_bytes=pool_bytes)
+        arrival = np.round(r["arrival_s"] * 1e9).astype(np.int64)
+        ptrs = (pool.data_ptr() + r["offset"]).astype(np.uint64)
+        results = np.zeros((n, 64), dtype=np.uint64)
+        srv = pp.pospop_server_create(budget, 4096, 4)
+        try:
+            recs = pp.pospop_server_run_trace(srv, arrival, r["w"], ptrs, r["nbytes"], results)
+        finally:
+            pp.pospop_server_destroy(srv)
+        lat_us = (recs["t_done_ns"] - recs["t_submit_ns"]) / 1e3
+        span_s = (int(recs["t_done_ns"].max()) - int(recs["t_submit_ns"].min())) / 1e9
+        total = int(r["nbytes"].sum())
+        gbs = total / span_s / 1e9
+        # each result equals the request's own single-array count (sampled)
+        idx = np.linspace(0, n - 1, min(n, 300)).astype(np.int64)
+        solo = torch.zeros((len(idx), 64), dtype=torch.int64, device=dev)
+        for j, i in enumerate(idx):
+            pp.pospopcnt_async(int(r["w"][i]), solo[j], int(ptrs[i]), int(r["nbytes"][i]))
+        torch.cuda.synchronize()
+        solo = solo.cpu().numpy().view(np.uint64)
+        same = all(np.array_equal(results[i, :r["w"][i]], solo[j, :r["w"][i]])
+                   for j, i in enumerate(idx))
+        out["loads"].append({
+            "offered_load": load, "offered_GBps": round(rate * mean / 1e9, 1), "requests": n,
+            "bytes": total, "GBps": round(gbs, 1), "frac_of_large_array": round(gbs / large_gbs, 4),
+            "p50_us": round(float(np.percentile(lat_us, 50)), 1),
+            "p99_us": round(float(np.percentile(lat_us, 99)), 1),
+            "status_ok": bool((recs["status"] == 0).all()), "results_match_solo": bool(same)})
+    return out
+
+
 def run_reference(args):
     """The CPU oracle (the reference arm of this tier) on the same workload."""
     world, rank, _ = _dist()
@@ -503,7 +554,10 @@ def main():
     ap.add_argument("--gib", type=int, default=8, help="array size in GiB (8 = the workload)")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--ref-sample-mib", type=int, default=16)
-    ap.add_argument("--quick", action="store_true", help="skip e2e, batched, short, cpu baseline")
+    ap.add_argument("--quick", action="store_true",
+                    help="skip e2e, batched, short, serving and the cpu baseline")
+    ap.add_argument("--sections", default="",
+                    help="comma list of extra sections to run (e2e,batched,short,serving,cpu_baseline)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")

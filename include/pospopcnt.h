@@ -161,6 +161,71 @@ int pospopcnt_batch_graph_create(int w, uint64_t *counts, const void *base,
 int pospopcnt_graph_launch(void *graph, void *stream);
 int pospopcnt_graph_destroy(void *graph);
 
+/*
+ * ---------------------------------------------------------------------------
+ * Serving: continuous batching of pospopcnt requests.  The paper has no
+ * serving layer; each request is the byte-length count above (Fig. 2 /
+ * Section 1) of device-resident input, and the batching is this library's.
+ *
+ * A request is admitted when the input bytes of all admitted, unfinished
+ * requests plus its own fit `mem_budget` and fewer than `max_inflight` are
+ * admitted; admitted requests are gathered into one launch as soon as one of
+ * the server's `max_batches` streams is free, so requests arriving while
+ * others run are counted in the next batch while earlier batches are still
+ * on the device.  Each result is the same as the request's single-array
+ * count.  Waits are bounded by the caller's timeouts.
+ * ---------------------------------------------------------------------------
+ */
+typedef struct pospop_server pospop_server;
+
+typedef struct pospop_completion {
+  uint64_t id;           /* from pospop_server_submit */
+  int32_t status;        /* POSPOP_OK, or the error that ended the request */
+  int32_t w;
+  uint64_t nbytes;
+  int64_t t_submit_ns;   /* steady-clock timestamps (nanoseconds) */
+  int64_t t_admit_ns;
+  int64_t t_launch_ns;
+  int64_t t_done_ns;
+} pospop_completion;
+
+/* Start a server on the current device (its own streams, pinned staging
+ * and device counters; a host thread runs the loop).  mem_budget > 0 bytes,
+ * 1 <= max_inflight <= 2^20, 1 <= max_batches <= 64. */
+int pospop_server_create(size_t mem_budget, int max_inflight, int max_batches,
+                         pospop_server **out);
+
+/* Queue one request: count the nbytes device-addressable bytes at `bytes`
+ * with width w (1, 2, 4, 8, 16, 32, 64).  When it completes, result[0..w-1]
+ * (host memory, valid until then; may be NULL) is OVERWRITTEN with the
+ * counts.  Never blocks.  nbytes > mem_budget returns POSPOP_ERANGE; a plain
+ * host pointer returns POSPOP_EPTR.  *id (may be NULL) receives the id. */
+int pospop_server_submit(pospop_server *s, int w, const void *bytes, size_t nbytes,
+                         uint64_t *result, uint64_t *id);
+
+/* Move up to max finished requests' records to out, waiting up to
+ * timeout_ms for the first.  Returns how many (>= 1) or POSPOP_ETIMEDOUT. */
+int pospop_server_poll(pospop_server *s, pospop_completion *out, int max, int timeout_ms);
+
+/* Wait up to timeout_ms until every submitted request has finished. */
+int pospop_server_drain(pospop_server *s, int timeout_ms);
+
+/* stats: submitted, finished, waiting for admission, admitted and
+ * unfinished, their input bytes, last loop error. */
+int pospop_server_stats(pospop_server *s, uint64_t stats[6]);
+
+/* Load generator: submit request i at arrival_ns[i] nanoseconds after the
+ * call starts (w[i], device address ptrs[i], nbytes[i], counts into
+ * results + 64*i), then collect all n completion records into out[i] (the
+ * server's finished queue must be empty and this the only submitter).
+ * Returns POSPOP_ETIMEDOUT if they do not all finish within timeout_ms. */
+int pospop_server_run_trace(pospop_server *s, size_t n, const int64_t *arrival_ns,
+                            const int32_t *w, const uint64_t *ptrs, const uint64_t *nbytes,
+                            uint64_t *results, pospop_completion *out, int timeout_ms);
+
+/* Finish every submitted request, stop the loop and free the server. */
+int pospop_server_destroy(pospop_server *s);
+
 /* Number of library kernel launches enqueued by this process so far. */
 uint64_t pospopcnt_launch_count(void);
 

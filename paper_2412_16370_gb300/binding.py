@@ -61,7 +61,27 @@ _SIGNATURES = {
     "pospopcnt_graph_launch": ([_vp, _vp], _int),
     "pospopcnt_graph_destroy": ([_vp], _int),
     "pospopcnt_launch_count": ([], ctypes.c_uint64),
+    "pospop_server_create": ([_sz, _int, _int, ctypes.POINTER(_vp)], _int),
+    "pospop_server_submit": ([_vp, _int, _vp, _sz, _vp, ctypes.POINTER(ctypes.c_uint64)], _int),
+    "pospop_server_poll": ([_vp, _vp, _int, _int], _int),
+    "pospop_server_drain": ([_vp, _int], _int),
+    "pospop_server_stats": ([_vp, ctypes.POINTER(ctypes.c_uint64)], _int),
+    "pospop_server_run_trace": ([_vp, _sz, _vp, _vp, _vp, _vp, _vp, _vp, _int], _int),
+    "pospop_server_destroy": ([_vp], _int),
 }
+
+
+class Completion(ctypes.Structure):
+    """pospop_completion."""
+    _fields_ = [("id", ctypes.c_uint64), ("status", ctypes.c_int32), ("w", ctypes.c_int32),
+                ("nbytes", ctypes.c_uint64), ("t_submit_ns", ctypes.c_int64),
+                ("t_admit_ns", ctypes.c_int64), ("t_launch_ns", ctypes.c_int64),
+                ("t_done_ns", ctypes.c_int64)]
+
+
+COMPLETION_DTYPE = [("id", "<u8"), ("status", "<i4"), ("w", "<i4"), ("nbytes", "<u8"),
+                    ("t_submit_ns", "<i8"), ("t_admit_ns", "<i8"), ("t_launch_ns", "<i8"),
+                    ("t_done_ns", "<i8")]
 
 
 def lib():
@@ -229,3 +249,65 @@ def pospopcnt_graph_destroy(graph: int):
 
 def pospopcnt_launch_count() -> int:
     return int(lib().pospopcnt_launch_count())
+
+
+# --- serving -----------------------------------------------------------------
+def pospop_server_create(mem_budget: int, max_inflight: int = 4096, max_batches: int = 4) -> int:
+    h = _vp()
+    _check(lib().pospop_server_create(mem_budget, max_inflight, max_batches, ctypes.byref(h)))
+    return h.value
+
+
+def pospop_server_submit(server: int, w: int, data, nbytes=None, result=None) -> int:
+    if nbytes is None:
+        nbytes = _nbytes(data)
+    rid = ctypes.c_uint64()
+    _check(lib().pospop_server_submit(server, w, _ptr(data), nbytes, _ptr(result),
+                                      ctypes.byref(rid)))
+    return rid.value
+
+
+def pospop_server_poll(server: int, max_records: int = 1024, timeout_ms: int = 1000) -> list:
+    """Finished requests' records (an empty list on timeout)."""
+    buf = (Completion * max_records)()
+    n = lib().pospop_server_poll(server, buf, max_records, timeout_ms)
+    if n == POSPOP_ETIMEDOUT:
+        return []
+    _check(n if n < 0 else 0)
+    return [buf[i] for i in range(n)]
+
+
+def pospop_server_drain(server: int, timeout_ms: int = 60000) -> int:
+    """POSPOP_OK, or POSPOP_ETIMEDOUT (does not raise on a timeout)."""
+    rc = lib().pospop_server_drain(server, timeout_ms)
+    if rc not in (POSPOP_OK, POSPOP_ETIMEDOUT):
+        _check(rc)
+    return rc
+
+
+def pospop_server_stats(server: int) -> dict:
+    out = (ctypes.c_uint64 * 6)()
+    _check(lib().pospop_server_stats(server, out))
+    keys = ("submitted", "finished", "waiting", "inflight", "inflight_bytes", "loop_error")
+    vals = list(out)
+    vals[5] = ctypes.c_int64(vals[5]).value
+    return dict(zip(keys, vals))
+
+
+def pospop_server_run_trace(server: int, arrival_ns, w, ptrs, nbytes, results, timeout_ms=600000):
+    """Replay a request trace natively; returns the completion records (numpy structured array)."""
+    import numpy as np
+    n = len(arrival_ns)
+    arrival_ns = np.ascontiguousarray(arrival_ns, dtype=np.int64)
+    w = np.ascontiguousarray(w, dtype=np.int32)
+    ptrs = np.ascontiguousarray(ptrs, dtype=np.uint64)
+    nbytes = np.ascontiguousarray(nbytes, dtype=np.uint64)
+    out = np.zeros(n, dtype=COMPLETION_DTYPE)
+    _check(lib().pospop_server_run_trace(server, n, arrival_ns.ctypes.data, w.ctypes.data,
+                                         ptrs.ctypes.data, nbytes.ctypes.data, _ptr(results),
+                                         out.ctypes.data, timeout_ms))
+    return out
+
+
+def pospop_server_destroy(server: int):
+    return _check(lib().pospop_server_destroy(server))

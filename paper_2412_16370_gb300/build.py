@@ -26,8 +26,8 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
                      "-I", INCLUDE, "-I", CSRC]
 
-LIB_SOURCES = ["pospop_stream.cu", "pospop_batch.cu", "pospop_api.cu", "pospop_tune.cu",
-               "pospop_serve.cu"]
+LIB_SOURCES = ["pospop_stream.cu", "pospop_batch.cu", "pospop_desc.cu", "pospop_api.cu",
+               "pospop_tune.cu", "pospop_serve.cu"]
 SYNTH_SOURCES = ["synth.cu"]
 
 

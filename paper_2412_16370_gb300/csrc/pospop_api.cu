@@ -493,6 +493,7 @@ int launch_batch_with(DevCtx &ctx, const TuneTable &t, int w, unsigned long long
     return POSPOP_ECUDA;
   }
   PlanParams pp;
+  pp.desc = nullptr;
   pp.offsets = offsets;
   pp.m = m;
   pp.base_addr = (uint64_t)base;
@@ -506,6 +507,7 @@ int launch_batch_with(DevCtx &ctx, const TuneTable &t, int w, unsigned long long
   if (rc != POSPOP_OK) return rc;
 
   BatchParams bp;
+  bp.desc = nullptr;
   bp.base = static_cast<const uint8_t *>(base);
   bp.offsets = offsets;
   bp.m = m;
@@ -516,6 +518,10 @@ int launch_batch_with(DevCtx &ctx, const TuneTable &t, int w, unsigned long long
   bp.status = ws->status;
   bp.item_rows = t.batch.item_rows;
   bp.grab = t.batch.grab;
+  bp.remaining = nullptr;
+  bp.host_res = nullptr;
+  bp.flags = nullptr;
+  bp.seq = 0;
   const Variant &v = batch_variant(t.batch.variant);
   int cps = t.batch.ctas_per_sm < ctx.occ_batch[t.batch.variant] ? t.batch.ctas_per_sm
                                                                  : ctx.occ_batch[t.batch.variant];

@@ -1,0 +1,202 @@
+// pospop_batch.cuh -- batched counting over many arrays: planning kernels
+// (work items per array, prefix sums) and the persistent counting kernel.
+// Templated on the array source: CSR byte offsets from one base with one w
+// (pospopcnt_batch), or per-array descriptors with their own pointer,
+// length, w and output row (the serving loop's mixed batches).
+#pragma once
+
+#include <cstdint>
+
+#include "pospop_device.cuh"
+#include "pospop_internal.h"
+
+namespace pospop {
+
+// Byte range [s, e) of array a, its width and its output counters.
+template <bool DESC>
+struct ArrayRef {
+  uint64_t s, e;
+  int w;
+  unsigned long long *out;
+};
+
+template <bool DESC>
+__device__ __forceinline__ ArrayRef<DESC> array_ref(const BatchParams &P, uint64_t a) {
+  ArrayRef<DESC> r;
+  if (DESC) {
+    const Desc d = P.desc[a];
+    r.s = (uint64_t)d.ptr;
+    r.e = r.s + d.nbytes;
+    r.w = d.w;
+    r.out = d.out;
+  } else {
+    const uint64_t base = (uint64_t)P.base;
+    r.s = base + __ldg(P.offsets + a);
+    r.e = base + __ldg(P.offsets + a + 1);
+    r.w = P.w;
+    r.out = P.counts + a * (uint64_t)P.w;
+  }
+  return r;
+}
+
+// ---------------------------------------------------------------------------
+// Planning.  Array a spans granules [s/16, ceil(e/16)); its rows of 32
+// granules are cut into work items of item_rows rows.  item_start is the
+// exclusive prefix sum of the items per array.  Decreasing CSR offsets set
+// the status and give the array no items.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t span_items(uint64_t s, uint64_t e, uint32_t item_rows) {
+  if (e <= s) return 0;
+  const uint64_t G = (((e + 15u) & ~15ull) - (s & ~15ull)) >> 4;
+  const uint64_t R = (G + 31u) >> 5;
+  return (R + item_rows - 1) / item_rows;
+}
+
+// Inclusive block-wide scan of one value per thread (kPlanThreads threads).
+__device__ __forceinline__ uint64_t block_inclusive_scan(uint64_t v, uint64_t *warp_tot) {
+  const unsigned lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const uint64_t t = __shfl_up_sync(kFull, v, d);
+    if ((int)lane >= d) v += t;
+  }
+  if (lane == 31) warp_tot[warp] = v;
+  __syncthreads();
+  if (warp == 0) {
+    uint64_t t = warp_tot[lane];
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const uint64_t u = __shfl_up_sync(kFull, t, d);
+      if ((int)lane >= d) t += u;
+    }
+    warp_tot[lane] = t;
+  }
+  __syncthreads();
+  if (warp > 0) v += warp_tot[warp - 1];
+  return v;
+}
+
+template <bool DESC>
+__global__ void __launch_bounds__(kPlanThreads) plan_items_kernel(PlanParams P) {
+  __shared__ uint64_t red[32];
+  const uint64_t a0 = (uint64_t)blockIdx.x * kPlanChunk + (uint64_t)threadIdx.x * kPlanPerThread;
+  uint64_t local = 0;
+  bool bad = false;
+#pragma unroll
+  for (int k = 0; k < kPlanPerThread; k++) {
+    const uint64_t a = a0 + k;
+    if (a < P.m) {
+      uint64_t s, e;
+      if (DESC) {
+        s = (uint64_t)P.desc[a].ptr;
+        e = s + P.desc[a].nbytes;
+      } else {
+        const uint64_t o0 = P.offsets[a], o1 = P.offsets[a + 1];
+        if (o1 < o0) bad = true;
+        s = P.base_addr + o0;
+        e = P.base_addr + o1;
+      }
+      const uint64_t it = span_items(s, e, P.item_rows);
+      P.item_start[a] = it;
+      local += it;
+    }
+  }
+  if (bad) *P.status = -1;
+  const uint64_t incl = block_inclusive_scan(local, red);
+  if (threadIdx.x == kPlanThreads - 1) P.block_sum[blockIdx.x] = incl;
+}
+
+// ---------------------------------------------------------------------------
+// Persistent counting.  Warps take `grab` consecutive work items per
+// atomic, find the first item's array with a 32-way warp search over
+// item_start, then walk forward.  Each item is a contiguous run of rows of
+// one array, counted with the per-thread algorithm and added to that
+// array's counters.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t find_array(const uint64_t *__restrict__ item_start, uint64_t m,
+                                               uint64_t i, unsigned lane) {
+  // Largest a in [0, m) with item_start[a] <= i (item_start[0] = 0 <= i < item_start[m]).
+  uint64_t lo = 0, hi = m;
+  while (hi - lo > 1) {
+    const uint64_t span = hi - lo;
+    const uint64_t idx = lo + span * (lane + 1) / 33;
+    const bool le = __ldg(item_start + idx) <= i;
+    const unsigned b = __ballot_sync(kFull, le);
+    const int c = __popc(b);
+    const uint64_t nlo = c > 0 ? lo + span * (uint64_t)c / 33 : lo;
+    const uint64_t nhi = c < 32 ? lo + span * (uint64_t)(c + 1) / 33 : hi;
+    lo = nlo;
+    hi = nhi > lo ? nhi : lo + 1;
+  }
+  return lo;
+}
+
+// Per-array completion for descriptor batches: the warp whose work item
+// brings the array's countdown to zero publishes the array's counters to
+// mapped host memory and then raises the array's flag.  Every warp orders
+// its counter atomics before its decrement with a device-scope fence; the
+// last warp reads the counters at L2 (atomic add of zero) after its own
+// fence, and system-scope fences order the published counts before the flag.
+__device__ __forceinline__ void signal_if_last(const BatchParams &P, uint64_t a, int w,
+                                               unsigned long long *out, unsigned lane) {
+  __threadfence();
+  unsigned last = 0;
+  if (lane == 0) last = atomicSub(P.remaining + a, 1u) == 1u ? 1u : 0u;
+  last = __shfl_sync(kFull, last, 0);
+  if (!last) return;
+  __threadfence();
+  unsigned long long *res = P.host_res + 64 * a;
+  for (int j = (int)lane; j < w; j += 32) res[j] = atomicAdd(out + j, 0ull);
+  __threadfence_system();
+  __syncwarp();
+  if (lane == 0) {
+    __threadfence_system();
+    *reinterpret_cast<volatile unsigned int *>(P.flags + a) = P.seq;
+    __threadfence_system();
+  }
+}
+
+template <bool DESC, int BS, int MINB, int DEPTH, int HINT>
+__global__ void __launch_bounds__(BS, MINB) batch_kernel(BatchParams P) {
+  if (*P.status != 0) return;   // planning rejected the offsets: change nothing
+  const unsigned lane = threadIdx.x & 31u;
+  const Xpose xk = make_xpose(lane);
+  const uint64_t total = P.item_start[P.m];
+  for (;;) {
+    unsigned long long i0 = 0;
+    if (lane == 0) i0 = atomicAdd(P.next, (unsigned long long)P.grab);
+    i0 = __shfl_sync(kFull, i0, 0);
+    if (i0 >= total) break;
+    uint64_t a = find_array(P.item_start, P.m, i0, lane);
+    const uint64_t i1 = (i0 + P.grab < total) ? i0 + P.grab : total;
+    for (uint64_t i = i0; i < i1; i++) {
+      while (__ldg(P.item_start + a + 1) <= i) a++;
+      const uint64_t k = i - __ldg(P.item_start + a);
+      const ArrayRef<DESC> r = array_ref<DESC>(P, a);
+      Span s;
+      const uint64_t A = r.s & ~15ull;
+      s.A = reinterpret_cast<const uint8_t *>(A);
+      s.head = (uint32_t)(r.s - A);
+      s.G = (((r.e + 15u) & ~15ull) - A) >> 4;
+      s.tail = (uint32_t)(r.e - (A + 16u * (s.G - 1)));
+      const uint32_t rot = (8u * s.head) & (uint32_t)(r.w - 1);
+      const uint64_t R = span_rows(s);
+      const uint64_t r0 = k * P.item_rows;
+      const uint64_t r1 = (r0 + P.item_rows < R) ? r0 + P.item_rows : R;
+      uint32_t cnt[4] = {0u, 0u, 0u, 0u};
+      count_rows<DEPTH, HINT>(s, r0, 1, r1 - r0, lane, xk, cnt);
+      unsigned long long *out = r.out;
+      fold_counts(cnt, r.w, rot, lane, [&](uint32_t j, unsigned long long v) {
+        if (v) atomicAdd(out + j, v);
+      });
+      if (DESC && P.remaining) signal_if_last(P, a, r.w, out, lane);
+    }
+  }
+}
+
+#define POSPOP_FAMILY(M)                                                  \
+  M(256, 2, 16, 0), M(256, 2, 16, 1), M(256, 2, 32, 0), M(256, 2, 32, 1), \
+  M(512, 1, 16, 0), M(512, 1, 16, 1), M(512, 1, 32, 0), M(512, 1, 32, 1), \
+  M(128, 4, 16, 0), M(128, 4, 16, 1), M(128, 4, 32, 0), M(128, 4, 32, 1)
+
+}  // namespace pospop

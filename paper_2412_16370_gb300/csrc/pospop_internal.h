@@ -26,7 +26,17 @@ struct StreamParams {
   uint32_t rot;                 // (8 * head) mod w
 };
 
+// One array of a descriptor batch (32 bytes).
+struct Desc {
+  const void *ptr;              // first byte (device addressable, any alignment)
+  uint64_t nbytes;
+  unsigned long long *out;      // w counters (device), added into
+  int32_t w;
+  int32_t reserved;
+};
+
 struct BatchParams {
+  const Desc *desc;             // descriptor batches (else CSR below)
   const uint8_t *base;
   const uint64_t *offsets;      // m + 1 byte offsets (device)
   uint64_t m;
@@ -37,9 +47,17 @@ struct BatchParams {
   const int *status;            // planning status (workspace)
   uint32_t item_rows;           // rows of 512 B per work item
   uint32_t grab;                // work items taken per atomic
+  // Descriptor batches only (may be null): per-array completion.  The warp
+  // that finishes an array's last work item copies its counters to
+  // host_res[64 a ..] (mapped host memory) and sets flags[a] = seq.
+  unsigned int *remaining;      // work items left per array (device)
+  unsigned long long *host_res; // 64 per array (mapped pinned host memory)
+  unsigned int *flags;          // one per array (mapped pinned host memory)
+  unsigned int seq;
 };
 
 struct PlanParams {
+  const Desc *desc;             // descriptor batches (else CSR offsets)
   const uint64_t *offsets;
   uint64_t m;
   uint64_t base_addr;           // (uint64_t)base, for granule alignment
@@ -78,7 +96,11 @@ const Variant &batch_variant(int i);
 int roofline_variant_count();
 const Variant &roofline_variant(int i);
 
+int desc_variant_count();
+const Variant &desc_variant(int i);
+
 const void *plan_items_fn();
+const void *plan_items_desc_fn();
 const void *plan_scan_fn();
 const void *plan_apply_fn();
 

@@ -1,0 +1,532 @@
+// pospop_serve.cu -- continuous-batching serving loop for pospopcnt
+// requests (declared in include/pospopcnt.h, pospop_server_*).
+//
+// Requests name device-resident input (any pointer, length and w).  A
+// request is ADMITTED when the input bytes of all admitted, unfinished
+// requests plus its own fit the server's device-memory budget and a slot is
+// free; admitted requests that are not yet on the GPU are gathered into one
+// batch as soon as one of the server's batch streams is free, so requests
+// that arrive while others run are counted in the next batch, overlapping on
+// the device with the batches already in flight.  A batch is one launch of
+// the descriptor counting kernel (pospop_batch.cuh): the host plans the work
+// items (it knows every request's address and length) and uploads them with
+// the descriptors in one copy; the counters stay in device memory until the
+// batch's event fires, then each request's w counts are copied to its
+// result buffer and the request completes.  All waits are bounded.
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+#include "pospopcnt.h"
+#include "pospop_runtime.h"
+
+namespace pospop {
+namespace {
+
+int64_t now_ns() {
+  return std::chrono::duration_cast<std::chrono::nanoseconds>(
+             std::chrono::steady_clock::now().time_since_epoch())
+      .count();
+}
+
+struct Request {
+  uint64_t id;
+  int w;
+  const void *dptr;
+  size_t nbytes;
+  uint64_t *result;
+  pospop_completion rec;
+};
+
+struct Batch {
+  cudaStream_t s = nullptr;
+  cudaEvent_t done = nullptr;
+  uint8_t *hblock = nullptr;            // pinned upload block
+  uint8_t *dblock = nullptr;            // device copy of it
+  unsigned long long *dcounts = nullptr;
+  unsigned long long *hcounts = nullptr;  // pinned (whole-batch copy, the fallback)
+  unsigned long long *hres = nullptr;   // mapped pinned: per-request counts from the device
+  unsigned int *hflags = nullptr;       // mapped pinned: per-request done flags
+  unsigned long long *dres = nullptr;   // device addresses of the two above
+  unsigned int *dflags = nullptr;
+  unsigned int seq = 0;
+  std::vector<Request *> reqs;          // null once completed
+  size_t open = 0;                      // requests of this batch not yet completed
+  bool busy = false;
+};
+
+}  // namespace
+}  // namespace pospop
+
+struct pospop_server {
+  pospop::DevCtx *ctx = nullptr;
+  size_t budget = 0;
+  int max_inflight = 0;
+  std::vector<pospop::Batch> batches;
+  size_t block_bytes = 0;
+
+  std::mutex mu;
+  std::condition_variable cv_loop, cv_done;
+  std::deque<pospop::Request *> pending;    // submitted, waiting for admission
+  std::deque<pospop::Request *> admitted;   // admitted, not yet on the GPU
+  std::deque<pospop_completion> finished;   // completions not yet polled
+  size_t inflight_bytes = 0;
+  int inflight = 0;
+  uint64_t next_id = 1;
+  uint64_t submitted = 0, completed = 0;
+  bool stop = false;
+  int loop_error = POSPOP_OK;
+  std::thread loop;
+};
+
+namespace pospop {
+namespace {
+
+// Upload block layout: [next u64][status i32 + pad][item_start (n+1) u64]
+// [remaining n u32, padded to 8 B][desc n x 32 B].
+size_t rem_offset(int n) { return 16 + 8 * (size_t)(n + 1); }
+size_t desc_offset(int n) { return rem_offset(n) + ((4 * (size_t)n + 7) & ~size_t(7)); }
+size_t block_size(int n) { return desc_offset(n) + sizeof(Desc) * (size_t)n; }
+
+void free_batch(Batch &b) {
+  if (b.hblock) cudaFreeHost(b.hblock);
+  if (b.hcounts) cudaFreeHost(b.hcounts);
+  if (b.hres) cudaFreeHost(b.hres);
+  if (b.hflags) cudaFreeHost(b.hflags);
+  if (b.dblock) cudaFree(b.dblock);
+  if (b.dcounts) cudaFree(b.dcounts);
+  if (b.done) cudaEventDestroy(b.done);
+  if (b.s) cudaStreamDestroy(b.s);
+  b = Batch();
+  cudaGetLastError();
+}
+
+// Enqueue one batch of the requests in b.reqs on b.s (loop thread only).
+// Requests are ordered smallest first, so that the persistent kernel, which
+// hands out work items in array order, finishes small requests early.
+int launch_batch(pospop_server &srv, Batch &b, const BatchTune &bt) {
+  std::stable_sort(b.reqs.begin(), b.reqs.end(),
+                   [](const Request *x, const Request *y) { return x->nbytes < y->nbytes; });
+  const int n = (int)b.reqs.size();
+  b.seq = b.seq + 1 == 0 ? 1 : b.seq + 1;
+  b.open = (size_t)n;
+  uint8_t *h = b.hblock;
+  uint64_t *item_start = reinterpret_cast<uint64_t *>(h + 16);
+  uint32_t *remaining = reinterpret_cast<uint32_t *>(h + rem_offset(n));
+  Desc *desc = reinterpret_cast<Desc *>(h + desc_offset(n));
+  memset(h, 0, 16);
+  uint64_t items = 0;
+  const uint32_t ir = bt.item_rows;
+  for (int k = 0; k < n; k++) {
+    const Request *r = b.reqs[k];
+    const uint64_t s = (uint64_t)r->dptr, e = s + r->nbytes;
+    item_start[k] = items;
+    uint64_t it = 0;
+    if (r->nbytes > 0) {
+      const uint64_t G = (((e + 15u) & ~15ull) - (s & ~15ull)) >> 4;
+      const uint64_t R = (G + 31u) >> 5;
+      it = (R + ir - 1) / ir;
+    }
+    items += it;
+    remaining[k] = (uint32_t)it;
+    desc[k] = Desc{r->dptr, (uint64_t)r->nbytes, b.dcounts + 64 * (size_t)k, r->w, 0};
+    if (it == 0) {   // nothing to count: done as soon as the loop looks
+      memset(b.hres + 64 * (size_t)k, 0, 64 * sizeof(unsigned long long));
+      __atomic_store_n(b.hflags + k, b.seq, __ATOMIC_RELEASE);
+    }
+  }
+  item_start[n] = items;
+  const size_t up = block_size(n);
+  if (cudaMemcpyAsync(b.dblock, h, up, cudaMemcpyHostToDevice, b.s) != cudaSuccess ||
+      cudaMemsetAsync(b.dcounts, 0, 64 * sizeof(unsigned long long) * (size_t)n, b.s) !=
+          cudaSuccess) {
+    cudaGetLastError();
+    return POSPOP_ECUDA;
+  }
+  BatchParams P;
+  memset(&P, 0, sizeof P);
+  P.desc = reinterpret_cast<const Desc *>(b.dblock + desc_offset(n));
+  P.m = (uint64_t)n;
+  P.item_start = reinterpret_cast<const uint64_t *>(b.dblock + 16);
+  P.next = reinterpret_cast<unsigned long long *>(b.dblock);
+  P.status = reinterpret_cast<const int *>(b.dblock + 8);
+  P.item_rows = ir;
+  P.grab = bt.grab;
+  P.remaining = reinterpret_cast<unsigned int *>(b.dblock + rem_offset(n));
+  P.host_res = b.dres;
+  P.flags = b.dflags;
+  P.seq = b.seq;
+  const Variant &v = desc_variant(bt.variant);
+  int cps = std::min(bt.ctas_per_sm, srv.ctx->occ_batch[bt.variant]);
+  if (cps < 1) cps = 1;
+  const uint64_t wpb = (uint64_t)v.bs / 32;
+  uint64_t grid = (items + wpb - 1) / wpb;
+  const uint64_t max_grid = (uint64_t)srv.ctx->sms * (uint64_t)cps;
+  if (grid > max_grid) grid = max_grid;
+  if (grid < 1) grid = 1;
+  void *args[] = {&P};
+  if (items > 0) {
+    if (cudaLaunchKernel(v.fn, dim3((unsigned)grid), dim3(v.bs), args, 0, b.s) != cudaSuccess) {
+      cudaGetLastError();
+      return POSPOP_ECUDA;
+    }
+    note_launches(1);
+  }
+  if (cudaMemcpyAsync(b.hcounts, b.dcounts, 64 * sizeof(unsigned long long) * (size_t)n,
+                      cudaMemcpyDeviceToHost, b.s) != cudaSuccess ||
+      cudaEventRecord(b.done, b.s) != cudaSuccess) {
+    cudaGetLastError();
+    return POSPOP_ECUDA;
+  }
+  return POSPOP_OK;
+}
+
+// Bookkeeping of a finished request; caller holds srv.mu.
+void complete(pospop_server &srv, Request *r, int status, int64_t t) {
+  r->rec.status = status;
+  r->rec.t_done_ns = t;
+  srv.inflight -= 1;
+  srv.inflight_bytes -= r->nbytes;
+  srv.completed += 1;
+  srv.finished.push_back(r->rec);
+  delete r;
+}
+
+// The loop thread owns the batches and every request it has taken out of
+// the admitted queue; the mutex guards only the queues and counters, and no
+// CUDA call is made while holding it.
+void serve_loop(pospop_server *srv) {
+  cudaSetDevice(srv->ctx->device);
+  std::vector<Batch *> finished_batches;
+  std::vector<Request *> done_reqs;
+  std::vector<std::pair<Batch *, std::vector<Request *>>> to_launch;
+  while (true) {
+    bool progress = false;
+    // 1. completions, without the lock: requests whose flag the device has
+    //    raised, and whole batches whose event has fired (which also frees
+    //    the batch's buffers; any request not flagged by then takes its
+    //    counts from the batch's copy)
+    finished_batches.clear();
+    done_reqs.clear();
+    for (Batch &b : srv->batches) {
+      if (!b.busy) continue;
+      for (size_t k = 0; k < b.reqs.size(); k++) {
+        Request *r = b.reqs[k];
+        if (!r || __atomic_load_n(b.hflags + k, __ATOMIC_ACQUIRE) != b.seq) continue;
+        if (r->result)
+          for (int j = 0; j < r->w; j++) r->result[j] = b.hres[64 * k + j];
+        r->rec.status = POSPOP_OK;
+        done_reqs.push_back(r);
+        b.reqs[k] = nullptr;
+        b.open -= 1;
+      }
+      const cudaError_t q = cudaEventQuery(b.done);
+      if (q == cudaErrorNotReady) continue;
+      if (q != cudaSuccess) cudaGetLastError();
+      const int st = q == cudaSuccess ? POSPOP_OK : POSPOP_ECUDA;
+      for (size_t k = 0; k < b.reqs.size(); k++) {
+        Request *r = b.reqs[k];
+        if (!r) continue;
+        if (st == POSPOP_OK && r->result)
+          for (int j = 0; j < r->w; j++) r->result[j] = b.hcounts[64 * k + j];
+        r->rec.status = st;
+        done_reqs.push_back(r);
+        b.reqs[k] = nullptr;
+      }
+      b.open = 0;
+      finished_batches.push_back(&b);
+    }
+    to_launch.clear();
+    bool stop_now = false;
+    {
+      std::unique_lock<std::mutex> lk(srv->mu);
+      const int64_t tnow = now_ns();
+      for (Request *r : done_reqs) complete(*srv, r, r->rec.status, tnow);
+      for (Batch *b : finished_batches) {
+        b->reqs.clear();
+        b->busy = false;
+      }
+      if (!done_reqs.empty() || !finished_batches.empty()) {
+        progress = true;
+        srv->cv_done.notify_all();
+      }
+      // 2. admission by device memory and slots (FIFO)
+      while (!srv->pending.empty() && srv->inflight < srv->max_inflight &&
+             srv->inflight_bytes + srv->pending.front()->nbytes <= srv->budget) {
+        Request *r = srv->pending.front();
+        srv->pending.pop_front();
+        r->rec.t_admit_ns = tnow;
+        srv->inflight += 1;
+        srv->inflight_bytes += r->nbytes;
+        srv->admitted.push_back(r);
+        progress = true;
+      }
+      // 3. everything admitted goes into the next free batch
+      for (Batch &b : srv->batches) {
+        if (b.busy || srv->admitted.empty()) continue;
+        std::vector<Request *> reqs;
+        while (!srv->admitted.empty() && (int)reqs.size() < srv->max_inflight) {
+          reqs.push_back(srv->admitted.front());
+          srv->admitted.pop_front();
+        }
+        b.busy = true;
+        to_launch.emplace_back(&b, std::move(reqs));
+        progress = true;
+      }
+      const bool busy = std::any_of(srv->batches.begin(), srv->batches.end(),
+                                    [](const Batch &b) { return b.busy; });
+      if (srv->stop && !busy && srv->admitted.empty() && srv->pending.empty()) stop_now = true;
+      if (!progress && !busy && !stop_now)
+        srv->cv_loop.wait_for(lk, std::chrono::milliseconds(50));
+    }
+    // launches, without the lock
+    BatchTune bt{};
+    if (!to_launch.empty()) {
+      std::lock_guard<std::mutex> g(srv->ctx->mu);
+      bt = srv->ctx->tune.batch;
+    }
+    for (auto &bl : to_launch) {
+      Batch &b = *bl.first;
+      b.reqs = std::move(bl.second);
+      const int64_t tl = now_ns();
+      for (Request *r : b.reqs) r->rec.t_launch_ns = tl;
+      const int rc = launch_batch(*srv, b, bt);
+      if (rc != POSPOP_OK) {
+        // nothing of this batch reached the device in a usable state:
+        // fail its requests (wait for what was enqueued before reusing it)
+        cudaStreamSynchronize(b.s);
+        cudaGetLastError();
+        std::lock_guard<std::mutex> g(srv->mu);
+        srv->loop_error = rc;
+        for (Request *r : b.reqs)
+          if (r) complete(*srv, r, rc, now_ns());
+        b.reqs.clear();
+        b.open = 0;
+        b.busy = false;
+        srv->cv_done.notify_all();
+      }
+    }
+    if (stop_now) break;
+    if (!progress) std::this_thread::yield();
+  }
+}
+
+// Queue one request.  `t_arrival` is its arrival time (the submit time, or a
+// load generator's scheduled arrival, so that latency includes any delay in
+// submitting it).
+int submit_impl(pospop_server *srv, int w, const void *dptr, size_t nbytes, uint64_t *result,
+                uint64_t *id, int64_t t_arrival) {
+  Request *r = new Request();
+  r->w = w;
+  r->dptr = dptr;
+  r->nbytes = nbytes;
+  r->result = result;
+  memset(&r->rec, 0, sizeof r->rec);
+  r->rec.w = w;
+  r->rec.nbytes = nbytes;
+  uint64_t rid;
+  {
+    std::lock_guard<std::mutex> g(srv->mu);
+    if (srv->stop) {
+      delete r;
+      return POSPOP_EBUSY;
+    }
+    rid = srv->next_id++;
+    r->id = rid;
+    r->rec.id = rid;
+    r->rec.t_submit_ns = t_arrival;
+    srv->pending.push_back(r);
+    srv->submitted += 1;
+  }
+  srv->cv_loop.notify_one();
+  if (id) *id = rid;
+  return POSPOP_OK;
+}
+
+bool valid_width(int w) {
+  return w == 1 || w == 2 || w == 4 || w == 8 || w == 16 || w == 32 || w == 64;
+}
+
+// Device address of a request's input, or POSPOP_EPTR.
+int request_ptr(pospop_server *srv, const void *bytes, size_t nbytes, const void **dptr) {
+  *dptr = bytes;
+  if (nbytes == 0) return POSPOP_OK;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return POSPOP_EPTR;
+  }
+  if (a.type == cudaMemoryTypeHost && a.devicePointer) {
+    *dptr = a.devicePointer;
+    return POSPOP_OK;
+  }
+  if ((a.type == cudaMemoryTypeDevice && a.device == srv->ctx->device) ||
+      a.type == cudaMemoryTypeManaged)
+    return POSPOP_OK;
+  return POSPOP_EPTR;
+}
+
+}  // namespace
+}  // namespace pospop
+
+using namespace pospop;
+
+extern "C" {
+
+int pospop_server_create(size_t mem_budget, int max_inflight, int max_batches,
+                         pospop_server **out) {
+  if (!out || mem_budget == 0 || max_inflight < 1 || max_inflight > (1 << 20) || max_batches < 1 ||
+      max_batches > 64)
+    return POSPOP_EINVAL;
+  *out = nullptr;
+  int rc = POSPOP_OK;
+  DevCtx *c = current_ctx(&rc);
+  if (!c) return rc;
+  pospop_server *srv = new pospop_server();
+  srv->ctx = c;
+  srv->budget = mem_budget;
+  srv->max_inflight = max_inflight;
+  srv->block_bytes = block_size(max_inflight);
+  srv->batches.resize((size_t)max_batches);
+  for (Batch &b : srv->batches) {
+    const size_t cbytes = 64 * sizeof(unsigned long long) * (size_t)max_inflight;
+    if (cudaStreamCreateWithFlags(&b.s, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b.done, cudaEventDisableTiming) != cudaSuccess ||
+        cudaMallocHost(&b.hblock, srv->block_bytes) != cudaSuccess ||
+        cudaMallocHost(&b.hcounts, cbytes) != cudaSuccess ||
+        cudaMalloc(&b.dblock, srv->block_bytes) != cudaSuccess ||
+        cudaMalloc(&b.dcounts, cbytes) != cudaSuccess ||
+        cudaHostAlloc(&b.hres, cbytes, cudaHostAllocMapped) != cudaSuccess ||
+        cudaHostAlloc(&b.hflags, sizeof(unsigned int) * (size_t)max_inflight,
+                      cudaHostAllocMapped) != cudaSuccess ||
+        cudaHostGetDevicePointer(reinterpret_cast<void **>(&b.dres), b.hres, 0) != cudaSuccess ||
+        cudaHostGetDevicePointer(reinterpret_cast<void **>(&b.dflags), b.hflags, 0) !=
+            cudaSuccess) {
+      cudaGetLastError();
+      for (Batch &x : srv->batches) free_batch(x);
+      delete srv;
+      return POSPOP_ENOMEM;
+    }
+    memset(b.hflags, 0, sizeof(unsigned int) * (size_t)max_inflight);   // seq starts at 1
+  }
+  srv->loop = std::thread(serve_loop, srv);
+  *out = srv;
+  return POSPOP_OK;
+}
+
+int pospop_server_submit(pospop_server *srv, int w, const void *bytes, size_t nbytes,
+                         uint64_t *result, uint64_t *id) {
+  if (!srv || !valid_width(w)) return POSPOP_EINVAL;
+  if (nbytes > 0 && !bytes) return POSPOP_EINVAL;
+  if (nbytes > srv->budget) return POSPOP_ERANGE;
+  const void *dptr = nullptr;
+  const int rc = request_ptr(srv, bytes, nbytes, &dptr);
+  if (rc != POSPOP_OK) return rc;
+  return submit_impl(srv, w, dptr, nbytes, result, id, now_ns());
+}
+
+int pospop_server_poll(pospop_server *srv, pospop_completion *out, int max, int timeout_ms) {
+  if (!srv || !out || max < 1) return POSPOP_EINVAL;
+  std::unique_lock<std::mutex> lk(srv->mu);
+  if (srv->finished.empty() && timeout_ms > 0)
+    srv->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms),
+                          [&] { return !srv->finished.empty(); });
+  if (srv->finished.empty()) return POSPOP_ETIMEDOUT;
+  int n = 0;
+  while (n < max && !srv->finished.empty()) {
+    out[n++] = srv->finished.front();
+    srv->finished.pop_front();
+  }
+  return n;
+}
+
+int pospop_server_drain(pospop_server *srv, int timeout_ms) {
+  if (!srv) return POSPOP_EINVAL;
+  std::unique_lock<std::mutex> lk(srv->mu);
+  const bool ok = srv->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms < 0 ? 0 : timeout_ms),
+                                        [&] { return srv->completed == srv->submitted; });
+  return ok ? POSPOP_OK : POSPOP_ETIMEDOUT;
+}
+
+int pospop_server_stats(pospop_server *srv, uint64_t stats[6]) {
+  if (!srv || !stats) return POSPOP_EINVAL;
+  std::lock_guard<std::mutex> g(srv->mu);
+  stats[0] = srv->submitted;
+  stats[1] = srv->completed;
+  stats[2] = srv->pending.size();
+  stats[3] = (uint64_t)srv->inflight;
+  stats[4] = srv->inflight_bytes;
+  stats[5] = (uint64_t)(int64_t)srv->loop_error;
+  return POSPOP_OK;
+}
+
+int pospop_server_run_trace(pospop_server *srv, size_t n, const int64_t *arrival_ns,
+                            const int32_t *w, const uint64_t *ptrs, const uint64_t *nbytes,
+                            uint64_t *results, pospop_completion *out, int timeout_ms) {
+  if (!srv || (n > 0 && (!arrival_ns || !w || !ptrs || !nbytes || !out))) return POSPOP_EINVAL;
+  if (n == 0) return POSPOP_OK;
+  // validate every request before the clock starts
+  std::vector<const void *> dptr(n);
+  for (size_t i = 0; i < n; i++) {
+    if (!valid_width(w[i]) || (nbytes[i] > 0 && ptrs[i] == 0)) return POSPOP_EINVAL;
+    if (nbytes[i] > srv->budget) return POSPOP_ERANGE;
+    if (i > 0 && arrival_ns[i] < arrival_ns[i - 1]) return POSPOP_EINVAL;
+    const int rc = request_ptr(srv, reinterpret_cast<const void *>(ptrs[i]), nbytes[i], &dptr[i]);
+    if (rc != POSPOP_OK) return rc;
+  }
+  uint64_t first_id = 0;
+  const int64_t t0 = now_ns();
+  for (size_t i = 0; i < n; i++) {
+    const int64_t due = t0 + arrival_ns[i];
+    while (now_ns() < due) {
+    }
+    uint64_t rid = 0;
+    const int rc = submit_impl(srv, w[i], dptr[i], nbytes[i], results ? results + 64 * i : nullptr,
+                               &rid, due);
+    if (rc != POSPOP_OK) return rc;
+    if (i == 0) first_id = rid;
+  }
+  // collect the n completions (ids are consecutive when this is the only submitter)
+  size_t got = 0;
+  std::vector<pospop_completion> buf(4096);
+  const int64_t deadline = now_ns() + (int64_t)timeout_ms * 1000000;
+  while (got < n) {
+    const int64_t left_ms = (deadline - now_ns()) / 1000000;
+    if (left_ms <= 0) return POSPOP_ETIMEDOUT;
+    const int k = pospop_server_poll(srv, buf.data(), (int)buf.size(),
+                                     (int)std::min<int64_t>(left_ms, 100));
+    if (k == POSPOP_ETIMEDOUT) continue;
+    if (k < 0) return k;
+    for (int j = 0; j < k; j++) {
+      const uint64_t idx = buf[j].id - first_id;
+      if (idx < n) {
+        out[idx] = buf[j];
+        got++;
+      }
+    }
+  }
+  return POSPOP_OK;
+}
+
+int pospop_server_destroy(pospop_server *srv) {
+  if (!srv) return POSPOP_EINVAL;
+  {
+    std::lock_guard<std::mutex> g(srv->mu);
+    srv->stop = true;
+  }
+  srv->cv_loop.notify_all();
+  if (srv->loop.joinable()) srv->loop.join();
+  for (Batch &b : srv->batches) {
+    if (b.s) cudaStreamSynchronize(b.s);
+    free_batch(b);
+  }
+  delete srv;
+  return POSPOP_OK;
+}
+
+}  // extern "C"

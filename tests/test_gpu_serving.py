@@ -1,0 +1,155 @@
+"""The continuous-batching serving loop (pospop_server_*) on the GPU.
+
+Requests of mixed width and size over a device-resident pool must give the
+same counts in the mix as alone (and as the CPU oracle), admission must keep
+the in-flight input bytes within the budget and the admitted requests within
+the slot cap, later arrivals must be launched while earlier batches are still
+running, and every wait must end with a status.
+"""
+import numpy as np
+import pytest
+import torch
+
+from paper_2412_16370_gb300 import binding as pp
+from paper_2412_16370_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+MIB = 1 << 20
+
+
+@pytest.fixture(scope="module")
+def pool(gpu):
+    n = 256 * MIB
+    t = torch.empty(n + 64, dtype=torch.uint8, device=gpu)
+    t.random_(0, 256)
+    torch.cuda.synchronize()
+    return t
+
+
+def _requests(n, seed, lo, hi, pool_bytes):
+    r = synth.poisson_requests(n, 1.0, seed, lo, hi, pool_bytes=pool_bytes)
+    return r["w"].astype(np.int32), r["nbytes"].astype(np.uint64), r["offset"].astype(np.uint64)
+
+
+def _solo(pool, w, nbytes, offs):
+    out = torch.zeros((len(w), 64), dtype=torch.int64, device=pool.device)
+    base = pool.data_ptr()
+    for k in range(len(w)):
+        pp.pospopcnt_async(int(w[k]), out[k], base + int(offs[k]), int(nbytes[k]))
+    torch.cuda.synchronize()
+    return out.cpu().numpy().view(np.uint64)
+
+
+def test_mix_equals_solo_and_oracle(gpu, orc, pool):
+    n = 3000
+    w, nbytes, offs = _requests(n, 11, 1, 8 * MIB, 256 * MIB)
+    nbytes[::97] = 0   # some empty requests
+    srv = pp.pospop_server_create(1 << 30, 512, 4)
+    try:
+        results = np.zeros((n, 64), dtype=np.uint64)
+        arrival = (np.arange(n) * 2000).astype(np.int64)   # one request every 2 us
+        ptrs = pool.data_ptr() + offs
+        recs = pp.pospop_server_run_trace(srv, arrival, w, ptrs, nbytes, results)
+        assert (recs["status"] == 0).all()
+        assert np.array_equal(recs["nbytes"], nbytes)
+        st = pp.pospop_server_stats(srv)
+        assert st["submitted"] == st["finished"] == n and st["inflight"] == 0
+    finally:
+        pp.pospop_server_destroy(srv)
+    solo = _solo(pool, w, nbytes, offs)
+    for k in range(n):
+        assert np.array_equal(results[k, :w[k]], solo[k, :w[k]]), k
+    host = pool.cpu().numpy()
+    for k in range(0, n, 37):
+        seg = host[int(offs[k]):int(offs[k]) + int(nbytes[k])]
+        assert np.array_equal(results[k, :w[k]], orc.bytes(int(w[k]), seg)), k
+
+
+def _max_overlap(recs, start_key, weight=None):
+    """Largest sum of weights over requests whose [start, done) intervals overlap."""
+    ev = []
+    for k, r in enumerate(recs):
+        wt = 1 if weight is None else int(weight[k])
+        ev.append((int(r[start_key]), wt))
+        ev.append((int(r["t_done_ns"]), -wt))
+    ev.sort(key=lambda x: (x[0], x[1]))
+    cur = best = 0
+    for _, d in ev:
+        cur += d
+        best = max(best, cur)
+    return best
+
+
+def test_budget_and_slots_respected(gpu, pool):
+    n = 400
+    w, nbytes, offs = _requests(n, 12, 1 * MIB, 4 * MIB, 256 * MIB)
+    budget = 6 * MIB
+    srv = pp.pospop_server_create(budget, 3, 4)
+    try:
+        results = np.zeros((n, 64), dtype=np.uint64)
+        recs = pp.pospop_server_run_trace(srv, np.zeros(n, dtype=np.int64), w,
+                                          pool.data_ptr() + offs, nbytes, results)
+    finally:
+        pp.pospop_server_destroy(srv)
+    assert (recs["status"] == 0).all()
+    assert _max_overlap(recs, "t_admit_ns", nbytes) <= budget
+    assert _max_overlap(recs, "t_admit_ns") <= 3
+    solo = _solo(pool, w, nbytes, offs)
+    for k in range(n):
+        assert np.array_equal(results[k, :w[k]], solo[k, :w[k]]), k
+
+
+def test_later_arrivals_overlap_running_batches(gpu, pool):
+    """Continuous batching: requests are launched while earlier batches run."""
+    n = 64
+    w = np.full(n, 16, dtype=np.int32)
+    nbytes = np.full(n, 128 * MIB, dtype=np.uint64)
+    offs = (np.arange(n) % 2 * 64).astype(np.uint64)
+    arrival = (np.arange(n) * 5000).astype(np.int64)     # every 5 us; each takes ~20 us
+    srv = pp.pospop_server_create(64 << 30, 4096, 4)
+    try:
+        results = np.zeros((n, 64), dtype=np.uint64)
+        recs = pp.pospop_server_run_trace(srv, arrival, w, pool.data_ptr() + offs, nbytes, results)
+    finally:
+        pp.pospop_server_destroy(srv)
+    assert (recs["status"] == 0).all()
+    launches = sorted(set(int(x) for x in recs["t_launch_ns"]))
+    assert len(launches) > 1
+    # some batch was launched before an earlier batch had finished
+    first_done = {}
+    for r in recs:
+        first_done.setdefault(int(r["t_launch_ns"]), int(r["t_done_ns"]))
+    overlapped = any(launches[i + 1] < first_done[launches[i]] for i in range(len(launches) - 1))
+    assert overlapped
+    exp = _solo(pool, w[:2], nbytes[:2], offs[:2])
+    for k in range(n):
+        assert np.array_equal(results[k, :16], exp[k % 2, :16])
+
+
+def test_errors_and_bounded_waits(gpu, pool):
+    srv = pp.pospop_server_create(1 * MIB, 4, 1)
+    try:
+        L = pp.lib()
+        import ctypes
+        rid = ctypes.c_uint64()
+        res = np.zeros(64, dtype=np.uint64)
+        assert L.pospop_server_submit(srv, 16, pool.data_ptr(), 2 * MIB, res.ctypes.data,
+                                      ctypes.byref(rid)) == pp.POSPOP_ERANGE
+        assert L.pospop_server_submit(srv, 12, pool.data_ptr(), 16, res.ctypes.data,
+                                      ctypes.byref(rid)) == pp.POSPOP_EINVAL
+        host = np.zeros(64, dtype=np.uint8)
+        assert L.pospop_server_submit(srv, 8, host.ctypes.data, 64, res.ctypes.data,
+                                      ctypes.byref(rid)) == pp.POSPOP_EPTR
+        # nothing submitted: a poll times out, a drain returns at once
+        assert pp.pospop_server_poll(srv, timeout_ms=50) == []
+        assert pp.pospop_server_drain(srv, 1000) == pp.POSPOP_OK
+        # an empty request completes with zero counts
+        res[:] = 7
+        pp.pospop_server_submit(srv, 8, None, 0, res)
+        assert pp.pospop_server_drain(srv, 5000) == pp.POSPOP_OK
+        recs = pp.pospop_server_poll(srv, timeout_ms=100)
+        assert len(recs) == 1 and recs[0].status == 0
+        assert not res[:8].any() and (res[8:] == 7).all()
+    finally:
+        pp.pospop_server_destroy(srv)
