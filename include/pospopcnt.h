@@ -103,6 +103,27 @@ int pospopcnt_async(int w, uint64_t *counts, const void *bytes, size_t nbytes, v
 int pospopcnt_batch(int w, uint64_t *counts, const void *base, const uint64_t *offsets,
                     size_t m, void *stream);
 
+/*
+ * pospopcnt_batch for callers that cannot allocate device memory: code
+ * recording a CUDA graph in a capture mode that rejects allocation, services
+ * that must keep a fixed memory footprint once running, programs whose device
+ * memory belongs to another allocator.  The paper has no counterpart; this
+ * is a property of this library's batching.
+ *
+ * Same arguments, kernels and results as pospopcnt_batch, but the work plan
+ * lives in a fixed array of the library's own device image (about 513 KiB,
+ * held by every GPU that loads the library until the process exits) instead
+ * of a cudaMalloc'ed workspace: no call allocates or frees anything.  Limit:
+ * m <= 65535 arrays, else POSPOP_ERANGE.  The first call on a device looks
+ * up the array's address with that device current; make it before capturing
+ * any stream.  Every call shares the array, so calls that overlap on the GPU
+ * (two streams at once, unordered host threads) race and give wrong counts:
+ * order them.  Decreasing offsets leave the counters untouched (no status is
+ * reported; use pospopcnt_batch to get one).
+ */
+int pospopcnt_batch_noalloc(int w, uint64_t *counts, const void *base, const uint64_t *offsets,
+                            size_t m, void *stream);
+
 /* Synchronise `stream` and return (then clear) the device-side status of
  * the last pospopcnt_batch call on it: POSPOP_OK or POSPOP_EINVAL. */
 int pospopcnt_batch_status(void *stream);

@@ -49,6 +49,7 @@ _SIGNATURES = {
     "pospopcnt_u64": ([_vp, _vp, _sz], _int),
     "pospopcnt_async": ([_int, _vp, _vp, _sz, _vp], _int),
     "pospopcnt_batch": ([_int, _vp, _vp, _vp, _sz, _vp], _int),
+    "pospopcnt_batch_noalloc": ([_int, _vp, _vp, _vp, _sz, _vp], _int),
     "pospopcnt_batch_status": ([_vp], _int),
     "pospopcnt_reserve": ([_sz, _vp], _int),
     "pospopcnt_host": ([_int, _vp, _vp, _sz], _int),
@@ -183,6 +184,14 @@ def pospopcnt_batch(w: int, counts, base, offsets, m=None, stream=None):
         m = offsets.numel() - 1 if hasattr(offsets, "numel") else len(offsets) - 1
     return _check(lib().pospopcnt_batch(w, _ptr(counts), _ptr(base), _ptr(offsets), m,
                                         _stream(stream)))
+
+
+def pospopcnt_batch_noalloc(w: int, counts, base, offsets, m=None, stream=None):
+    """pospopcnt_batch without any device allocation (m <= 65535; see the header)."""
+    if m is None:
+        m = offsets.numel() - 1 if hasattr(offsets, "numel") else len(offsets) - 1
+    return _check(lib().pospopcnt_batch_noalloc(w, _ptr(counts), _ptr(base), _ptr(offsets), m,
+                                                _stream(stream)))
 
 
 def pospopcnt_batch_status(stream=None) -> int:
