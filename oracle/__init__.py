@@ -35,6 +35,8 @@ MUTANTS = {
     3: "position index off by one",
     4: "last byte skipped",
     5: "counts overwritten instead of added to",
+    6: "selection bitmap read most significant bit first",
+    7: "gathered regions counted as one continuous stream",
 }
 
 _CFLAGS = ["-std=c99", "-O2", "-fno-tree-vectorize", "-fPIC", "-shared", "-pthread", "-Wall"]
@@ -79,6 +81,10 @@ class Oracle:
         lib.oracle_pospop_bytes_mt.argtypes = [ctypes.c_int, u64p, vp, ctypes.c_size_t,
                                                ctypes.c_int]
         lib.oracle_pospop_bytes_mt.restype = ctypes.c_int
+        lib.oracle_pospop_gather.argtypes = [ctypes.c_int, u64p, vp, vp, ctypes.c_size_t]
+        lib.oracle_pospop_gather.restype = ctypes.c_int
+        lib.oracle_pospop_masked.argtypes = [ctypes.c_int, u64p, vp, ctypes.c_size_t, vp]
+        lib.oracle_pospop_masked.restype = ctypes.c_int
         lib.oracle_mutant_id.argtypes = []
         lib.oracle_mutant_id.restype = ctypes.c_int
         self.lib = lib
@@ -140,6 +146,31 @@ class Oracle:
                                           offsets.ctypes.data, m)
         if rc != OK:
             raise ValueError(f"oracle_pospop_batch returned {rc}")
+        return counts
+
+    def gather(self, w: int, regions, counts=None) -> np.ndarray:
+        """Several byte arrays (a list of uint8 arrays) counted into one counter array."""
+        regions = [np.ascontiguousarray(r, dtype=np.uint8) for r in regions]
+        ptrs = np.array([r.ctypes.data if r.size else 0 for r in regions], dtype=np.uint64)
+        lens = np.array([r.size for r in regions], dtype=np.uint64)
+        counts = self._counts(w, counts)
+        rc = self.lib.oracle_pospop_gather(w, self._u64p(counts), ptrs.ctypes.data,
+                                           lens.ctypes.data, len(regions))
+        if rc != OK:
+            raise ValueError(f"oracle_pospop_gather returned {rc}")
+        return counts
+
+    def masked(self, w: int, words: np.ndarray, n: int, mask: np.ndarray, counts=None) -> np.ndarray:
+        """Fig. 2 over the n words (little-endian bytes) whose selection bit is set."""
+        words = np.ascontiguousarray(words, dtype=np.uint8)
+        mask = np.ascontiguousarray(mask, dtype=np.uint8)
+        if words.size < n * (w // 8) or mask.size < (n + 7) // 8:
+            raise ValueError("words or mask too short")
+        counts = self._counts(w, counts)
+        rc = self.lib.oracle_pospop_masked(w, self._u64p(counts), words.ctypes.data, n,
+                                           mask.ctypes.data)
+        if rc != OK:
+            raise ValueError(f"oracle_pospop_masked returned {rc}")
         return counts
 
     def batch_rc(self, w: int, base: np.ndarray, offsets: np.ndarray, counts: np.ndarray) -> int:

@@ -26,6 +26,16 @@
  *   - oracle_pospop_batch: the same definition over many arrays given by
  *     CSR byte offsets (one counts row of w entries per array).
  *
+ *   - oracle_pospop_gather: several separate regions counted into ONE
+ *     counter array, each region its own word stream (Section 4, step 1
+ *     footnote: leaving C uncleared lets non-contiguous memory regions be
+ *     counted together).
+ *
+ *   - oracle_pospop_masked: Fig. 2 restricted to the words whose bit in a
+ *     selection bitmap is set (bit i of the bitmap, least significant bit
+ *     of byte i/8 first, selects word i): the GROUP BY count of Section 1
+ *     with a WHERE filter.
+ *
  *   - oracle_pospop_bytes_mt: the timed CPU baseline.  It splits the input
  *     at word boundaries across threads and sums the per-thread counts,
  *     which is exact because the counts of a concatenation of whole words
@@ -161,6 +171,56 @@ int oracle_pospop_batch(int w, uint64_t *counts, const uint8_t *base,
         if (len == 0) continue;
         if (base == NULL) return ORACLE_EINVAL;
         stream_counts(w, counts + (size_t)w * a, base + offsets[a], len);
+    }
+    return ORACLE_OK;
+}
+
+int oracle_pospop_gather(int w, uint64_t *counts, const uint64_t *ptrs, const uint64_t *lens,
+                         size_t n)
+{
+    if (!valid_w(w)) return ORACLE_EINVAL;
+    if (n == 0) return ORACLE_OK;
+    if (counts == NULL || ptrs == NULL || lens == NULL) return ORACLE_EINVAL;
+    for (size_t r = 0; r < n; r++)
+        if (lens[r] > 0 && ptrs[r] == 0) return ORACLE_EINVAL;
+#if ORACLE_MUTANT == 7
+    /* planted: the regions are counted as one continuous stream (bit
+     * positions carry over from one region to the next) */
+    {
+        uint64_t q0 = 0;
+        for (size_t r = 0; r < n; r++) {
+            const uint8_t *b = (const uint8_t *)(uintptr_t)ptrs[r];
+            for (uint64_t k = 0; k < lens[r]; k++)
+                for (unsigned bit = 0; bit < 8; bit++)
+                    counts[(q0 + 8u * k + bit) & ((uint64_t)w - 1u)] += (b[k] >> bit) & 1u;
+            q0 += 8u * lens[r];
+        }
+        return ORACLE_OK;
+    }
+#endif
+    for (size_t r = 0; r < n; r++)
+        if (lens[r] > 0)
+            stream_counts(w, counts, (const uint8_t *)(uintptr_t)ptrs[r], (size_t)lens[r]);
+    return ORACLE_OK;
+}
+
+int oracle_pospop_masked(int w, uint64_t *counts, const uint8_t *words, size_t n,
+                         const uint8_t *mask)
+{
+    if (!(w == 8 || w == 16 || w == 32 || w == 64)) return ORACLE_EINVAL;
+    if (n == 0) return ORACLE_OK;
+    if (counts == NULL || words == NULL || mask == NULL) return ORACLE_EINVAL;
+    size_t W = (size_t)w / 8;
+    for (size_t i = 0; i < n; i++) {
+        unsigned sel = (mask[i / 8] >> (i % 8)) & 1u;
+#if ORACLE_MUTANT == 6
+        /* planted: selection bits read most significant bit first */
+        sel = (mask[i / 8] >> (7 - i % 8)) & 1u;
+#endif
+        if (sel == 0) continue;
+        uint64_t v = 0;
+        for (size_t k = 0; k < W; k++) v |= (uint64_t)words[i * W + k] << (8u * k);
+        for (int j = 0; j < w; j++) counts[j] += (v >> j) & 1u;
     }
     return ORACLE_OK;
 }

@@ -20,7 +20,13 @@ None of these re-types the oracle's loop.  The expected values come from:
 * the one-hot category histogram (Section 1's GROUP BY use), counted with
   ``numpy.bincount`` from the generator's categories,
 * fold consistency between widths w and 2w,
-* a 6-sigma band around n*p for Bernoulli(p) bits.
+* a 6-sigma band around n*p for Bernoulli(p) bits,
+* for the gathered form: each region's numpy brute force, summed (Section 4
+  step 1's footnote: non-contiguous regions counted into one C), and the
+  split of one array at word boundaries giving the whole array's count,
+* for the selected (WHERE) form: numpy brute force (the unpacked word bits
+  times the unpacked selection bits), all-ones and all-zero selections, and
+  the one-hot category histogram of the selected rows.
 """
 from __future__ import annotations
 
@@ -219,12 +225,62 @@ def pin_batch(o):
     return None
 
 
+def pin_gather(o):
+    rng = np.random.default_rng(3)
+    for w in ALL_W:
+        lens = [0, 1, 3, 16, 17, 255, 1000, 4097, 0, 9]
+        regions = [synth.random_bytes(n, seed=100 + k) for k, n in enumerate(lens)]
+        exp = sum(_unpack_counts(r, w) for r in regions)
+        got = o.gather(w, regions)
+        if not np.array_equal(got, exp):
+            return f"gather w={w}"
+        W = max(1, w // 8)
+        whole = synth.random_bytes(64 * W + 5, seed=7)
+        cuts = sorted(set(int(c) * W for c in rng.integers(0, 64, 6)))
+        pieces = [whole[a:b] for a, b in zip([0] + cuts, cuts + [whole.size])]
+        if not np.array_equal(o.gather(w, pieces), _unpack_counts(whole, w)):
+            return f"gather split w={w}"
+    return None
+
+
+def _masked_expected(w, words, n, mask):
+    W = w // 8
+    bits = np.unpackbits(words[:n * W], bitorder="little").reshape(n, w).astype(np.uint64)
+    sel = np.unpackbits(mask, bitorder="little")[:n].astype(np.uint64)
+    return (bits * sel[:, None]).sum(axis=0, dtype=np.uint64)
+
+
+def pin_masked(o):
+    for w in WORD_W:
+        W = w // 8
+        for n in (1, 7, 8, 9, 63, 64, 65, 1000):
+            words = synth.random_bytes(n * W, seed=n + w)
+            mask = synth.random_bytes((n + 7) // 8, seed=3 * n + w)
+            if not np.array_equal(o.masked(w, words, n, mask), _masked_expected(w, words, n, mask)):
+                return f"masked w={w} n={n}"
+            ones = np.full((n + 7) // 8, 0xFF, dtype=np.uint8)
+            if not np.array_equal(o.masked(w, words, n, ones), o.bytes(w, words)):
+                return f"masked all-ones w={w} n={n}"
+            if o.masked(w, words, n, np.zeros_like(ones)).any():
+                return f"masked all-zero w={w} n={n}"
+    th = synth.zipf_thresholds()
+    n = 10000
+    cats = synth.one_hot_categories(n, 9, th)
+    data = synth.one_hot_bytes(n, 9, th)
+    mask = synth.random_bytes((n + 7) // 8, seed=10)
+    sel = np.unpackbits(mask, bitorder="little")[:n].astype(bool)
+    exp = np.bincount(cats[sel], minlength=8).astype(np.uint64)
+    if not np.array_equal(o.masked(8, data, n, mask), exp):
+        return "masked one-hot GROUP BY"
+    return None
+
+
 ALL_PINS = [
     pin_exhaustive_u8, pin_exhaustive_u16, pin_bruteforce_tiny, pin_popcount_sum,
     pin_additivity, pin_one_hot, pin_closed_forms, pin_fold, pin_statistical,
-    pin_typed_vs_bytes, pin_mt, pin_batch,
+    pin_typed_vs_bytes, pin_mt, pin_batch, pin_gather, pin_masked,
 ]
 
 #: a fast subset used on the planted-mistake builds
 QUICK_PINS = [pin_exhaustive_u8, pin_bruteforce_tiny, pin_popcount_sum, pin_additivity,
-              pin_typed_vs_bytes, pin_closed_forms]
+              pin_typed_vs_bytes, pin_closed_forms, pin_gather, pin_masked]
