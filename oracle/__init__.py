@@ -24,7 +24,7 @@ _BUILD = os.path.join(_HERE, "_build")
 _LOCK = threading.Lock()
 _LIBS: dict[int, "Oracle"] = {}
 
-WIDTHS = (1, 2, 4, 8, 16, 32, 64)
+WIDTHS = (1, 2, 4, 8, 16, 32, 64, 128, 256)
 OK = 0
 EINVAL = -1
 

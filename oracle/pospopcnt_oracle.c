@@ -21,7 +21,8 @@
  *     bit b of byte k is stream bit 8k+b and goes to counter (8k+b) mod w.
  *     For whole words this equals Fig. 2 read little-endian; a trailing
  *     partial word behaves as if zero-padded.  It also accepts w = 1, 2, 4
- *     (w = 1 is the conventional population count, Section 3.3).
+ *     (w = 1 is the conventional population count, Section 3.3) and the
+ *     wider folds w = 128, 256.
  *
  *   - oracle_pospop_batch: the same definition over many arrays given by
  *     CSR byte offsets (one counts row of w entries per array).
@@ -101,9 +102,13 @@ void oracle_pospop_u64(uint64_t counts[64], const uint64_t *words, size_t n)
  * Section 1: w interleaved bit streams over a byte stream.
  * ---------------------------------------------------------------------- */
 
+/* Any power of two from 1 to 256: the interleaved-streams definition holds
+ * for every w, and Section 4 states the algorithm for a general maximum word
+ * size (the paper's code fixes it at 64). */
 static int valid_w(int w)
 {
-    return w == 1 || w == 2 || w == 4 || w == 8 || w == 16 || w == 32 || w == 64;
+    return w == 1 || w == 2 || w == 4 || w == 8 || w == 16 || w == 32 || w == 64 ||
+           w == 128 || w == 256;
 }
 
 /* Counts of one byte stream, added into counts[0..w-1].  Stream bit q = 8k+b
@@ -234,7 +239,7 @@ struct mt_job {
     int w;
     const uint8_t *bytes;
     size_t nbytes;
-    uint64_t counts[64];
+    uint64_t counts[256];
 };
 
 /* Fig. 2 on little-endian words assembled from the byte stream; a trailing
@@ -246,11 +251,19 @@ static void fig2_word_loop(int w, uint64_t *counts, const uint8_t *bytes, size_t
     unsigned bits = (w >= 8) ? (unsigned)w : 8u;
     size_t nwords = (nbytes + W - 1) / W;
     for (size_t i = 0; i < nwords; i++) {
-        uint64_t v = 0;
-        for (size_t k = 0; k < W && i * W + k < nbytes; k++)
-            v |= (uint64_t)bytes[i * W + k] << (8u * k);
-        for (unsigned j = 0; j < bits; j++)
-            counts[j & (unsigned)(w - 1)] += (v >> j) & 1u;
+        if (w <= 64) {
+            uint64_t v = 0;
+            for (size_t k = 0; k < W && i * W + k < nbytes; k++)
+                v |= (uint64_t)bytes[i * W + k] << (8u * k);
+            for (unsigned j = 0; j < bits; j++)
+                counts[j & (unsigned)(w - 1)] += (v >> j) & 1u;
+        } else {
+            /* a 128- or 256-bit word: bit j is bit j % 8 of its byte j / 8 */
+            for (unsigned j = 0; j < bits; j++) {
+                size_t k = i * W + j / 8;
+                if (k < nbytes) counts[j] += (bytes[k] >> (j % 8)) & 1u;
+            }
+        }
     }
 }
 

@@ -34,7 +34,7 @@ import numpy as np
 
 from paper_2412_16370_gb300 import synth
 
-ALL_W = (1, 2, 4, 8, 16, 32, 64)
+ALL_W = (1, 2, 4, 8, 16, 32, 64, 128, 256)
 WORD_W = (8, 16, 32, 64)
 
 
@@ -165,8 +165,8 @@ def pin_closed_forms(o):
 
 
 def pin_fold(o):
-    data = synth.random_bytes(8 * 1000, seed=42)
-    for w in (1, 2, 4, 8, 16, 32):
+    data = synth.random_bytes(32 * 1000, seed=42)
+    for w in (1, 2, 4, 8, 16, 32, 64, 128):
         pw = o.bytes(w, data)
         p2 = o.bytes(2 * w, data)
         if not np.array_equal(pw, p2[:w] + p2[w:]):

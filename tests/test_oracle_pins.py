@@ -38,7 +38,7 @@ def test_argument_errors(orc):
     counts = np.zeros(8, dtype=np.uint64)
     data = np.zeros(4, dtype=np.uint8)
     assert orc.bytes_rc(3, counts, data.ctypes.data, 4) == oracle.EINVAL
-    assert orc.bytes_rc(128, counts, data.ctypes.data, 4) == oracle.EINVAL
+    assert orc.bytes_rc(512, counts, data.ctypes.data, 4) == oracle.EINVAL
     assert orc.bytes_rc(8, counts, None, 4) == oracle.EINVAL
     assert orc.bytes_rc(8, counts, None, 0) == oracle.OK  # n == 0 is a no-op
 
