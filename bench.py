@@ -291,9 +291,13 @@ def run_ours(args):
             extra["e2e"] = _e2e(args, pp, data, nbytes, world, dist)
         if rank == 0:
             for key, fn in (("batched", lambda: _batched(pp, synth, synth_device, dev, stream,
-                                                         achieved, hbm_peak)),
+                                                         achieved, hbm_peak, m=args.batched_m)),
                             ("short", lambda: _short(pp, synth, dev, stream)),
                             ("serving", lambda: _serving(pp, synth, data, nbytes, achieved, dev)),
+                            ("masked", lambda: _masked(pp, synth_device, data, nbytes, dev,
+                                                       stream, achieved, hbm_peak)),
+                            ("gather", lambda: _gather(pp, synth, data, nbytes, dev, stream,
+                                                       achieved, hbm_peak)),
                             ("cpu_baseline", lambda: _cpu_baseline(data))):
                 if not want(key):
                     continue
@@ -407,9 +411,17 @@ def _batched(pp, synth, synth_device, dev, stream, large_gbs, hbm_peak, m=200000
     wall = time.perf_counter() - t0
     ms_per = e0.elapsed_time(e1)
     gbs = total / (ms / 1e3) / 1e9
+    # the oracle on the first 2000 arrays, timed on the host cores
+    import oracle
+    orc = oracle.load()
+    k = 2000
+    sub_off = offs[:k + 1]
+    sub = base[:int(sub_off[-1])].cpu().numpy()
+    ora = _oracle_rate(lambda: orc.batch(8, sub, sub_off), lambda: sub.size)
     del base
     torch.cuda.empty_cache()
-    return {"workload": f"{m} one-hot uint8 arrays (Zipf(1.1) over 8 classes), sizes log-uniform "
+    return {"oracle_GBps": ora, "oracle_sample": f"first {k} arrays ({sub.size} bytes), 1 thread",
+            "workload": f"{m} one-hot uint8 arrays (Zipf(1.1) over 8 classes), sizes log-uniform "
                         "1 B..4 MiB, back to back (unaligned starts), w=8",
             "bytes": total, "GBps": round(gbs, 1), "ms": round(ms, 3),
             "frac_of_large_array": round(gbs / large_gbs, 4),
@@ -510,6 +522,82 @@ def _serving(pp, synth, pool, pool_bytes, large_gbs, dev, loads=(0.3, 0.6, 0.9),
     return out
 
 
+def _oracle_rate(fn, nbytes_fn, budget_s=2.0):
+    """GB/s of an oracle call on the host cores, repeated for about budget_s seconds."""
+    t0 = time.perf_counter()
+    done = 0
+    while True:
+        fn()
+        done += nbytes_fn()
+        if time.perf_counter() - t0 > budget_s:
+            break
+    return round(done / (time.perf_counter() - t0) / 1e9, 4)
+
+
+def _time_ms(fn, stream, reps=10, warm=3):
+    import torch
+    for _ in range(warm):
+        fn()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def _masked(pp, synth_device, data, nbytes, dev, stream, large_gbs, hbm_peak):
+    """WHERE-selected count: the 8 GiB array as 32-bit words, half of them selected."""
+    import torch
+    n = nbytes // 4
+    sel = torch.empty((n + 7) // 8, dtype=torch.uint8, device=dev)
+    synth_device.random_(sel, 4242)
+    c = torch.zeros(32, dtype=torch.int64, device=dev)
+    ms = _time_ms(lambda: pp.pospopcnt_masked(32, c, data, n, sel, stream), stream)
+    moved = nbytes + sel.numel()
+    gbs = moved / (ms / 1e3) / 1e9
+    import oracle
+    orc = oracle.load()
+    k = 16 << 20                     # 16 Mi words = 64 MiB sample
+    wh = data[:4 * k].cpu().numpy()
+    sh = sel[:k // 8].cpu().numpy()
+    ora = _oracle_rate(lambda: orc.masked(32, wh, k, sh), lambda: wh.size + sh.size)
+    del sel
+    return {"oracle_GBps": ora, "oracle_sample": "first 64 MiB of words + their bitmap, 1 thread",
+            "workload": "8 GiB array as 2^31 uint32 words, selection bitmap of 256 MiB with "
+                        "Bernoulli(0.5) bits, w=32",
+            "ms": round(ms, 4), "GBps": round(gbs, 1), "frac_of_hbm_peak": round(gbs / hbm_peak, 4),
+            "frac_of_plain_count": round(gbs / large_gbs, 4),
+            "bytes_per_launch": moved}
+
+
+def _gather(pp, synth, data, nbytes, dev, stream, large_gbs, hbm_peak, m=100000):
+    """Many separate regions of the resident array counted into one counter array."""
+    import torch
+    lens = synth.log_uniform_sizes(m, 1, 1 << 20, seed=61)
+    starts = np.floor(synth.uniforms(m, 62) * (nbytes - (1 << 20))).astype(np.int64)
+    ptrs = torch.from_numpy(data.data_ptr() + starts).to(dev)
+    ln = torch.from_numpy(lens.astype(np.int64)).to(dev)
+    c = torch.zeros(16, dtype=torch.int64, device=dev)
+    ms = _time_ms(lambda: pp.pospopcnt_gather(16, c, ptrs, ln, m, stream), stream)
+    total = int(lens.sum())
+    gbs = total / (ms / 1e3) / 1e9
+    import oracle
+    orc = oracle.load()
+    k = 1000
+    regions = [data[int(a):int(a) + int(b)].cpu().numpy() for a, b in zip(starts[:k], lens[:k])]
+    ora = _oracle_rate(lambda: orc.gather(16, regions), lambda: sum(r.size for r in regions))
+    return {"oracle_GBps": ora, "oracle_sample": f"first {k} regions, 1 thread",
+            "workload": f"{m} regions of the 8 GiB array, lengths log-uniform 1 B..1 MiB, "
+                        "uniform unaligned starts, w=16, one counter array",
+            "bytes": total, "ms": round(ms, 4), "GBps": round(gbs, 1),
+            "frac_of_hbm_peak": round(gbs / hbm_peak, 4),
+            "frac_of_large_array": round(gbs / large_gbs, 4)}
+
+
 def run_reference(args):
     """The CPU oracle (the reference arm of this tier) on the same workload."""
     world, rank, _ = _dist()
@@ -553,11 +641,14 @@ def main():
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--gib", type=int, default=8, help="array size in GiB (8 = the workload)")
     ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--batched-m", type=int, default=200000,
+                    help="arrays in the batched section (200000 = the workload)")
     ap.add_argument("--ref-sample-mib", type=int, default=16)
     ap.add_argument("--quick", action="store_true",
                     help="skip e2e, batched, short, serving and the cpu baseline")
     ap.add_argument("--sections", default="",
-                    help="comma list of extra sections to run (e2e,batched,short,serving,cpu_baseline)")
+                    help="comma list of extra sections to run "
+                         "(e2e,batched,short,serving,masked,gather,cpu_baseline)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")

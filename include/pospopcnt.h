@@ -19,8 +19,10 @@
  *     optional, which lets streamed or non-contiguous input be counted into
  *     one counter array).  Zero them first for a fresh count.
  *   - Widths.  w is 8, 16, 32 or 64 (the paper's f_8 .. f_64, Section 5).
- *     The byte-length and batch forms also accept w = 1, 2, 4 (w = 1 is the
- *     ordinary population count).
+ *     The byte-length, batch, gather and serving forms also accept w = 1, 2,
+ *     4 (w = 1 is the ordinary population count), and pospopcnt_async and
+ *     pospopcnt_host the wider folds w = 128 and 256 (Section 4's general
+ *     maximum word size; counters then hold 128 or 256 entries).
  *   - Memory.  Unless a function says otherwise, pointers are DEVICE
  *     pointers of the current CUDA device (cudaMalloc, PyTorch tensors,
  *     cudaMallocManaged or pinned host memory that the device can address).
@@ -102,6 +104,32 @@ int pospopcnt_async(int w, uint64_t *counts, const void *bytes, size_t nbytes, v
  */
 int pospopcnt_batch(int w, uint64_t *counts, const void *base, const uint64_t *offsets,
                     size_t m, void *stream);
+
+/*
+ * Gathered regions (Section 4, step 1 and its footnote: leaving the
+ * counters uncleared lets non-contiguous memory regions be counted into one
+ * counter array): counts[0..w-1] += the counts of the n regions
+ * [ptrs[r], ptrs[r] + lens[r]), each counted as its own word stream (its
+ * start fixes its word phase; a trailing partial word is zero-padded).
+ * ptrs and lens are DEVICE arrays of n uint64_t; every region must be
+ * device-addressable (it is read by the kernel, not checked on the host).
+ * Same planning and persistent counting as pospopcnt_batch, and the same
+ * per-stream workspace.
+ */
+int pospopcnt_gather(int w, uint64_t *counts, const uint64_t *ptrs, const uint64_t *lens,
+                     size_t n, void *stream);
+
+/*
+ * Word-selected count (Section 1's GROUP BY count with a WHERE filter):
+ * counts[j] += number of words i < n with bit i of `select` set and bit j
+ * of word i set, w = 8, 16, 32 or 64.  Bit i of the selection bitmap is bit
+ * i % 8 of byte i / 8; the bitmap is read in whole 32-bit words, so
+ * 4 * ceil(n / 32) bytes must be readable (bits past n are ignored).
+ * `words` must be aligned to the word size and `select` to 4 bytes (else
+ * POSPOP_EINVAL).  Device pointers, asynchronous on `stream`.
+ */
+int pospopcnt_masked(int w, uint64_t *counts, const void *words, size_t n, const void *select,
+                     void *stream);
 
 /*
  * pospopcnt_batch for callers that cannot allocate device memory: code

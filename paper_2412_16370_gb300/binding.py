@@ -50,6 +50,8 @@ _SIGNATURES = {
     "pospopcnt_async": ([_int, _vp, _vp, _sz, _vp], _int),
     "pospopcnt_batch": ([_int, _vp, _vp, _vp, _sz, _vp], _int),
     "pospopcnt_batch_noalloc": ([_int, _vp, _vp, _vp, _sz, _vp], _int),
+    "pospopcnt_gather": ([_int, _vp, _vp, _vp, _sz, _vp], _int),
+    "pospopcnt_masked": ([_int, _vp, _vp, _sz, _vp, _vp], _int),
     "pospopcnt_batch_status": ([_vp], _int),
     "pospopcnt_reserve": ([_sz, _vp], _int),
     "pospopcnt_host": ([_int, _vp, _vp, _sz], _int),
@@ -192,6 +194,20 @@ def pospopcnt_batch_noalloc(w: int, counts, base, offsets, m=None, stream=None):
         m = offsets.numel() - 1 if hasattr(offsets, "numel") else len(offsets) - 1
     return _check(lib().pospopcnt_batch_noalloc(w, _ptr(counts), _ptr(base), _ptr(offsets), m,
                                                 _stream(stream)))
+
+
+def pospopcnt_gather(w: int, counts, ptrs, lens, n=None, stream=None):
+    """Count n device regions (device arrays of start addresses and lengths) into one counter array."""
+    if n is None:
+        n = ptrs.numel() if hasattr(ptrs, "numel") else len(ptrs)
+    return _check(lib().pospopcnt_gather(w, _ptr(counts), _ptr(ptrs), _ptr(lens), n,
+                                         _stream(stream)))
+
+
+def pospopcnt_masked(w: int, counts, words, n: int, select, stream=None):
+    """Count the n words whose bit in the selection bitmap is set (device pointers)."""
+    return _check(lib().pospopcnt_masked(w, _ptr(counts), _ptr(words), n, _ptr(select),
+                                         _stream(stream)))
 
 
 def pospopcnt_batch_status(stream=None) -> int:

@@ -6,6 +6,7 @@
 // pospop_batch.cu; this file only validates, plans and enqueues.
 #include <dlfcn.h>
 
+#include <algorithm>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -26,6 +27,23 @@ void note_launches(uint64_t n) { g_launches.fetch_add(n, std::memory_order_relax
 
 static bool valid_w(int w) {
   return w == 1 || w == 2 || w == 4 || w == 8 || w == 16 || w == 32 || w == 64;
+}
+
+// The single-array forms also take the wider folds.
+static bool valid_w_single(int w) { return valid_w(w) || w == 128 || w == 256; }
+
+// Index in a kernel family (stride `step`) of the variant launched with the
+// same block shape as `want` -- a kernel must be launched with the block size
+// it was compiled for -- preferring the same load hint.  -1 if none.
+static int pick_shape(int count, const Variant &(*get)(int), int step, const Variant &want) {
+  int same_shape = -1;
+  for (int i = 0; i < count; i += step) {
+    const Variant &c = get(i);
+    if (c.bs != want.bs || c.minb != want.minb) continue;
+    if (c.hint == want.hint) return i;
+    if (same_shape < 0) same_shape = i;
+  }
+  return same_shape;
 }
 
 // ---------------------------------------------------------------------------
@@ -355,7 +373,13 @@ int launch_stream_with(const DevCtx &ctx, const TuneTable &t, int w, unsigned lo
   P.rot = (8u * P.s.head) & (uint32_t)(w - 1);
   const uint64_t R = (P.s.G + 31) >> 5;
   const StreamPlan pl = plan_stream(ctx, t, R);
-  const Variant &v = stream_variant(pl.variant);
+  const Variant *vp = &stream_variant(pl.variant);
+  if (w == 256) {   // the two-parity kernel with the planned block shape
+    const int pick = pick_shape(stream256_variant_count(), stream256_variant, 1, *vp);
+    if (pick < 0) return POSPOP_EINVAL;
+    vp = &stream256_variant(pick);
+  }
+  const Variant &v = *vp;
   for (uint64_t rb = 0; rb < R; rb += pl.rows_per_launch) {
     P.row_begin = rb;
     P.row_end = (R - rb > pl.rows_per_launch) ? rb + pl.rows_per_launch : R;
@@ -494,6 +518,8 @@ int launch_batch_with(DevCtx &ctx, const TuneTable &t, int w, unsigned long long
   }
   PlanParams pp;
   pp.desc = nullptr;
+  pp.gptrs = nullptr;
+  pp.glens = nullptr;
   pp.offsets = offsets;
   pp.m = m;
   pp.base_addr = (uint64_t)base;
@@ -508,6 +534,8 @@ int launch_batch_with(DevCtx &ctx, const TuneTable &t, int w, unsigned long long
 
   BatchParams bp;
   bp.desc = nullptr;
+  bp.gptrs = nullptr;
+  bp.glens = nullptr;
   bp.base = static_cast<const uint8_t *>(base);
   bp.offsets = offsets;
   bp.m = m;
@@ -537,6 +565,108 @@ int launch_batch_with(DevCtx &ctx, const TuneTable &t, int w, unsigned long long
 }
 
 // ---------------------------------------------------------------------------
+// Gathered regions and word-selected counts.
+// ---------------------------------------------------------------------------
+static int launch_gather_with(DevCtx &ctx, const TuneTable &t, int w, unsigned long long *counts,
+                              const uint64_t *ptrs, const uint64_t *lens, size_t n,
+                              cudaStream_t stream) {
+  Workspace *ws = nullptr;
+  {
+    std::lock_guard<std::mutex> g(ctx.mu);
+    const int rc = get_ws(ctx, stream, n, &ws);
+    if (rc != POSPOP_OK) return rc;
+  }
+  if (cudaMemsetAsync(ws->status, 0, sizeof(int), stream) != cudaSuccess) {
+    cudaGetLastError();
+    return POSPOP_ECUDA;
+  }
+  PlanParams pp;
+  memset(&pp, 0, sizeof pp);
+  pp.gptrs = ptrs;
+  pp.glens = lens;
+  pp.m = n;
+  pp.item_start = ws->item_start;
+  pp.block_sum = ws->block_sum;
+  pp.next = ws->next;
+  pp.status = ws->status;
+  pp.item_rows = t.batch.item_rows;
+  pp.nblocks = (uint32_t)((n + kPlanChunk - 1) / kPlanChunk);
+  void *pargs[] = {&pp};
+  if (cudaLaunchKernel(plan_items_gather_fn(), dim3(pp.nblocks), dim3(kPlanThreads), pargs, 0,
+                       stream) != cudaSuccess ||
+      cudaLaunchKernel(plan_scan_fn(), dim3(1), dim3(kPlanThreads), pargs, 0, stream) !=
+          cudaSuccess ||
+      cudaLaunchKernel(plan_apply_fn(), dim3(pp.nblocks), dim3(kPlanThreads), pargs, 0, stream) !=
+          cudaSuccess) {
+    cudaGetLastError();
+    return POSPOP_ECUDA;
+  }
+  BatchParams bp;
+  memset(&bp, 0, sizeof bp);
+  bp.gptrs = ptrs;
+  bp.glens = lens;
+  bp.m = n;
+  bp.counts = counts;
+  bp.w = w;
+  bp.item_start = ws->item_start;
+  bp.next = ws->next;
+  bp.status = ws->status;
+  bp.item_rows = t.batch.item_rows;
+  bp.grab = t.batch.grab;
+  const Variant &v = gather_variant(t.batch.variant);
+  int cps = std::min(t.batch.ctas_per_sm, ctx.occ_batch[t.batch.variant]);
+  if (cps < 1) cps = 1;
+  void *bargs[] = {&bp};
+  if (cudaLaunchKernel(v.fn, dim3((unsigned)(ctx.sms * cps)), dim3(v.bs), bargs, 0, stream) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    return POSPOP_ECUDA;
+  }
+  note_launches(4);
+  return POSPOP_OK;
+}
+
+static int launch_select_with(const DevCtx &ctx, const TuneTable &t, int w,
+                              unsigned long long *counts, const void *words, size_t n,
+                              const void *select, cudaStream_t stream) {
+  const uint64_t W = (uint64_t)w / 8;
+  const uint64_t nbytes = n * W;
+  const uint64_t p0 = (uint64_t)words, e = p0 + nbytes;
+  SelectParams Q;
+  StreamParams &P = Q.sp;
+  const uint64_t A = p0 & ~15ull;
+  P.s.A = reinterpret_cast<const uint8_t *>(A);
+  P.s.head = (uint32_t)(p0 - A);
+  P.s.G = (((e + 15u) & ~15ull) - A) >> 4;
+  P.s.tail = (uint32_t)(e - (A + 16u * (P.s.G - 1)));
+  P.counts = counts;
+  P.w = w;
+  P.rot = (8u * P.s.head) & (uint32_t)(w - 1);
+  Q.bits = static_cast<const uint8_t *>(select);
+  Q.nbits = n;
+  Q.nbytes = 4 * ((n + 31) / 32);
+  Q.wlog = w == 8 ? 0u : w == 16 ? 1u : w == 32 ? 2u : 3u;
+  const uint64_t R = (P.s.G + 31) >> 5;
+  const StreamPlan pl = plan_stream(ctx, t, R);
+  // the selection kernels come in the tune table's block shapes (flush depth
+  // 16), four word sizes each; take the planned block shape
+  const int shape = pick_shape(select_variant_count(), select_variant, 4, stream_variant(pl.variant));
+  if (shape < 0) return POSPOP_EINVAL;
+  const Variant &v = select_variant(shape + (int)Q.wlog);
+  for (uint64_t rb = 0; rb < R; rb += pl.rows_per_launch) {
+    P.row_begin = rb;
+    P.row_end = (R - rb > pl.rows_per_launch) ? rb + pl.rows_per_launch : R;
+    void *args[] = {&Q};
+    if (cudaLaunchKernel(v.fn, dim3(pl.grid), dim3(pl.block), args, 0, stream) != cudaSuccess) {
+      cudaGetLastError();
+      return POSPOP_ECUDA;
+    }
+    note_launches(1);
+  }
+  return POSPOP_OK;
+}
+
+// ---------------------------------------------------------------------------
 // Host-memory path.
 // ---------------------------------------------------------------------------
 static int ensure_staging(DevCtx &ctx) {
@@ -544,8 +674,8 @@ static int ensure_staging(DevCtx &ctx) {
   if (st.ready) return POSPOP_OK;
   bool ok = cudaStreamCreateWithFlags(&st.copy, cudaStreamNonBlocking) == cudaSuccess &&
             cudaStreamCreateWithFlags(&st.comp, cudaStreamNonBlocking) == cudaSuccess &&
-            cudaMalloc(&st.dcounts, 64 * sizeof(unsigned long long)) == cudaSuccess &&
-            cudaMallocHost(&st.hcounts, 64 * sizeof(unsigned long long)) == cudaSuccess;
+            cudaMalloc(&st.dcounts, 256 * sizeof(unsigned long long)) == cudaSuccess &&
+            cudaMallocHost(&st.hcounts, 256 * sizeof(unsigned long long)) == cudaSuccess;
   for (int b = 0; ok && b < kStageBufs; b++)
     ok = cudaMalloc(&st.buf[b], kStageChunk) == cudaSuccess &&
          cudaEventCreateWithFlags(&st.copied[b], cudaEventDisableTiming) == cudaSuccess &&
@@ -573,7 +703,7 @@ static int host_count(DevCtx &ctx, int w, uint64_t *counts, const void *bytes, s
     std::lock_guard<std::mutex> g2(ctx.mu);
     t = ctx.tune;
   }
-  if (cudaMemsetAsync(st.dcounts, 0, 64 * sizeof(unsigned long long), st.comp) != cudaSuccess) {
+  if (cudaMemsetAsync(st.dcounts, 0, 256 * sizeof(unsigned long long), st.comp) != cudaSuccess) {
     cudaGetLastError();
     return POSPOP_ECUDA;
   }
@@ -662,7 +792,7 @@ void pospopcnt_shutdown(void) {
 }
 
 int pospopcnt_async(int w, uint64_t *counts, const void *bytes, size_t nbytes, void *stream) {
-  if (!valid_w(w)) return POSPOP_EINVAL;
+  if (!valid_w_single(w)) return POSPOP_EINVAL;
   if (nbytes == 0) return POSPOP_OK;
   if (!counts || !bytes) return POSPOP_EINVAL;
   int rc = POSPOP_OK;
@@ -735,6 +865,53 @@ int pospopcnt_batch(int w, uint64_t *counts, const void *base, const uint64_t *o
                            static_cast<cudaStream_t>(stream));
 }
 
+int pospopcnt_gather(int w, uint64_t *counts, const uint64_t *ptrs, const uint64_t *lens,
+                     size_t n, void *stream) {
+  if (!valid_w(w)) return POSPOP_EINVAL;
+  if (n == 0) return POSPOP_OK;
+  if (!counts || !ptrs || !lens) return POSPOP_EINVAL;
+  if (n > (SIZE_MAX / 8) / 64 - 1) return POSPOP_ERANGE;
+  int rc = POSPOP_OK;
+  DevCtx *c = current_ctx(&rc);
+  if (!c) return rc;
+  const void *dc = nullptr, *dp = nullptr, *dl = nullptr;
+  if (!device_addressable(counts, c->device, &dc) || !device_addressable(ptrs, c->device, &dp) ||
+      !device_addressable(lens, c->device, &dl))
+    return POSPOP_EPTR;
+  TuneTable t;
+  {
+    std::lock_guard<std::mutex> g(c->mu);
+    t = c->tune;
+  }
+  return launch_gather_with(*c, t, w, (unsigned long long *)const_cast<void *>(dc),
+                            static_cast<const uint64_t *>(dp), static_cast<const uint64_t *>(dl), n,
+                            static_cast<cudaStream_t>(stream));
+}
+
+int pospopcnt_masked(int w, uint64_t *counts, const void *words, size_t n, const void *select,
+                     void *stream) {
+  if (!(w == 8 || w == 16 || w == 32 || w == 64)) return POSPOP_EINVAL;
+  if (n == 0) return POSPOP_OK;
+  if (!counts || !words || !select) return POSPOP_EINVAL;
+  const size_t W = (size_t)w / 8;
+  if (((uintptr_t)words % W) != 0 || ((uintptr_t)select % 4) != 0) return POSPOP_EINVAL;
+  if (n > SIZE_MAX / W) return POSPOP_ERANGE;
+  int rc = POSPOP_OK;
+  DevCtx *c = current_ctx(&rc);
+  if (!c) return rc;
+  const void *dc = nullptr, *dw = nullptr, *ds = nullptr;
+  if (!device_addressable(counts, c->device, &dc) || !device_addressable(words, c->device, &dw) ||
+      !device_addressable(select, c->device, &ds))
+    return POSPOP_EPTR;
+  TuneTable t;
+  {
+    std::lock_guard<std::mutex> g(c->mu);
+    t = c->tune;
+  }
+  return launch_select_with(*c, t, w, (unsigned long long *)const_cast<void *>(dc), dw, n, ds,
+                            static_cast<cudaStream_t>(stream));
+}
+
 int pospopcnt_batch_status(void *stream) {
   int rc = POSPOP_OK;
   DevCtx *c = current_ctx(&rc);
@@ -770,7 +947,7 @@ int pospopcnt_reserve(size_t m_max, void *stream) {
 }
 
 int pospopcnt_host(int w, uint64_t *counts, const void *bytes, size_t nbytes) {
-  if (!valid_w(w)) return POSPOP_EINVAL;
+  if (!valid_w_single(w)) return POSPOP_EINVAL;
   if (nbytes == 0) return POSPOP_OK;
   if (!counts || !bytes) return POSPOP_EINVAL;
   int rc = POSPOP_OK;
@@ -798,7 +975,7 @@ int pospopcnt_roofline_read(const void *bytes, size_t nbytes, uint64_t *sum, voi
 }
 
 int pospopcnt_plan(int w, size_t nbytes, uint32_t plan[8]) {
-  if (!valid_w(w) || !plan) return POSPOP_EINVAL;
+  if (!valid_w_single(w) || !plan) return POSPOP_EINVAL;
   int rc = POSPOP_OK;
   DevCtx *c = current_ctx(&rc);
   if (!c) return rc;

@@ -52,14 +52,14 @@ __global__ void __launch_bounds__(kPlanThreads) plan_apply_kernel(PlanParams P) 
 }
 
 #define POSPOP_BV(BS, MINB, D, H) \
-  Variant{reinterpret_cast<const void *>(&batch_kernel<false, BS, MINB, D, H>), BS, MINB, D, H}
+  Variant{reinterpret_cast<const void *>(&batch_kernel<kSrcCsr, BS, MINB, D, H>), BS, MINB, D, H}
 
 static const Variant kBatch[] = {POSPOP_FAMILY(POSPOP_BV)};
 
 int batch_variant_count() { return (int)(sizeof(kBatch) / sizeof(kBatch[0])); }
 const Variant &batch_variant(int i) { return kBatch[i]; }
 
-const void *plan_items_fn() { return reinterpret_cast<const void *>(&plan_items_kernel<false>); }
+const void *plan_items_fn() { return reinterpret_cast<const void *>(&plan_items_kernel<kSrcCsr>); }
 const void *plan_scan_fn() { return reinterpret_cast<const void *>(&plan_scan_kernel); }
 const void *plan_apply_fn() { return reinterpret_cast<const void *>(&plan_apply_kernel); }
 

@@ -1,8 +1,9 @@
 // pospop_batch.cuh -- batched counting over many arrays: planning kernels
 // (work items per array, prefix sums) and the persistent counting kernel.
 // Templated on the array source: CSR byte offsets from one base with one w
-// (pospopcnt_batch), or per-array descriptors with their own pointer,
-// length, w and output row (the serving loop's mixed batches).
+// (pospopcnt_batch), per-array descriptors with their own pointer, length,
+// w and output row (the serving loop's mixed batches), or gathered regions
+// all counted into one counter array (pospopcnt_gather).
 #pragma once
 
 #include <cstdint>
@@ -13,22 +14,26 @@
 namespace pospop {
 
 // Byte range [s, e) of array a, its width and its output counters.
-template <bool DESC>
 struct ArrayRef {
   uint64_t s, e;
   int w;
   unsigned long long *out;
 };
 
-template <bool DESC>
-__device__ __forceinline__ ArrayRef<DESC> array_ref(const BatchParams &P, uint64_t a) {
-  ArrayRef<DESC> r;
-  if (DESC) {
+template <int SRC>
+__device__ __forceinline__ ArrayRef array_ref(const BatchParams &P, uint64_t a) {
+  ArrayRef r;
+  if (SRC == kSrcDesc) {
     const Desc d = P.desc[a];
     r.s = (uint64_t)d.ptr;
     r.e = r.s + d.nbytes;
     r.w = d.w;
     r.out = d.out;
+  } else if (SRC == kSrcGather) {
+    r.s = __ldg(P.gptrs + a);
+    r.e = r.s + __ldg(P.glens + a);
+    r.w = P.w;
+    r.out = P.counts;
   } else {
     const uint64_t base = (uint64_t)P.base;
     r.s = base + __ldg(P.offsets + a);
@@ -76,7 +81,7 @@ __device__ __forceinline__ uint64_t block_inclusive_scan(uint64_t v, uint64_t *w
   return v;
 }
 
-template <bool DESC>
+template <int SRC>
 __global__ void __launch_bounds__(kPlanThreads) plan_items_kernel(PlanParams P) {
   __shared__ uint64_t red[32];
   const uint64_t a0 = (uint64_t)blockIdx.x * kPlanChunk + (uint64_t)threadIdx.x * kPlanPerThread;
@@ -87,9 +92,12 @@ __global__ void __launch_bounds__(kPlanThreads) plan_items_kernel(PlanParams P) 
     const uint64_t a = a0 + k;
     if (a < P.m) {
       uint64_t s, e;
-      if (DESC) {
+      if (SRC == kSrcDesc) {
         s = (uint64_t)P.desc[a].ptr;
         e = s + P.desc[a].nbytes;
+      } else if (SRC == kSrcGather) {
+        s = P.gptrs[a];
+        e = s + P.glens[a];
       } else {
         const uint64_t o0 = P.offsets[a], o1 = P.offsets[a + 1];
         if (o1 < o0) bad = true;
@@ -156,8 +164,15 @@ __device__ __forceinline__ void signal_if_last(const BatchParams &P, uint64_t a,
   }
 }
 
-template <bool DESC, int BS, int MINB, int DEPTH, int HINT>
+template <int SRC, int BS, int MINB, int DEPTH, int HINT>
 __global__ void __launch_bounds__(BS, MINB) batch_kernel(BatchParams P) {
+  // Gathered regions all add into one counter array: accumulate per block in
+  // shared memory, one atomic per counter per block at the end.
+  __shared__ unsigned long long gacc[SRC == kSrcGather ? 64 : 1];
+  if (SRC == kSrcGather) {
+    if (threadIdx.x < 64) gacc[threadIdx.x] = 0ull;
+    __syncthreads();
+  }
   if (*P.status != 0) return;   // planning rejected the offsets: change nothing
   const unsigned lane = threadIdx.x & 31u;
   const Xpose xk = make_xpose(lane);
@@ -172,7 +187,7 @@ __global__ void __launch_bounds__(BS, MINB) batch_kernel(BatchParams P) {
     for (uint64_t i = i0; i < i1; i++) {
       while (__ldg(P.item_start + a + 1) <= i) a++;
       const uint64_t k = i - __ldg(P.item_start + a);
-      const ArrayRef<DESC> r = array_ref<DESC>(P, a);
+      const ArrayRef r = array_ref<SRC>(P, a);
       Span s;
       const uint64_t A = r.s & ~15ull;
       s.A = reinterpret_cast<const uint8_t *>(A);
@@ -184,13 +199,23 @@ __global__ void __launch_bounds__(BS, MINB) batch_kernel(BatchParams P) {
       const uint64_t r0 = k * P.item_rows;
       const uint64_t r1 = (r0 + P.item_rows < R) ? r0 + P.item_rows : R;
       uint32_t cnt[4] = {0u, 0u, 0u, 0u};
-      count_rows<DEPTH, HINT>(s, r0, 1, r1 - r0, lane, xk, cnt);
+      count_rows<DEPTH, HINT>(s, r0, 1, r1 - r0, lane, xk, cnt, PlainLoader<HINT>{});
       unsigned long long *out = r.out;
-      fold_counts(cnt, r.w, rot, lane, [&](uint32_t j, unsigned long long v) {
-        if (v) atomicAdd(out + j, v);
-      });
-      if (DESC && P.remaining) signal_if_last(P, a, r.w, out, lane);
+      if (SRC == kSrcGather) {
+        fold_counts(cnt, r.w, rot, lane, [&](uint32_t j, unsigned long long v) {
+          if (v) atomicAdd(&gacc[j], v);
+        });
+      } else {
+        fold_counts(cnt, r.w, rot, lane, [&](uint32_t j, unsigned long long v) {
+          if (v) atomicAdd(out + j, v);
+        });
+      }
+      if (SRC == kSrcDesc && P.remaining) signal_if_last(P, a, r.w, out, lane);
     }
+  }
+  if (SRC == kSrcGather) {
+    __syncthreads();
+    if ((int)threadIdx.x < P.w && gacc[threadIdx.x]) atomicAdd(P.counts + threadIdx.x, gacc[threadIdx.x]);
   }
 }
 

@@ -7,13 +7,13 @@
 namespace pospop {
 
 #define POSPOP_DV(BS, MINB, D, H) \
-  Variant{reinterpret_cast<const void *>(&batch_kernel<true, BS, MINB, D, H>), BS, MINB, D, H}
+  Variant{reinterpret_cast<const void *>(&batch_kernel<kSrcDesc, BS, MINB, D, H>), BS, MINB, D, H}
 
 static const Variant kDesc[] = {POSPOP_FAMILY(POSPOP_DV)};
 
 int desc_variant_count() { return (int)(sizeof(kDesc) / sizeof(kDesc[0])); }
 const Variant &desc_variant(int i) { return kDesc[i]; }
 
-const void *plan_items_desc_fn() { return reinterpret_cast<const void *>(&plan_items_kernel<true>); }
+const void *plan_items_desc_fn() { return reinterpret_cast<const void *>(&plan_items_kernel<kSrcDesc>); }
 
 }  // namespace pospop

@@ -175,6 +175,24 @@ __device__ __forceinline__ void flush_plane(uint32_t cnt[4], const V4 &v, const 
   for (int r = 0; r < 4; r++) cnt[r] += xpose_popc(v.x[r], k) << SHIFT;
 }
 
+// Flush for w = 256, where a word spans two granules: granule g's bits
+// belong to word half g mod 2, and g mod 2 is the lane's parity (rows start
+// at even granules), so even and odd lanes are transposed and counted apart.
+template <int SHIFT, bool PAR2>
+__device__ __forceinline__ void flush_par(uint32_t cnt[4], uint32_t cnt_odd[4], const V4 &v,
+                                          const Xpose &k, unsigned lane) {
+  if (PAR2) {
+    const uint32_t odd = 0u - (lane & 1u);
+#pragma unroll
+    for (int r = 0; r < 4; r++) {
+      cnt[r] += xpose_popc(v.x[r] & ~odd, k) << SHIFT;
+      cnt_odd[r] += xpose_popc(v.x[r] & odd, k) << SHIFT;
+    }
+  } else {
+    flush_plane<SHIFT>(cnt, v, k);
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Loads.
 // ---------------------------------------------------------------------------
@@ -224,15 +242,136 @@ __device__ __forceinline__ V4 load_granule_masked(const Span &s, uint64_t g) {
 }
 
 // ---------------------------------------------------------------------------
+// Loader policies.  count_rows fetches granules through a loader: `fast`
+// for granules known to lie wholly inside the span, `edge` for any granule
+// (bytes outside the span read as zero).  PlainLoader is the plain count;
+// SelectLoader (below) also applies a word-selection bitmap.
+// ---------------------------------------------------------------------------
+template <int HINT>
+struct PlainLoader {
+  __device__ __forceinline__ V4 fast(const uint8_t *p, uint64_t) const { return ldg_granule<HINT>(p); }
+  __device__ __forceinline__ V4 edge(const Span &s, uint64_t g) const {
+    return load_granule_masked<HINT>(s, g);
+  }
+};
+
+// Word selection (the WHERE bitmap of a GROUP BY count, Section 1): bit i of
+// the bitmap (least significant bit of byte i/8 first) selects word i of the
+// span, whose start is a multiple of the word size W = 2^WLOG bytes.
+struct Selection {
+  const uint8_t *bits;   // bitmap, 4-byte aligned, ceil(nbits / 32) readable 32-bit words
+  uint64_t nbits;        // words in the span (selection bits that count)
+  uint64_t nbytes;       // readable bytes of the bitmap (4 * ceil(nbits / 32))
+  uint32_t h;            // words before the start in granule 0 (span head / W)
+};
+
+// 32 bitmap bits starting at bit 32q (bits past the readable bytes read as 0).
+__device__ __forceinline__ uint32_t sel_word(const Selection &m, uint64_t q) {
+  const uint64_t b0 = 4 * q;
+  if (b0 + 4 <= m.nbytes) return __ldg(reinterpret_cast<const uint32_t *>(m.bits) + q);
+  uint32_t v = 0;
+  for (uint64_t b = b0; b < m.nbytes && b < b0 + 4; b++) v |= (uint32_t)__ldg(m.bits + b) << (8 * (b - b0));
+  return v;
+}
+
+// Selection bits of granule g: bit t (t < 16 / W) selects the word that
+// occupies bytes [t W, (t + 1) W) of the granule.
+template <int WLOG>
+__device__ __forceinline__ uint32_t granule_selection(const Selection &m, uint64_t g) {
+  constexpr uint32_t CNT = 16u >> WLOG;
+  constexpr uint32_t ALL = (1u << CNT) - 1u;
+  const uint64_t gb = g * CNT;
+  uint32_t bits;
+  uint64_t lo;
+  uint32_t lead;   // selection slots before the start (granule 0 only)
+  if (gb >= m.h) {
+    lo = gb - m.h;
+    lead = 0;
+  } else {
+    lo = 0;
+    lead = (uint32_t)(m.h - gb);
+  }
+  const uint64_t q = lo >> 5;
+  const uint32_t sh = (uint32_t)lo & 31u;
+  const uint32_t w0 = sel_word(m, q);
+  const uint32_t w1 = (sh + CNT > 32u) ? sel_word(m, q + 1) : 0u;
+  bits = __funnelshift_r(w0, w1, sh) << lead;
+  if (lo + CNT > m.nbits + lead) {   // selection bits past the last word do not count
+    const uint64_t keep = (m.nbits > lo ? m.nbits - lo : 0) + lead;
+    if (keep < 32) bits &= (1u << (uint32_t)keep) - 1u;
+  }
+  return bits & ALL;
+}
+
+// Byte mask of one 32-bit lane from its selection bits.  prmt with the
+// sign-replicate selector copies bit 7 of a chosen byte over the whole byte,
+// so the selection bits are first moved (one multiply, no carries since the
+// shifted copies do not overlap) to bit 7 of the bytes they cover.
+template <int WLOG>
+__device__ __forceinline__ uint32_t lane_mask(uint32_t bits, int r) {
+  uint32_t e;
+  if (WLOG == 0) {          // w = 8: bit k of the nibble -> byte k
+    const uint32_t t = ((bits >> (4 * r)) & 0xfu) * 0x10204080u;
+    asm("prmt.b32 %0, %1, 0, 0xBA98;" : "=r"(e) : "r"(t));
+  } else if (WLOG == 1) {   // w = 16: bit k of the pair -> 16-bit half k
+    const uint32_t t = ((bits >> (2 * r)) & 0x3u) * 0x40008000u;
+    asm("prmt.b32 %0, %1, 0, 0xBB99;" : "=r"(e) : "r"(t));
+  } else if (WLOG == 2) {   // w = 32: one bit per lane
+    e = 0u - ((bits >> r) & 1u);
+  } else {                  // w = 64: one bit per two lanes
+    e = 0u - ((bits >> (r >> 1)) & 1u);
+  }
+  return e;
+}
+
+template <int WLOG>
+__device__ __forceinline__ void apply_selection(V4 &v, uint32_t bits) {
+#pragma unroll
+  for (int r = 0; r < 4; r++) v.x[r] &= lane_mask<WLOG>(bits, r);
+}
+
+// Selection bits of an interior granule (not granule 0, not in the last
+// row): all its words lie inside the span, so the window needs no clipping,
+// and both bitmap words are read unconditionally (the second index clamped
+// to the last word) -- no control flow between a group's loads.
+template <int WLOG>
+__device__ __forceinline__ uint32_t interior_selection(const Selection &m, uint64_t g) {
+  constexpr uint32_t CNT = 16u >> WLOG;
+  const uint64_t lo = g * CNT - m.h;
+  const uint64_t q = lo >> 5;
+  const uint64_t last = (m.nbytes >> 2) - 1;
+  const uint32_t *b32 = reinterpret_cast<const uint32_t *>(m.bits);
+  const uint32_t w0 = __ldg(b32 + q);
+  const uint32_t w1 = __ldg(b32 + (q + 1 < last ? q + 1 : last));
+  return __funnelshift_r(w0, w1, (uint32_t)lo & 31u) & ((1u << CNT) - 1u);
+}
+
+template <int HINT, int WLOG>
+struct SelectLoader {
+  Selection m;
+  __device__ __forceinline__ V4 fast(const uint8_t *p, uint64_t g) const {
+    V4 v = ldg_granule<HINT>(p);
+    apply_selection<WLOG>(v, interior_selection<WLOG>(m, g));
+    return v;
+  }
+  __device__ __forceinline__ V4 edge(const Span &s, uint64_t g) const {
+    V4 v = load_granule_masked<HINT>(s, g);
+    if (g < s.G) apply_selection<WLOG>(v, granule_selection<WLOG>(m, g));
+    return v;
+  }
+};
+
+// ---------------------------------------------------------------------------
 // The per-thread algorithm (Section 4, steps 2-7) over a sequence of rows
 // row0, row0 + stride, ..., nrows of them.  Lane `lane` handles granule
 // 32 * row + lane of each row.  Adds the warp-wide counts of granule bit
 // positions 32r + lane (r = 0..3) into cnt[r].  Warp-uniform control flow.
 // ---------------------------------------------------------------------------
-template <int DEPTH, int HINT>
+template <int DEPTH, int HINT, class Loader, bool PAR2 = false>
 __device__ __forceinline__ void count_rows(const Span &s, uint64_t row0, uint64_t stride,
                                            uint64_t nrows, unsigned lane, const Xpose &xk,
-                                           uint32_t cnt[4]) {
+                                           uint32_t cnt[4], const Loader &ld,
+                                           uint32_t *cnt_odd = nullptr) {
   if (nrows == 0) return;
   const uint64_t R = span_rows(s);
   const uint64_t gstride = stride * 32u;          // granules between consecutive rows
@@ -242,8 +381,8 @@ __device__ __forceinline__ void count_rows(const Span &s, uint64_t row0, uint64_
     // Short sequence (Section 4.6): too few vectors for a CSA network to pay;
     // count every vector directly.
     for (uint64_t i = 0; i < nrows; i++, g += gstride) {
-      const V4 v = load_granule_masked<HINT>(s, g);
-      flush_plane<0>(cnt, v, xk);
+      const V4 v = ld.edge(s, g);
+      flush_par<0, PAR2>(cnt, cnt_odd, v, xk, lane);
     }
     return;
   }
@@ -255,8 +394,7 @@ __device__ __forceinline__ void count_rows(const Span &s, uint64_t row0, uint64_
     V4 v[15];
 #pragma unroll
     for (int i = 0; i < 15; i++)
-      v[i] = ((uint64_t)i < nrows) ? load_granule_masked<HINT>(s, g + (uint64_t)i * gstride)
-                                   : v4_zero();
+      v[i] = ((uint64_t)i < nrows) ? ld.edge(s, g + (uint64_t)i * gstride) : v4_zero();
     csa15(p, v);
   }
   p.a16 = v4_zero();
@@ -277,10 +415,11 @@ __device__ __forceinline__ void count_rows(const Span &s, uint64_t row0, uint64_
         V4 v[16];
         if (interior) {
 #pragma unroll
-          for (int k = 0; k < 16; k++) v[k] = ldg_granule<HINT>(ptr + (uint64_t)k * pstep);
+          for (int k = 0; k < 16; k++)
+            v[k] = ld.fast(ptr + (uint64_t)k * pstep, g + (uint64_t)k * gstride);
         } else {
 #pragma unroll
-          for (int k = 0; k < 16; k++) v[k] = load_granule_masked<HINT>(s, g + (uint64_t)k * gstride);
+          for (int k = 0; k < 16; k++) v[k] = ld.edge(s, g + (uint64_t)k * gstride);
         }
         x = csa16(p, v);
       }
@@ -288,17 +427,17 @@ __device__ __forceinline__ void count_rows(const Span &s, uint64_t row0, uint64_
         V4 v[16];
         if (interior) {
 #pragma unroll
-          for (int k = 0; k < 16; k++) v[k] = ldg_granule<HINT>(ptr + (uint64_t)(16 + k) * pstep);
+          for (int k = 0; k < 16; k++)
+            v[k] = ld.fast(ptr + (uint64_t)(16 + k) * pstep, g + (uint64_t)(16 + k) * gstride);
         } else {
 #pragma unroll
-          for (int k = 0; k < 16; k++)
-            v[k] = load_granule_masked<HINT>(s, g + (uint64_t)(16 + k) * gstride);
+          for (int k = 0; k < 16; k++) v[k] = ld.edge(s, g + (uint64_t)(16 + k) * gstride);
         }
         y = csa16(p, v);
       }
       V4 a32;
       fa(p.a16, a32, p.a16, x, y);
-      flush_plane<5>(cnt, a32, xk);
+      flush_par<5, PAR2>(cnt, cnt_odd, a32, xk, lane);
     }
   }
   for (; i < nrows; i += 16, g += 16u * gstride, ptr += 16u * pstep) {
@@ -308,30 +447,41 @@ __device__ __forceinline__ void count_rows(const Span &s, uint64_t row0, uint64_
     V4 v[16];
     if (interior) {
 #pragma unroll
-      for (int k = 0; k < 16; k++) v[k] = ldg_granule<HINT>(ptr + (uint64_t)k * pstep);
+      for (int k = 0; k < 16; k++) v[k] = ld.fast(ptr + (uint64_t)k * pstep, g + (uint64_t)k * gstride);
     } else {
       // Tail (Section 4.6): rows past the sequence and bytes past the end are zero.
 #pragma unroll
       for (int k = 0; k < 16; k++)
-        v[k] = (i + (uint64_t)k < nrows) ? load_granule_masked<HINT>(s, g + (uint64_t)k * gstride)
-                                         : v4_zero();
+        v[k] = (i + (uint64_t)k < nrows) ? ld.edge(s, g + (uint64_t)k * gstride) : v4_zero();
     }
     const V4 a16 = csa16(p, v);
     if (DEPTH == 32) {
       V4 a32;
       ha(p.a16, a32, p.a16, a16);
-      flush_plane<5>(cnt, a32, xk);
+      flush_par<5, PAR2>(cnt, cnt_odd, a32, xk, lane);
     } else {
-      flush_plane<4>(cnt, a16, xk);
+      flush_par<4, PAR2>(cnt, cnt_odd, a16, xk, lane);
     }
   }
 
   // Final accumulation (Section 4.5): the carried planes with weights 8, 4, 2, 1.
-  if (DEPTH == 32) flush_plane<4>(cnt, p.a16, xk);
-  flush_plane<3>(cnt, p.a8, xk);
-  flush_plane<2>(cnt, p.a4, xk);
-  flush_plane<1>(cnt, p.a2, xk);
-  flush_plane<0>(cnt, p.a1, xk);
+  if (DEPTH == 32) flush_par<4, PAR2>(cnt, cnt_odd, p.a16, xk, lane);
+  flush_par<3, PAR2>(cnt, cnt_odd, p.a8, xk, lane);
+  flush_par<2, PAR2>(cnt, cnt_odd, p.a4, xk, lane);
+  flush_par<1, PAR2>(cnt, cnt_odd, p.a2, xk, lane);
+  flush_par<0, PAR2>(cnt, cnt_odd, p.a1, xk, lane);
+}
+
+// w = 256: even lanes hold word bits 0..127 of their granule's phase, odd
+// lanes bits 128..255.
+template <typename Emit>
+__device__ __forceinline__ void fold_counts_256(const uint32_t cnt[4], const uint32_t cnt_odd[4],
+                                                uint32_t rot, unsigned lane, Emit emit) {
+#pragma unroll
+  for (int r = 0; r < 4; r++) {
+    emit((32u * r + lane - rot) & 255u, (unsigned long long)cnt[r]);
+    emit((128u + 32u * r + lane - rot) & 255u, (unsigned long long)cnt_odd[r]);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -344,7 +494,10 @@ __device__ __forceinline__ void count_rows(const Span &s, uint64_t row0, uint64_
 template <typename Emit>
 __device__ __forceinline__ void fold_counts(const uint32_t cnt[4], int w, uint32_t rot,
                                             unsigned lane, Emit emit) {
-  if (w == 64) {
+  if (w == 128) {            // a granule is one word phase class: no folding
+#pragma unroll
+    for (int r = 0; r < 4; r++) emit((32u * r + lane - rot) & 127u, (unsigned long long)cnt[r]);
+  } else if (w == 64) {
     const unsigned long long v0 = (unsigned long long)cnt[0] + cnt[2];
     const unsigned long long v1 = (unsigned long long)cnt[1] + cnt[3];
     emit((lane - rot) & 63u, v0);

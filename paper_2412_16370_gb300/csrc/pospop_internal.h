@@ -35,8 +35,15 @@ struct Desc {
   int32_t reserved;
 };
 
+// Sources of a batched count (the template parameter SRC of the batch kernels).
+constexpr int kSrcCsr = 0;      // m arrays at base + offsets[a] .. base + offsets[a+1], one w
+constexpr int kSrcDesc = 1;     // per-array descriptors (pointer, length, w, output row)
+constexpr int kSrcGather = 2;   // regions ptrs[a], lens[a], all counted into one counter array
+
 struct BatchParams {
   const Desc *desc;             // descriptor batches (else CSR below)
+  const uint64_t *gptrs;        // gathered regions: start addresses (device array)
+  const uint64_t *glens;        //                   byte lengths (device array)
   const uint8_t *base;
   const uint64_t *offsets;      // m + 1 byte offsets (device)
   uint64_t m;
@@ -58,6 +65,8 @@ struct BatchParams {
 
 struct PlanParams {
   const Desc *desc;             // descriptor batches (else CSR offsets)
+  const uint64_t *gptrs;        // gathered regions
+  const uint64_t *glens;
   const uint64_t *offsets;
   uint64_t m;
   uint64_t base_addr;           // (uint64_t)base, for granule alignment
@@ -67,6 +76,16 @@ struct PlanParams {
   int *status;
   uint32_t item_rows;
   uint32_t nblocks;
+};
+
+// Word-selected single-array count (the stream kernel's parameters plus the
+// selection bitmap).
+struct SelectParams {
+  StreamParams sp;
+  const uint8_t *bits;          // selection bitmap (4-byte aligned)
+  uint64_t nbits;               // words
+  uint64_t nbytes;              // readable bitmap bytes
+  uint32_t wlog;                // log2 of the word size in bytes
 };
 
 struct RooflineParams {
@@ -91,6 +110,8 @@ constexpr int kPlanChunk = kPlanThreads * kPlanPerThread;
 
 int stream_variant_count();
 const Variant &stream_variant(int i);
+int stream256_variant_count();
+const Variant &stream256_variant(int i);
 int batch_variant_count();
 const Variant &batch_variant(int i);
 int roofline_variant_count();
@@ -98,6 +119,11 @@ const Variant &roofline_variant(int i);
 
 int desc_variant_count();
 const Variant &desc_variant(int i);
+int gather_variant_count();
+const Variant &gather_variant(int i);
+int select_variant_count();
+const Variant &select_variant(int i);
+const void *plan_items_gather_fn();
 
 const void *plan_items_fn();
 const void *plan_items_desc_fn();

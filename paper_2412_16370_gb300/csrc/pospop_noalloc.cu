@@ -112,6 +112,8 @@ extern "C" int pospopcnt_batch_noalloc(int w, uint64_t *counts, const void *base
 
   PlanParams pp;
   pp.desc = nullptr;
+  pp.gptrs = nullptr;
+  pp.glens = nullptr;
   pp.offsets = offsets;
   pp.m = m;
   pp.base_addr = (uint64_t)base;
@@ -133,6 +135,8 @@ extern "C" int pospopcnt_batch_noalloc(int w, uint64_t *counts, const void *base
 
   BatchParams bp;
   bp.desc = nullptr;
+  bp.gptrs = nullptr;
+  bp.glens = nullptr;
   bp.base = static_cast<const uint8_t *>(base);
   bp.offsets = offsets;
   bp.m = m;

@@ -28,12 +28,12 @@ __device__ __forceinline__ Span to_span(const SpanH &h) {
 // the warps' folded counters meet in shared memory; one atomic per counter
 // per block adds them to the caller's counts (step 8, f_w(C, c)).
 // ---------------------------------------------------------------------------
-template <int BS, int MINB, int DEPTH, int HINT>
+template <int BS, int MINB, int DEPTH, int HINT, bool PAR2 = false>
 __global__ void __launch_bounds__(BS, MINB) stream_kernel(StreamParams P) {
-  __shared__ unsigned long long acc[64];
+  __shared__ unsigned long long acc[256];
   const unsigned lane = threadIdx.x & 31u;
   const unsigned warp = threadIdx.x >> 5;
-  if (threadIdx.x < 64) acc[threadIdx.x] = 0ull;
+  for (int j = threadIdx.x; j < 256; j += BS) acc[j] = 0ull;
   __syncthreads();
 
   constexpr unsigned WPB = BS / 32;
@@ -44,14 +44,20 @@ __global__ void __launch_bounds__(BS, MINB) stream_kernel(StreamParams P) {
 
   const Xpose xk = make_xpose(lane);
   uint32_t cnt[4] = {0u, 0u, 0u, 0u};
-  count_rows<DEPTH, HINT>(to_span(P.s), P.row_begin + gw, NW, mine, lane, xk, cnt);
-  fold_counts(cnt, P.w, P.rot, lane, [&](uint32_t j, unsigned long long v) {
+  uint32_t cnt_odd[4] = {0u, 0u, 0u, 0u};
+  count_rows<DEPTH, HINT, PlainLoader<HINT>, PAR2>(to_span(P.s), P.row_begin + gw, NW, mine, lane,
+                                                   xk, cnt, PlainLoader<HINT>{}, cnt_odd);
+  auto to_shared = [&](uint32_t j, unsigned long long v) {
     if (v) atomicAdd(&acc[j], v);
-  });
+  };
+  if (PAR2)
+    fold_counts_256(cnt, cnt_odd, P.rot, lane, to_shared);
+  else
+    fold_counts(cnt, P.w, P.rot, lane, to_shared);
   __syncthreads();
-  if ((int)threadIdx.x < P.w) {
-    const unsigned long long v = acc[threadIdx.x];
-    if (v) atomicAdd(&P.counts[threadIdx.x], v);
+  for (int j = threadIdx.x; j < P.w; j += BS) {
+    const unsigned long long v = acc[j];
+    if (v) atomicAdd(&P.counts[j], v);
   }
 }
 
@@ -104,10 +110,18 @@ __global__ void __launch_bounds__(BS) roofline_kernel(RooflineParams P) {
   M(128, 4, 16, 0), M(128, 4, 16, 1), M(128, 4, 32, 0), M(128, 4, 32, 1)
 
 static const Variant kStream[] = {POSPOP_FAMILY(POSPOP_SV)};
+
+// w = 256 (two-parity flush): the tune table's launch shapes, flush depth 16.
+#define POSPOP_SV256(BS, MINB, H) \
+  Variant{reinterpret_cast<const void *>(&stream_kernel<BS, MINB, 16, H, true>), BS, MINB, 16, H}
+static const Variant kStream256[] = {POSPOP_SV256(512, 1, 0), POSPOP_SV256(512, 1, 1),
+                                     POSPOP_SV256(256, 2, 1), POSPOP_SV256(128, 4, 1)};
 static const Variant kRoof[] = {POSPOP_RV(256, 0), POSPOP_RV(256, 1), POSPOP_RV(512, 0),
                                 POSPOP_RV(512, 1), POSPOP_RV(1024, 0), POSPOP_RV(1024, 1)};
 
 int stream_variant_count() { return (int)(sizeof(kStream) / sizeof(kStream[0])); }
+int stream256_variant_count() { return (int)(sizeof(kStream256) / sizeof(kStream256[0])); }
+const Variant &stream256_variant(int i) { return kStream256[i]; }
 const Variant &stream_variant(int i) { return kStream[i]; }
 int roofline_variant_count() { return (int)(sizeof(kRoof) / sizeof(kRoof[0])); }
 const Variant &roofline_variant(int i) { return kRoof[i]; }

@@ -14,7 +14,7 @@ import pytest
 import torch
 
 from paper_2412_16370_gb300 import binding as pp
-from paper_2412_16370_gb300 import synth
+from paper_2412_16370_gb300 import synth, synth_device
 
 from _gpu import WORD_W, counts_np, gpu_count, to_dev
 
@@ -184,7 +184,7 @@ def test_argument_errors(gpu):
     assert L.pospopcnt_async(16, c.data_ptr(), d.data_ptr(), 0, s) == pp.POSPOP_OK
     assert L.pospopcnt_async(16, None, d.data_ptr(), 8, s) == pp.POSPOP_EINVAL
     assert L.pospopcnt_async(16, c.data_ptr(), None, 8, s) == pp.POSPOP_EINVAL
-    for bad_w in (0, 3, 12, 128):
+    for bad_w in (0, 3, 12, 96, 512):
         assert L.pospopcnt_async(bad_w, c.data_ptr(), d.data_ptr(), 8, s) == pp.POSPOP_EINVAL
     host = np.zeros(64, dtype=np.uint8)
     assert L.pospopcnt_async(16, c.data_ptr(), host.ctypes.data, 8, s) == pp.POSPOP_EPTR
@@ -208,3 +208,47 @@ def test_plan_and_launch_counter(gpu):
     assert p["rows"] == (8 << 30) // 512
     small = pp.pospopcnt_plan(16, 100)
     assert small["grid"] == 1 and small["size_class"] == 0
+
+
+@pytest.mark.parametrize("w", (128, 256))
+def test_wide_folds(gpu, orc, w):
+    """w = 128 and 256 (Section 4's general maximum word size)."""
+    rng = np.random.default_rng(w)
+    sizes = [1, 15, 16, 17, 31, 32, 33, 255, 256, 257, 511, 512, 513, 4096, 100003, 3 << 20]
+    sizes += [int(x) for x in rng.integers(1, 1 << 22, 10)]
+    for k, n in enumerate(sizes):
+        off = k % 16
+        host = synth.random_bytes(n, seed=w + k)
+        d = to_dev(host, gpu, align_pad=off)
+        assert np.array_equal(gpu_count(w, d), orc.bytes(w, host)), (w, n, off)
+    host = synth.random_bytes((5 << 20) + 77, seed=9)
+    got = np.zeros(w, dtype=np.uint64)
+    pp.pospopcnt_host(w, got, host)
+    assert np.array_equal(got, orc.bytes(w, host))
+
+
+@pytest.mark.parametrize("w", (128, 256))
+def test_wide_folds_every_shape_and_row_count(gpu, orc, tune_override, w):
+    host = synth.random_bytes((1 << 20) + 333, seed=5)
+    for bs, minb, hint in ((512, 1, 0), (512, 1, 1), (256, 2, 1), (128, 4, 1)):
+        lines = [f"stream {c} {bs} {minb} 16 {hint} 1 64" for c in range(5)]
+        tune_override("\n".join(lines) + "\n")
+        dd = to_dev(host, gpu, align_pad=7)
+        assert np.array_equal(gpu_count(w, dd), orc.bytes(w, host)), (bs, hint)
+    lines = [f"stream {c} 128 4 16 1 1 1000000" for c in range(5)]
+    tune_override("\n".join(lines) + "\n")
+    for k in (1, 2, 3, 4, 15, 16, 17, 31, 32, 33, 40):
+        n = 4 * k * 512 - 5
+        h = synth.random_bytes(n, seed=k)
+        dd = to_dev(h, gpu, align_pad=k % 16)
+        assert np.array_equal(gpu_count(w, dd), orc.bytes(w, h)), (k,)
+
+
+def test_wide_folds_large(gpu, orc):
+    n = 1 << 30
+    d = torch.empty(n + 64, dtype=torch.uint8, device=gpu)
+    synth_device.random_(d, 31337)
+    data = d[3:3 + n - 11]
+    host = data.cpu().numpy()
+    for w in (128, 256):
+        assert np.array_equal(gpu_count(w, data), orc.bytes_mt(w, host, 16)), w
