@@ -79,6 +79,7 @@ TuneTable default_tune() {
   for (int c = 0; c < kClasses; c++) t.stream[c] = StreamTune{sv, 1, minrows[c]};
   t.batch = BatchTune{find_variant(true, 256, 2, 16, 1), 2, 511, 1};
   t.roof = RoofTune{find_roof_variant(512, 1), 4};
+  t.max_rows_per_warp = kMaxRowsPerWarp;
   t.source = "built-in defaults";
   return t;
 }
@@ -87,6 +88,8 @@ TuneTable default_tune() {
 //   stream <class> <bs> <minb> <depth> <hint> <ctas_per_sm> <min_rows>
 //   batch <bs> <minb> <depth> <hint> <ctas_per_sm> <item_rows> <grab>
 //   roofline <bs> <hint> <ctas_per_sm>
+//   split <max_rows_per_warp>     (1 .. 2^26; a single-array count is split into
+//                                  several launches so that no warp takes more)
 int parse_tune(const char *text, TuneTable *out) {
   TuneTable t = default_tune();
   std::string s(text);
@@ -120,6 +123,11 @@ int parse_tune(const char *text, TuneTable *out) {
       if (v < 0 || cps < 1 || ir < 1 || ir > (1u << 20) || grab < 1 || grab > 64)
         return POSPOP_EINVAL;
       t.batch = BatchTune{v, cps, ir, grab};
+    } else if (strcmp(kind, "split") == 0) {
+      unsigned long long mr;
+      if (sscanf(line.c_str(), "%*s %llu", &mr) != 1 || mr < 1 || mr > kMaxRowsPerWarp)
+        return POSPOP_EINVAL;
+      t.max_rows_per_warp = mr;
     } else if (strcmp(kind, "roofline") == 0) {
       int bs, h, cps;
       if (sscanf(line.c_str(), "%*s %d %d %d", &bs, &h, &cps) != 3) return POSPOP_EINVAL;
@@ -157,6 +165,10 @@ std::string format_tune(const DevCtx &ctx, const TuneTable &t) {
     s += "# batch <bs> <minb> <depth> <hint> <ctas_per_sm> <item_rows> <grab>\n";
     snprintf(line, sizeof line, "batch %d %d %d %d %d %u %u\n", v.bs, v.minb, v.depth, v.hint,
              t.batch.ctas_per_sm, t.batch.item_rows, t.batch.grab);
+    s += line;
+  }
+  if (t.max_rows_per_warp != kMaxRowsPerWarp) {
+    snprintf(line, sizeof line, "split %llu\n", (unsigned long long)t.max_rows_per_warp);
     s += line;
   }
   {
@@ -353,7 +365,7 @@ StreamPlan plan_stream(const DevCtx &ctx, const TuneTable &t, uint64_t rows) {
   p.grid = (unsigned)grid;
   p.block = (unsigned)v.bs;
   p.rows = rows;
-  p.rows_per_launch = grid * wpb * kMaxRowsPerWarp;
+  p.rows_per_launch = grid * wpb * t.max_rows_per_warp;
   p.launches = rows == 0 ? 0 : (int)((rows + p.rows_per_launch - 1) / p.rows_per_launch);
   return p;
 }

@@ -41,6 +41,7 @@ struct TuneTable {
   StreamTune stream[kClasses];
   BatchTune batch;
   RoofTune roof;
+  uint64_t max_rows_per_warp;   // single-array launch split (<= kMaxRowsPerWarp)
   std::string source;
 };
 

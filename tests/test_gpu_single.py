@@ -252,3 +252,30 @@ def test_wide_folds_large(gpu, orc):
     host = data.cpu().numpy()
     for w in (128, 256):
         assert np.array_equal(gpu_count(w, data), orc.bytes_mt(w, host, 16)), w
+
+
+def test_launch_split_overflow_guard(gpu, orc, tune_override):
+    """The single-array count splits into several launches when a warp would
+    take more rows than the counter bound allows (here lowered to 3 rows per
+    warp, so a 2 MiB count needs many launches); results stay exact."""
+    lines = [f"stream {c} 128 4 16 1 1 1" for c in range(5)] + ["split 3"]
+    tune_override("\n".join(lines) + "\n")
+    n = (2 << 20) + 4099
+    plan = pp.pospopcnt_plan(64, n)
+    assert plan["launches"] > 1, plan
+    host = synth.random_bytes(n, seed=123)
+    d = to_dev(host, gpu, align_pad=11)
+    before = pp.pospopcnt_launch_count()
+    for w in (8, 64, 256):
+        assert np.array_equal(gpu_count(w, d), orc.bytes(w, host)), w
+    assert pp.pospopcnt_launch_count() - before == 3 * plan["launches"]
+    # the selected count splits the same way
+    W = 4
+    nw = n // W
+    sel_h = synth.random_bytes((nw + 31) // 32 * 4, seed=5)
+    sel = to_dev(sel_h, gpu)
+    c = torch.zeros(32, dtype=torch.int64, device=gpu)
+    words = to_dev(host[:nw * W], gpu, align_pad=8)
+    pp.pospopcnt_masked(32, c, words, nw, sel)
+    torch.cuda.synchronize()
+    assert np.array_equal(counts_np(c), orc.masked(32, host[:nw * W], nw, sel_h))
