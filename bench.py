@@ -487,7 +487,7 @@ def _serving(pp, synth, pool, pool_bytes, large_gbs, dev, loads=(0.3, 0.6, 0.9),
     mean = (hi - lo) / math.log((hi + 1) / lo)      # mean of the log-uniform size
     out = {"workload": "Poisson arrivals; w uniform in {8,16,32,64}; sizes log-uniform "
                        "64 B..256 MiB at uniform offsets of the resident 8 GiB array",
-           "mem_budget_bytes": budget, "max_inflight": 4096, "batch_streams": 4, "loads": []}
+           "mem_budget_bytes": budget, "max_inflight": 4096, "batch_streams": 8, "loads": []}
     for k, load in enumerate(loads):
         rate = load * large_gbs * 1e9 / mean
         n = max(100, int(rate * duration_s))
@@ -495,7 +495,7 @@ def _serving(pp, synth, pool, pool_bytes, large_gbs, dev, loads=(0.3, 0.6, 0.9),
         arrival = np.round(r["arrival_s"] * 1e9).astype(np.int64)
         ptrs = (pool.data_ptr() + r["offset"]).astype(np.uint64)
         results = np.zeros((n, 64), dtype=np.uint64)
-        srv = pp.pospop_server_create(budget, 4096, 4)
+        srv = pp.pospop_server_create(budget, 4096, 8)
         try:
             recs = pp.pospop_server_run_trace(srv, arrival, r["w"], ptrs, r["nbytes"], results)
         finally:

@@ -49,6 +49,8 @@ static int pick_shape(int count, const Variant &(*get)(int), int step, const Var
 // ---------------------------------------------------------------------------
 // Tune table.
 // ---------------------------------------------------------------------------
+void TuneTable::set_source(const char *s) { snprintf(source, sizeof source, "%s", s ? s : ""); }
+
 int size_class(uint64_t rows) {
   if (rows <= 64) return 0;          // <= 32 KiB
   if (rows <= 2048) return 1;        // <= 1 MiB
@@ -80,7 +82,7 @@ TuneTable default_tune() {
   t.batch = BatchTune{find_variant(true, 256, 2, 16, 1), 2, 511, 1};
   t.roof = RoofTune{find_roof_variant(512, 1), 4};
   t.max_rows_per_warp = kMaxRowsPerWarp;
-  t.source = "built-in defaults";
+  t.set_source("built-in defaults");
   return t;
 }
 
@@ -151,7 +153,7 @@ std::string format_tune(const DevCtx &ctx, const TuneTable &t) {
     snprintf(prop.name, sizeof(prop.name), "unknown");
   }
   snprintf(line, sizeof line, "# pospopcnt tune table: %s, %d SMs (%s)\n", prop.name, ctx.sms,
-           t.source.c_str());
+           t.source);
   s += line;
   s += "# stream <class> <bs> <minb> <depth> <hint> <ctas_per_sm> <min_rows>\n";
   for (int c = 0; c < kClasses; c++) {
@@ -210,7 +212,7 @@ static TuneTable initial_tune() {
   std::string text;
   TuneTable t;
   if (!path.empty() && read_file(path, &text) && parse_tune(text.c_str(), &t) == POSPOP_OK) {
-    t.source = path;
+    t.set_source(path.c_str());
     return t;
   }
   return default_tune();
@@ -529,7 +531,6 @@ int launch_batch_with(DevCtx &ctx, const TuneTable &t, int w, unsigned long long
     return POSPOP_ECUDA;
   }
   PlanParams pp;
-  pp.desc = nullptr;
   pp.gptrs = nullptr;
   pp.glens = nullptr;
   pp.offsets = offsets;
@@ -545,7 +546,6 @@ int launch_batch_with(DevCtx &ctx, const TuneTable &t, int w, unsigned long long
   if (rc != POSPOP_OK) return rc;
 
   BatchParams bp;
-  bp.desc = nullptr;
   bp.gptrs = nullptr;
   bp.glens = nullptr;
   bp.base = static_cast<const uint8_t *>(base);
@@ -558,10 +558,6 @@ int launch_batch_with(DevCtx &ctx, const TuneTable &t, int w, unsigned long long
   bp.status = ws->status;
   bp.item_rows = t.batch.item_rows;
   bp.grab = t.batch.grab;
-  bp.remaining = nullptr;
-  bp.host_res = nullptr;
-  bp.flags = nullptr;
-  bp.seq = 0;
   const Variant &v = batch_variant(t.batch.variant);
   int cps = t.batch.ctas_per_sm < ctx.occ_batch[t.batch.variant] ? t.batch.ctas_per_sm
                                                                  : ctx.occ_batch[t.batch.variant];
@@ -1021,7 +1017,7 @@ int pospopcnt_tune_load(const char *path) {
   TuneTable t;
   rc = parse_tune(text.c_str(), &t);
   if (rc != POSPOP_OK) return rc;
-  t.source = path;
+  t.set_source(path);
   std::lock_guard<std::mutex> g(c->mu);
   c->tune = t;
   return POSPOP_OK;

@@ -1,9 +1,8 @@
 // pospop_batch.cuh -- batched counting over many arrays: planning kernels
 // (work items per array, prefix sums) and the persistent counting kernel.
 // Templated on the array source: CSR byte offsets from one base with one w
-// (pospopcnt_batch), per-array descriptors with their own pointer, length,
-// w and output row (the serving loop's mixed batches), or gathered regions
-// all counted into one counter array (pospopcnt_gather).
+// (pospopcnt_batch), or gathered regions all counted into one counter array
+// (pospopcnt_gather).
 #pragma once
 
 #include <cstdint>
@@ -23,13 +22,7 @@ struct ArrayRef {
 template <int SRC>
 __device__ __forceinline__ ArrayRef array_ref(const BatchParams &P, uint64_t a) {
   ArrayRef r;
-  if (SRC == kSrcDesc) {
-    const Desc d = P.desc[a];
-    r.s = (uint64_t)d.ptr;
-    r.e = r.s + d.nbytes;
-    r.w = d.w;
-    r.out = d.out;
-  } else if (SRC == kSrcGather) {
+  if (SRC == kSrcGather) {
     r.s = __ldg(P.gptrs + a);
     r.e = r.s + __ldg(P.glens + a);
     r.w = P.w;
@@ -92,10 +85,7 @@ __global__ void __launch_bounds__(kPlanThreads) plan_items_kernel(PlanParams P) 
     const uint64_t a = a0 + k;
     if (a < P.m) {
       uint64_t s, e;
-      if (SRC == kSrcDesc) {
-        s = (uint64_t)P.desc[a].ptr;
-        e = s + P.desc[a].nbytes;
-      } else if (SRC == kSrcGather) {
+      if (SRC == kSrcGather) {
         s = P.gptrs[a];
         e = s + P.glens[a];
       } else {
@@ -137,31 +127,6 @@ __device__ __forceinline__ uint64_t find_array(const uint64_t *__restrict__ item
     hi = nhi > lo ? nhi : lo + 1;
   }
   return lo;
-}
-
-// Per-array completion for descriptor batches: the warp whose work item
-// brings the array's countdown to zero publishes the array's counters to
-// mapped host memory and then raises the array's flag.  Every warp orders
-// its counter atomics before its decrement with a device-scope fence; the
-// last warp reads the counters at L2 (atomic add of zero) after its own
-// fence, and system-scope fences order the published counts before the flag.
-__device__ __forceinline__ void signal_if_last(const BatchParams &P, uint64_t a, int w,
-                                               unsigned long long *out, unsigned lane) {
-  __threadfence();
-  unsigned last = 0;
-  if (lane == 0) last = atomicSub(P.remaining + a, 1u) == 1u ? 1u : 0u;
-  last = __shfl_sync(kFull, last, 0);
-  if (!last) return;
-  __threadfence();
-  unsigned long long *res = P.host_res + 64 * a;
-  for (int j = (int)lane; j < w; j += 32) res[j] = atomicAdd(out + j, 0ull);
-  __threadfence_system();
-  __syncwarp();
-  if (lane == 0) {
-    __threadfence_system();
-    *reinterpret_cast<volatile unsigned int *>(P.flags + a) = P.seq;
-    __threadfence_system();
-  }
 }
 
 template <int SRC, int BS, int MINB, int DEPTH, int HINT>
@@ -210,7 +175,6 @@ __global__ void __launch_bounds__(BS, MINB) batch_kernel(BatchParams P) {
           if (v) atomicAdd(out + j, v);
         });
       }
-      if (SRC == kSrcDesc && P.remaining) signal_if_last(P, a, r.w, out, lane);
     }
   }
   if (SRC == kSrcGather) {

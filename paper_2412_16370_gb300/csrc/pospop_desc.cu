@@ -1,19 +1,96 @@
-// pospop_desc.cu -- the batched counting kernel over per-array descriptors
-// (pointer, length, w, output row), used by the serving loop to count
-// requests of mixed width and size in one launch.  Same planning and
-// counting templates as pospop_batch.cu.
+// pospop_desc.cu -- the serving loop's counting kernel: one launch counts up
+// to kServeMax requests of mixed width and size, passed by value in the
+// kernel's parameter block (a __grid_constant__ struct of about 8 KiB, read
+// in place through the constant cache: no upload copy before the launch).
+//
+// Work items (item_rows rows of 512 B of one request, as in the batched
+// count) are dealt to warps round-robin; each is counted with the paper's
+// per-thread algorithm (Section 4) and folded into its request slot's
+// counters.  The warp that finishes a request's last work item reads and
+// clears its counters, resets the slot's completion counter, publishes the
+// counts to mapped pinned host memory and then raises the request's flag,
+// so a request completes without waiting for the rest of the launch and the
+// slot's device state is clean for the next launch (no memset between
+// launches).  Fences: device scope before each completion count (this
+// warp's counter atomics first), device scope before the read-and-clear,
+// system scope before the flag.
 #include "pospop_batch.cuh"
 
 namespace pospop {
 
-#define POSPOP_DV(BS, MINB, D, H) \
-  Variant{reinterpret_cast<const void *>(&batch_kernel<kSrcDesc, BS, MINB, D, H>), BS, MINB, D, H}
+// Largest k in [0, n) with item_start[k] <= i (item_start[0] = 0 <= i <
+// item_start[n]), 32-way warp search over the parameter block.
+__device__ __forceinline__ uint32_t find_request(const uint64_t *item_start, uint32_t n,
+                                                 uint64_t i, unsigned lane) {
+  uint32_t lo = 0, hi = n;
+  while (hi - lo > 1) {
+    const uint32_t span = hi - lo;
+    const uint32_t idx = lo + (uint32_t)((uint64_t)span * (lane + 1) / 33);
+    const unsigned b = __ballot_sync(kFull, item_start[idx] <= i);
+    const int c = __popc(b);
+    const uint32_t nlo = c > 0 ? lo + (uint32_t)((uint64_t)span * c / 33) : lo;
+    const uint32_t nhi = c < 32 ? lo + (uint32_t)((uint64_t)span * (c + 1) / 33) : hi;
+    lo = nlo;
+    hi = nhi > lo ? nhi : lo + 1;
+  }
+  return lo;
+}
 
-static const Variant kDesc[] = {POSPOP_FAMILY(POSPOP_DV)};
+template <int BS, int MINB, int DEPTH, int HINT>
+__global__ void __launch_bounds__(BS, MINB) serve_kernel(const __grid_constant__ ServeParams P) {
+  constexpr unsigned WPB = BS / 32;
+  const unsigned lane = threadIdx.x & 31u;
+  const uint64_t NW = (uint64_t)gridDim.x * WPB;
+  const Xpose xk = make_xpose(lane);
+  for (uint64_t i = (uint64_t)blockIdx.x * WPB + (threadIdx.x >> 5); i < P.total; i += NW) {
+    const uint32_t k = find_request(P.item_start, P.n, i, lane);
+    const ServeReq &rq = P.req[k];
+    const uint64_t s0 = (uint64_t)rq.ptr, e0 = s0 + rq.nbytes;
+    Span s;
+    const uint64_t A = s0 & ~15ull;
+    s.A = reinterpret_cast<const uint8_t *>(A);
+    s.head = (uint32_t)(s0 - A);
+    s.G = (((e0 + 15u) & ~15ull) - A) >> 4;
+    s.tail = (uint32_t)(e0 - (A + 16u * (s.G - 1)));
+    const int w = rq.w;
+    const uint32_t rot = (8u * s.head) & (uint32_t)(w - 1);
+    const uint64_t R = span_rows(s);
+    const uint64_t r0 = (i - P.item_start[k]) * P.item_rows;
+    const uint64_t r1 = (r0 + P.item_rows < R) ? r0 + P.item_rows : R;
+    uint32_t cnt[4] = {0u, 0u, 0u, 0u};
+    count_rows<DEPTH, HINT>(s, r0, 1, r1 - r0, lane, xk, cnt, PlainLoader<HINT>{});
+    const uint32_t slot = P.slot0 + k;
+    unsigned long long *out = P.counts + 64ull * slot;
+    fold_counts(cnt, w, rot, lane, [&](uint32_t j, unsigned long long v) {
+      if (v) atomicAdd(out + j, v);
+    });
+    // completion of request k
+    __threadfence();
+    unsigned last = 0;
+    if (lane == 0) last = atomicAdd(P.done + slot, 1u) + 1u == rq.items ? 1u : 0u;
+    last = __shfl_sync(kFull, last, 0);
+    if (last) {
+      __threadfence();
+      unsigned long long *res = P.host_res + 64ull * slot;
+      for (int j = (int)lane; j < w; j += 32) res[j] = atomicExch(out + j, 0ull);
+      if (lane == 0) atomicExch(P.done + slot, 0u);
+      __threadfence_system();
+      __syncwarp();
+      if (lane == 0) {
+        __threadfence_system();
+        *reinterpret_cast<volatile unsigned int *>(P.flags + slot) = P.seq;
+        __threadfence_system();
+      }
+    }
+  }
+}
 
-int desc_variant_count() { return (int)(sizeof(kDesc) / sizeof(kDesc[0])); }
-const Variant &desc_variant(int i) { return kDesc[i]; }
+#define POSPOP_SERV(BS, MINB, D, H) \
+  Variant{reinterpret_cast<const void *>(&serve_kernel<BS, MINB, D, H>), BS, MINB, D, H}
 
-const void *plan_items_desc_fn() { return reinterpret_cast<const void *>(&plan_items_kernel<kSrcDesc>); }
+static const Variant kServe[] = {POSPOP_FAMILY(POSPOP_SERV)};
+
+int serve_variant_count() { return (int)(sizeof(kServe) / sizeof(kServe[0])); }
+const Variant &serve_variant(int i) { return kServe[i]; }
 
 }  // namespace pospop

@@ -26,22 +26,11 @@ struct StreamParams {
   uint32_t rot;                 // (8 * head) mod w
 };
 
-// One array of a descriptor batch (32 bytes).
-struct Desc {
-  const void *ptr;              // first byte (device addressable, any alignment)
-  uint64_t nbytes;
-  unsigned long long *out;      // w counters (device), added into
-  int32_t w;
-  int32_t reserved;
-};
-
 // Sources of a batched count (the template parameter SRC of the batch kernels).
 constexpr int kSrcCsr = 0;      // m arrays at base + offsets[a] .. base + offsets[a+1], one w
-constexpr int kSrcDesc = 1;     // per-array descriptors (pointer, length, w, output row)
 constexpr int kSrcGather = 2;   // regions ptrs[a], lens[a], all counted into one counter array
 
 struct BatchParams {
-  const Desc *desc;             // descriptor batches (else CSR below)
   const uint64_t *gptrs;        // gathered regions: start addresses (device array)
   const uint64_t *glens;        //                   byte lengths (device array)
   const uint8_t *base;
@@ -54,17 +43,37 @@ struct BatchParams {
   const int *status;            // planning status (workspace)
   uint32_t item_rows;           // rows of 512 B per work item
   uint32_t grab;                // work items taken per atomic
-  // Descriptor batches only (may be null): per-array completion.  The warp
-  // that finishes an array's last work item copies its counters to
-  // host_res[64 a ..] (mapped host memory) and sets flags[a] = seq.
-  unsigned int *remaining;      // work items left per array (device)
-  unsigned long long *host_res; // 64 per array (mapped pinned host memory)
-  unsigned int *flags;          // one per array (mapped pinned host memory)
-  unsigned int seq;
+};
+
+// One serving launch: up to kServeMax requests passed by value in the
+// kernel's parameter block (no upload copy), their work-item prefix sums,
+// and the per-request-slot state that the kernel leaves clean for reuse:
+// counters (read and cleared by the warp that finishes a request) and
+// completion counters (reset by the same warp).
+constexpr int kServeMax = 256;
+
+struct ServeReq {
+  const void *ptr;              // first byte (device addressable, any alignment)
+  uint64_t nbytes;
+  int32_t w;
+  uint32_t items;               // work items of this request
+};
+
+struct ServeParams {
+  uint32_t n;                   // requests in this launch
+  uint32_t item_rows;
+  uint64_t total;               // work items in this launch
+  unsigned long long *counts;   // 64 per request slot (device, zero between uses)
+  unsigned int *done;           // finished work items per request slot (device, zero between uses)
+  unsigned long long *host_res; // 64 per request slot (mapped pinned host memory)
+  unsigned int *flags;          // one per request slot (mapped pinned host memory)
+  uint32_t seq;                 // value written to a finished request's flag
+  uint32_t slot0;               // request slot of req[0]
+  ServeReq req[kServeMax];
+  uint64_t item_start[kServeMax + 1];
 };
 
 struct PlanParams {
-  const Desc *desc;             // descriptor batches (else CSR offsets)
   const uint64_t *gptrs;        // gathered regions
   const uint64_t *glens;
   const uint64_t *offsets;
@@ -117,8 +126,8 @@ const Variant &batch_variant(int i);
 int roofline_variant_count();
 const Variant &roofline_variant(int i);
 
-int desc_variant_count();
-const Variant &desc_variant(int i);
+int serve_variant_count();
+const Variant &serve_variant(int i);
 int gather_variant_count();
 const Variant &gather_variant(int i);
 int select_variant_count();
@@ -126,7 +135,6 @@ const Variant &select_variant(int i);
 const void *plan_items_gather_fn();
 
 const void *plan_items_fn();
-const void *plan_items_desc_fn();
 const void *plan_scan_fn();
 const void *plan_apply_fn();
 

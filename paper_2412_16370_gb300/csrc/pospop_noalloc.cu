@@ -111,7 +111,6 @@ extern "C" int pospopcnt_batch_noalloc(int w, uint64_t *counts, const void *base
   }
 
   PlanParams pp;
-  pp.desc = nullptr;
   pp.gptrs = nullptr;
   pp.glens = nullptr;
   pp.offsets = offsets;
@@ -134,7 +133,6 @@ extern "C" int pospopcnt_batch_noalloc(int w, uint64_t *counts, const void *base
   }
 
   BatchParams bp;
-  bp.desc = nullptr;
   bp.gptrs = nullptr;
   bp.glens = nullptr;
   bp.base = static_cast<const uint8_t *>(base);
@@ -147,10 +145,6 @@ extern "C" int pospopcnt_batch_noalloc(int w, uint64_t *counts, const void *base
   bp.status = status;
   bp.item_rows = bt.item_rows;
   bp.grab = bt.grab;
-  bp.remaining = nullptr;
-  bp.host_res = nullptr;
-  bp.flags = nullptr;
-  bp.seq = 0;
   const Variant &v = batch_variant(bt.variant);
   int cps = bt.ctas_per_sm < c->occ_batch[bt.variant] ? bt.ctas_per_sm : c->occ_batch[bt.variant];
   if (cps < 1) cps = 1;

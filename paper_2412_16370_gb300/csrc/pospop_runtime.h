@@ -42,7 +42,8 @@ struct TuneTable {
   BatchTune batch;
   RoofTune roof;
   uint64_t max_rows_per_warp;   // single-array launch split (<= kMaxRowsPerWarp)
-  std::string source;
+  char source[240];             // where the table came from (copied with the table: no heap)
+  void set_source(const char *s);
 };
 
 struct Workspace {

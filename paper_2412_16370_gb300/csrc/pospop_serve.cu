@@ -8,11 +8,14 @@
 // batch as soon as one of the server's batch streams is free, so requests
 // that arrive while others run are counted in the next batch, overlapping on
 // the device with the batches already in flight.  A batch is one launch of
-// the descriptor counting kernel (pospop_batch.cuh): the host plans the work
-// items (it knows every request's address and length) and uploads them with
-// the descriptors in one copy; the counters stay in device memory until the
-// batch's event fires, then each request's w counts are copied to its
-// result buffer and the request completes.  All waits are bounded.
+// serve_kernel (pospop_desc.cu) per kServeMax requests: the requests and
+// their work-item prefix sums, planned on the host (it knows every
+// request's address and length), travel in the kernel's parameter block, so
+// a batch is a launch and an event and nothing else.  Each request slot's
+// counters and completion counter live in device memory and are left clean
+// by the kernel; the warp that finishes a request publishes its counts to
+// mapped pinned memory and raises its flag, which the loop polls.  All
+// waits are bounded.
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -46,17 +49,14 @@ struct Request {
 struct Batch {
   cudaStream_t s = nullptr;
   cudaEvent_t done = nullptr;
-  uint8_t *hblock = nullptr;            // pinned upload block
-  uint8_t *dblock = nullptr;            // device copy of it
-  unsigned long long *dcounts = nullptr;
-  unsigned long long *hcounts = nullptr;  // pinned (whole-batch copy, the fallback)
+  unsigned long long *dcounts = nullptr;  // 64 per request slot, zero between uses
+  unsigned int *ddone = nullptr;        // completion counter per request slot, zero between uses
   unsigned long long *hres = nullptr;   // mapped pinned: per-request counts from the device
   unsigned int *hflags = nullptr;       // mapped pinned: per-request done flags
   unsigned long long *dres = nullptr;   // device addresses of the two above
   unsigned int *dflags = nullptr;
   unsigned int seq = 0;
   std::vector<Request *> reqs;          // null once completed
-  size_t open = 0;                      // requests of this batch not yet completed
   bool busy = false;
 };
 
@@ -68,7 +68,6 @@ struct pospop_server {
   size_t budget = 0;
   int max_inflight = 0;
   std::vector<pospop::Batch> batches;
-  size_t block_bytes = 0;
 
   std::mutex mu;
   std::condition_variable cv_loop, cv_done;
@@ -87,99 +86,73 @@ struct pospop_server {
 namespace pospop {
 namespace {
 
-// Upload block layout: [next u64][status i32 + pad][item_start (n+1) u64]
-// [remaining n u32, padded to 8 B][desc n x 32 B].
-size_t rem_offset(int n) { return 16 + 8 * (size_t)(n + 1); }
-size_t desc_offset(int n) { return rem_offset(n) + ((4 * (size_t)n + 7) & ~size_t(7)); }
-size_t block_size(int n) { return desc_offset(n) + sizeof(Desc) * (size_t)n; }
-
 void free_batch(Batch &b) {
-  if (b.hblock) cudaFreeHost(b.hblock);
-  if (b.hcounts) cudaFreeHost(b.hcounts);
   if (b.hres) cudaFreeHost(b.hres);
   if (b.hflags) cudaFreeHost(b.hflags);
-  if (b.dblock) cudaFree(b.dblock);
   if (b.dcounts) cudaFree(b.dcounts);
+  if (b.ddone) cudaFree(b.ddone);
   if (b.done) cudaEventDestroy(b.done);
   if (b.s) cudaStreamDestroy(b.s);
   b = Batch();
   cudaGetLastError();
 }
 
-// Enqueue one batch of the requests in b.reqs on b.s (loop thread only).
-// Requests are ordered smallest first, so that the persistent kernel, which
-// hands out work items in array order, finishes small requests early.
+// Enqueue one batch of the requests in b.reqs on b.s (loop thread only):
+// one launch per kServeMax requests, then the batch event.  Requests are
+// ordered smallest first, so that small requests' work items come first.
 int launch_batch(pospop_server &srv, Batch &b, const BatchTune &bt) {
   std::stable_sort(b.reqs.begin(), b.reqs.end(),
                    [](const Request *x, const Request *y) { return x->nbytes < y->nbytes; });
   const int n = (int)b.reqs.size();
   b.seq = b.seq + 1 == 0 ? 1 : b.seq + 1;
-  b.open = (size_t)n;
-  uint8_t *h = b.hblock;
-  uint64_t *item_start = reinterpret_cast<uint64_t *>(h + 16);
-  uint32_t *remaining = reinterpret_cast<uint32_t *>(h + rem_offset(n));
-  Desc *desc = reinterpret_cast<Desc *>(h + desc_offset(n));
-  memset(h, 0, 16);
-  uint64_t items = 0;
   const uint32_t ir = bt.item_rows;
-  for (int k = 0; k < n; k++) {
-    const Request *r = b.reqs[k];
-    const uint64_t s = (uint64_t)r->dptr, e = s + r->nbytes;
-    item_start[k] = items;
-    uint64_t it = 0;
-    if (r->nbytes > 0) {
-      const uint64_t G = (((e + 15u) & ~15ull) - (s & ~15ull)) >> 4;
-      const uint64_t R = (G + 31u) >> 5;
-      it = (R + ir - 1) / ir;
-    }
-    items += it;
-    remaining[k] = (uint32_t)it;
-    desc[k] = Desc{r->dptr, (uint64_t)r->nbytes, b.dcounts + 64 * (size_t)k, r->w, 0};
-    if (it == 0) {   // nothing to count: done as soon as the loop looks
-      memset(b.hres + 64 * (size_t)k, 0, 64 * sizeof(unsigned long long));
-      __atomic_store_n(b.hflags + k, b.seq, __ATOMIC_RELEASE);
-    }
-  }
-  item_start[n] = items;
-  const size_t up = block_size(n);
-  if (cudaMemcpyAsync(b.dblock, h, up, cudaMemcpyHostToDevice, b.s) != cudaSuccess ||
-      cudaMemsetAsync(b.dcounts, 0, 64 * sizeof(unsigned long long) * (size_t)n, b.s) !=
-          cudaSuccess) {
-    cudaGetLastError();
-    return POSPOP_ECUDA;
-  }
-  BatchParams P;
-  memset(&P, 0, sizeof P);
-  P.desc = reinterpret_cast<const Desc *>(b.dblock + desc_offset(n));
-  P.m = (uint64_t)n;
-  P.item_start = reinterpret_cast<const uint64_t *>(b.dblock + 16);
-  P.next = reinterpret_cast<unsigned long long *>(b.dblock);
-  P.status = reinterpret_cast<const int *>(b.dblock + 8);
-  P.item_rows = ir;
-  P.grab = bt.grab;
-  P.remaining = reinterpret_cast<unsigned int *>(b.dblock + rem_offset(n));
-  P.host_res = b.dres;
-  P.flags = b.dflags;
-  P.seq = b.seq;
-  const Variant &v = desc_variant(bt.variant);
+  const Variant &v = serve_variant(bt.variant);
   int cps = std::min(bt.ctas_per_sm, srv.ctx->occ_batch[bt.variant]);
   if (cps < 1) cps = 1;
   const uint64_t wpb = (uint64_t)v.bs / 32;
-  uint64_t grid = (items + wpb - 1) / wpb;
   const uint64_t max_grid = (uint64_t)srv.ctx->sms * (uint64_t)cps;
-  if (grid > max_grid) grid = max_grid;
-  if (grid < 1) grid = 1;
-  void *args[] = {&P};
-  if (items > 0) {
+  static thread_local ServeParams P;   // about 8 KiB: not on the loop thread's stack
+  for (int k0 = 0; k0 < n; k0 += kServeMax) {
+    const int cnt = std::min(kServeMax, n - k0);
+    P.n = (uint32_t)cnt;
+    P.item_rows = ir;
+    P.counts = b.dcounts;
+    P.done = b.ddone;
+    P.host_res = b.dres;
+    P.flags = b.dflags;
+    P.seq = b.seq;
+    P.slot0 = (uint32_t)k0;
+    uint64_t items = 0;
+    for (int k = 0; k < cnt; k++) {
+      const Request *r = b.reqs[k0 + k];
+      uint64_t it = 0;
+      if (r->nbytes > 0) {
+        const uint64_t s0 = (uint64_t)r->dptr, e0 = s0 + r->nbytes;
+        const uint64_t G = (((e0 + 15u) & ~15ull) - (s0 & ~15ull)) >> 4;
+        const uint64_t R = (G + 31u) >> 5;
+        it = (R + ir - 1) / ir;
+      }
+      P.item_start[k] = items;
+      P.req[k] = ServeReq{r->dptr, (uint64_t)r->nbytes, r->w, (uint32_t)it};
+      items += it;
+      if (it == 0) {   // nothing to count: done as soon as the loop looks
+        memset(b.hres + 64 * (size_t)(k0 + k), 0, 64 * sizeof(unsigned long long));
+        __atomic_store_n(b.hflags + k0 + k, b.seq, __ATOMIC_RELEASE);
+      }
+    }
+    P.item_start[cnt] = items;
+    P.total = items;
+    if (items == 0) continue;
+    uint64_t grid = (items + wpb - 1) / wpb;
+    if (grid > max_grid) grid = max_grid;
+    void *args[] = {&P};
     if (cudaLaunchKernel(v.fn, dim3((unsigned)grid), dim3(v.bs), args, 0, b.s) != cudaSuccess) {
       cudaGetLastError();
       return POSPOP_ECUDA;
     }
     note_launches(1);
   }
-  if (cudaMemcpyAsync(b.hcounts, b.dcounts, 64 * sizeof(unsigned long long) * (size_t)n,
-                      cudaMemcpyDeviceToHost, b.s) != cudaSuccess ||
-      cudaEventRecord(b.done, b.s) != cudaSuccess) {
+  if (cudaEventRecord(b.done, b.s) != cudaSuccess) {
     cudaGetLastError();
     return POSPOP_ECUDA;
   }
@@ -204,41 +177,53 @@ void serve_loop(pospop_server *srv) {
   cudaSetDevice(srv->ctx->device);
   std::vector<Batch *> finished_batches;
   std::vector<Request *> done_reqs;
+  uint32_t iter = 0;
+  int64_t last_activity = now_ns();
   std::vector<std::pair<Batch *, std::vector<Request *>>> to_launch;
   while (true) {
     bool progress = false;
     // 1. completions, without the lock: requests whose flag the device has
-    //    raised, and whole batches whose event has fired (which also frees
-    //    the batch's buffers; any request not flagged by then takes its
-    //    counts from the batch's copy)
+    //    raised, and whole batches whose event has fired (which frees the
+    //    batch's stream and request slots; a request still unflagged then
+    //    failed on the device)
     finished_batches.clear();
     done_reqs.clear();
+    const bool sweep = (++iter & 255u) == 0;   // periodic event check (device failures)
     for (Batch &b : srv->batches) {
       if (!b.busy) continue;
+      size_t open = 0;
       for (size_t k = 0; k < b.reqs.size(); k++) {
         Request *r = b.reqs[k];
-        if (!r || __atomic_load_n(b.hflags + k, __ATOMIC_ACQUIRE) != b.seq) continue;
+        if (!r) continue;
+        if (__atomic_load_n(b.hflags + k, __ATOMIC_ACQUIRE) != b.seq) {
+          open++;
+          continue;
+        }
         if (r->result)
           for (int j = 0; j < r->w; j++) r->result[j] = b.hres[64 * k + j];
         r->rec.status = POSPOP_OK;
         done_reqs.push_back(r);
         b.reqs[k] = nullptr;
-        b.open -= 1;
       }
+      // the event frees the stream and slots; ask only when every request is
+      // flagged (or on the periodic sweep, to catch a failed launch)
+      if (open > 0 && !sweep) continue;
       const cudaError_t q = cudaEventQuery(b.done);
       if (q == cudaErrorNotReady) continue;
       if (q != cudaSuccess) cudaGetLastError();
-      const int st = q == cudaSuccess ? POSPOP_OK : POSPOP_ECUDA;
       for (size_t k = 0; k < b.reqs.size(); k++) {
         Request *r = b.reqs[k];
         if (!r) continue;
-        if (st == POSPOP_OK && r->result)
-          for (int j = 0; j < r->w; j++) r->result[j] = b.hcounts[64 * k + j];
-        r->rec.status = st;
+        if (q == cudaSuccess && __atomic_load_n(b.hflags + k, __ATOMIC_ACQUIRE) == b.seq) {
+          if (r->result)
+            for (int j = 0; j < r->w; j++) r->result[j] = b.hres[64 * k + j];
+          r->rec.status = POSPOP_OK;
+        } else {
+          r->rec.status = POSPOP_ECUDA;
+        }
         done_reqs.push_back(r);
         b.reqs[k] = nullptr;
       }
-      b.open = 0;
       finished_batches.push_back(&b);
     }
     to_launch.clear();
@@ -281,7 +266,10 @@ void serve_loop(pospop_server *srv) {
       const bool busy = std::any_of(srv->batches.begin(), srv->batches.end(),
                                     [](const Batch &b) { return b.busy; });
       if (srv->stop && !busy && srv->admitted.empty() && srv->pending.empty()) stop_now = true;
-      if (!progress && !busy && !stop_now)
+      // idle: keep polling for a short while (a new request is picked up
+      // within a microsecond), then block on the condition variable
+      if (progress || busy) last_activity = tnow;
+      if (!progress && !busy && !stop_now && tnow - last_activity > 200000)
         srv->cv_loop.wait_for(lk, std::chrono::milliseconds(50));
     }
     // launches, without the lock
@@ -306,7 +294,6 @@ void serve_loop(pospop_server *srv) {
         for (Request *r : b.reqs)
           if (r) complete(*srv, r, rc, now_ns());
         b.reqs.clear();
-        b.open = 0;
         b.busy = false;
         srv->cv_done.notify_all();
       }
@@ -391,19 +378,18 @@ int pospop_server_create(size_t mem_budget, int max_inflight, int max_batches,
   srv->ctx = c;
   srv->budget = mem_budget;
   srv->max_inflight = max_inflight;
-  srv->block_bytes = block_size(max_inflight);
   srv->batches.resize((size_t)max_batches);
   for (Batch &b : srv->batches) {
     const size_t cbytes = 64 * sizeof(unsigned long long) * (size_t)max_inflight;
+    const size_t fbytes = sizeof(unsigned int) * (size_t)max_inflight;
     if (cudaStreamCreateWithFlags(&b.s, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&b.done, cudaEventDisableTiming) != cudaSuccess ||
-        cudaMallocHost(&b.hblock, srv->block_bytes) != cudaSuccess ||
-        cudaMallocHost(&b.hcounts, cbytes) != cudaSuccess ||
-        cudaMalloc(&b.dblock, srv->block_bytes) != cudaSuccess ||
         cudaMalloc(&b.dcounts, cbytes) != cudaSuccess ||
+        cudaMalloc(&b.ddone, fbytes) != cudaSuccess ||
+        cudaMemset(b.dcounts, 0, cbytes) != cudaSuccess ||
+        cudaMemset(b.ddone, 0, fbytes) != cudaSuccess ||
         cudaHostAlloc(&b.hres, cbytes, cudaHostAllocMapped) != cudaSuccess ||
-        cudaHostAlloc(&b.hflags, sizeof(unsigned int) * (size_t)max_inflight,
-                      cudaHostAllocMapped) != cudaSuccess ||
+        cudaHostAlloc(&b.hflags, fbytes, cudaHostAllocMapped) != cudaSuccess ||
         cudaHostGetDevicePointer(reinterpret_cast<void **>(&b.dres), b.hres, 0) != cudaSuccess ||
         cudaHostGetDevicePointer(reinterpret_cast<void **>(&b.dflags), b.hflags, 0) !=
             cudaSuccess) {
@@ -412,7 +398,13 @@ int pospop_server_create(size_t mem_budget, int max_inflight, int max_batches,
       delete srv;
       return POSPOP_ENOMEM;
     }
-    memset(b.hflags, 0, sizeof(unsigned int) * (size_t)max_inflight);   // seq starts at 1
+    memset(b.hflags, 0, fbytes);   // seq starts at 1
+  }
+  if (cudaDeviceSynchronize() != cudaSuccess) {   // the zeroed slots are in place
+    cudaGetLastError();
+    for (Batch &x : srv->batches) free_batch(x);
+    delete srv;
+    return POSPOP_ECUDA;
   }
   srv->loop = std::thread(serve_loop, srv);
   *out = srv;
