@@ -411,6 +411,46 @@ def _batched(pp, synth, synth_device, dev, stream, large_gbs, hbm_peak, m=200000
     wall = time.perf_counter() - t0
     ms_per = e0.elapsed_time(e1)
     gbs = total / (ms / 1e3) / 1e9
+    # the same batch with the other short-sequence method (per-lane bit
+    # regroup vs warp transpose flush for items of <= 3 rows), for comparison
+    import tempfile
+    desc = pp.pospopcnt_tune_describe()
+    cur = 1 if "\nshort 1" in desc else 0
+    alt_text = desc.replace(f"short {cur}", f"short {1 - cur}")
+    with tempfile.NamedTemporaryFile("w", suffix=".txt", delete=False) as f:
+        f.write(desc)
+        saved = f.name
+    with tempfile.NamedTemporaryFile("w", suffix=".txt", delete=False) as f:
+        f.write(alt_text)
+        alt = f.name
+    # a batch of only tiny arrays (every work item takes the short path)
+    tsz = synth.log_uniform_sizes(m, 1, 1536, seed=71)
+    toffs = synth.csr_offsets(tsz)
+    toffs_d = torch.from_numpy(toffs.view(np.int64)).to(dev)
+
+    def time_batch(offs_dev):
+        for _ in range(3):
+            pp.pospopcnt_batch(8, c, base, offs_dev, m, stream)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            pp.pospopcnt_batch(8, c, base, offs_dev, m, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    ms_tiny = time_batch(toffs_d)
+    pp.pospopcnt_tune_load(alt)
+    ms_alt = time_batch(offs_d)
+    ms_tiny_alt = time_batch(toffs_d)
+    pp.pospopcnt_tune_load(saved)
+    os.unlink(saved)
+    os.unlink(alt)
+    short_cmp = {"in_use": "regroup" if cur else "transpose",
+                 "other": "transpose" if cur else "regroup",
+                 "ragged_ms_in_use": round(ms, 3), "ragged_ms_other": round(ms_alt, 3),
+                 "tiny_workload": f"{m} arrays of 1..1536 B (log-uniform), {int(toffs[-1])} bytes",
+                 "tiny_ms_in_use": round(ms_tiny, 4), "tiny_ms_other": round(ms_tiny_alt, 4)}
     # the oracle on the first 2000 arrays, timed on the host cores
     import oracle
     orc = oracle.load()
@@ -421,6 +461,7 @@ def _batched(pp, synth, synth_device, dev, stream, large_gbs, hbm_peak, m=200000
     del base
     torch.cuda.empty_cache()
     return {"oracle_GBps": ora, "oracle_sample": f"first {k} arrays ({sub.size} bytes), 1 thread",
+            "short_sequence_method": short_cmp,
             "workload": f"{m} one-hot uint8 arrays (Zipf(1.1) over 8 classes), sizes log-uniform "
                         "1 B..4 MiB, back to back (unaligned starts), w=8",
             "bytes": total, "GBps": round(gbs, 1), "ms": round(ms, 3),

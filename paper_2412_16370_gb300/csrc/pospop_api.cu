@@ -82,6 +82,7 @@ TuneTable default_tune() {
   t.batch = BatchTune{find_variant(true, 256, 2, 16, 1), 2, 511, 1};
   t.roof = RoofTune{find_roof_variant(512, 1), 4};
   t.max_rows_per_warp = kMaxRowsPerWarp;
+  t.regroup = 0;
   t.set_source("built-in defaults");
   return t;
 }
@@ -92,6 +93,8 @@ TuneTable default_tune() {
 //   roofline <bs> <hint> <ctas_per_sm>
 //   split <max_rows_per_warp>     (1 .. 2^26; a single-array count is split into
 //                                  several launches so that no warp takes more)
+//   short <0|1>                   (w = 8 sequences of <= 3 rows: 0 = transpose
+//                                  flush, 1 = per-lane bit regroup)
 int parse_tune(const char *text, TuneTable *out) {
   TuneTable t = default_tune();
   std::string s(text);
@@ -125,6 +128,10 @@ int parse_tune(const char *text, TuneTable *out) {
       if (v < 0 || cps < 1 || ir < 1 || ir > (1u << 20) || grab < 1 || grab > 64)
         return POSPOP_EINVAL;
       t.batch = BatchTune{v, cps, ir, grab};
+    } else if (strcmp(kind, "short") == 0) {
+      unsigned rg;
+      if (sscanf(line.c_str(), "%*s %u", &rg) != 1 || rg > 1) return POSPOP_EINVAL;
+      t.regroup = rg;
     } else if (strcmp(kind, "split") == 0) {
       unsigned long long mr;
       if (sscanf(line.c_str(), "%*s %llu", &mr) != 1 || mr < 1 || mr > kMaxRowsPerWarp)
@@ -169,6 +176,9 @@ std::string format_tune(const DevCtx &ctx, const TuneTable &t) {
              t.batch.ctas_per_sm, t.batch.item_rows, t.batch.grab);
     s += line;
   }
+  snprintf(line, sizeof line, "# short <0 transpose | 1 per-lane regroup> (w = 8, <= 3 rows)\nshort %u\n",
+           t.regroup);
+  s += line;
   if (t.max_rows_per_warp != kMaxRowsPerWarp) {
     snprintf(line, sizeof line, "split %llu\n", (unsigned long long)t.max_rows_per_warp);
     s += line;
@@ -385,6 +395,7 @@ int launch_stream_with(const DevCtx &ctx, const TuneTable &t, int w, unsigned lo
   P.counts = counts;
   P.w = w;
   P.rot = (8u * P.s.head) & (uint32_t)(w - 1);
+  P.regroup = t.regroup;
   const uint64_t R = (P.s.G + 31) >> 5;
   const StreamPlan pl = plan_stream(ctx, t, R);
   const Variant *vp = &stream_variant(pl.variant);
@@ -558,6 +569,7 @@ int launch_batch_with(DevCtx &ctx, const TuneTable &t, int w, unsigned long long
   bp.status = ws->status;
   bp.item_rows = t.batch.item_rows;
   bp.grab = t.batch.grab;
+  bp.regroup = t.regroup;
   const Variant &v = batch_variant(t.batch.variant);
   int cps = t.batch.ctas_per_sm < ctx.occ_batch[t.batch.variant] ? t.batch.ctas_per_sm
                                                                  : ctx.occ_batch[t.batch.variant];
@@ -621,6 +633,7 @@ static int launch_gather_with(DevCtx &ctx, const TuneTable &t, int w, unsigned l
   bp.status = ws->status;
   bp.item_rows = t.batch.item_rows;
   bp.grab = t.batch.grab;
+  bp.regroup = t.regroup;
   const Variant &v = gather_variant(t.batch.variant);
   int cps = std::min(t.batch.ctas_per_sm, ctx.occ_batch[t.batch.variant]);
   if (cps < 1) cps = 1;
@@ -650,6 +663,7 @@ static int launch_select_with(const DevCtx &ctx, const TuneTable &t, int w,
   P.counts = counts;
   P.w = w;
   P.rot = (8u * P.s.head) & (uint32_t)(w - 1);
+  P.regroup = 0;
   Q.bits = static_cast<const uint8_t *>(select);
   Q.nbits = n;
   Q.nbytes = 4 * ((n + 31) / 32);

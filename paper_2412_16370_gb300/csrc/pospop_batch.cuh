@@ -163,9 +163,22 @@ __global__ void __launch_bounds__(BS, MINB) batch_kernel(BatchParams P) {
       const uint64_t R = span_rows(s);
       const uint64_t r0 = k * P.item_rows;
       const uint64_t r1 = (r0 + P.item_rows < R) ? r0 + P.item_rows : R;
+      unsigned long long *out = r.out;
+      if (P.regroup && r.w == 8 && r1 - r0 <= 3) {
+        uint32_t lo = 0u, hi = 0u;
+        regroup_rows_w8(s, r0, 1, r1 - r0, lane, PlainLoader<HINT>{}, lo, hi);
+        if (SRC == kSrcGather)
+          regroup_emit_w8(lo, hi, lane, [&](uint32_t j, unsigned long long v) {
+            if (v) atomicAdd(&gacc[j], v);
+          });
+        else
+          regroup_emit_w8(lo, hi, lane, [&](uint32_t j, unsigned long long v) {
+            if (v) atomicAdd(out + j, v);
+          });
+        continue;
+      }
       uint32_t cnt[4] = {0u, 0u, 0u, 0u};
       count_rows<DEPTH, HINT>(s, r0, 1, r1 - r0, lane, xk, cnt, PlainLoader<HINT>{});
-      unsigned long long *out = r.out;
       if (SRC == kSrcGather) {
         fold_counts(cnt, r.w, rot, lane, [&](uint32_t j, unsigned long long v) {
           if (v) atomicAdd(&gacc[j], v);

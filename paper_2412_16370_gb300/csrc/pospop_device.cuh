@@ -485,6 +485,71 @@ __device__ __forceinline__ void fold_counts_256(const uint32_t cnt[4], const uin
 }
 
 // ---------------------------------------------------------------------------
+// Per-lane bit regroup for w = 8 (the Future Work section's regrouping: each
+// byte collects the bits of one place value, then a per-byte popcount).
+// Eight bytes form an 8x8 bit matrix (row b = byte b); after the transpose
+// byte j holds bit j of all eight bytes, so its popcount is the number of
+// those bytes with bit j set.  A lane keeps its class counts as bytes
+// (classes 0..3 in acc_lo, 4..7 in acc_hi; at most 16 per granule, so up to
+// 15 granules fit a byte); the warp's sums come from redux.sync.  Used as an
+// alternative to the transpose flush for short sequences (at most 3 rows).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t transpose8x8(uint64_t x) {
+  uint64_t t;
+  t = (x ^ (x >> 7)) & 0x00AA00AA00AA00AAull;
+  x = x ^ t ^ (t << 7);
+  t = (x ^ (x >> 14)) & 0x0000CCCC0000CCCCull;
+  x = x ^ t ^ (t << 14);
+  t = (x ^ (x >> 28)) & 0x00000000F0F0F0F0ull;
+  x = x ^ t ^ (t << 28);
+  return x;
+}
+
+// Popcount of each byte of v, in place.
+__device__ __forceinline__ uint32_t popc_bytes(uint32_t v) {
+  v = v - ((v >> 1) & 0x55555555u);
+  v = (v & 0x33333333u) + ((v >> 2) & 0x33333333u);
+  return (v + (v >> 4)) & 0x0F0F0F0Fu;
+}
+
+__device__ __forceinline__ void regroup_add_w8(const V4 &v, uint32_t &acc_lo, uint32_t &acc_hi) {
+  const uint64_t a = transpose8x8(((uint64_t)v.x[1] << 32) | v.x[0]);
+  const uint64_t b = transpose8x8(((uint64_t)v.x[3] << 32) | v.x[2]);
+  acc_lo += popc_bytes((uint32_t)a) + popc_bytes((uint32_t)b);
+  acc_hi += popc_bytes((uint32_t)(a >> 32)) + popc_bytes((uint32_t)(b >> 32));
+}
+
+// Class counts (w = 8) of a short row sequence (nrows <= 3), per lane.
+template <class Loader>
+__device__ __forceinline__ void regroup_rows_w8(const Span &s, uint64_t row0, uint64_t stride,
+                                                uint64_t nrows, unsigned lane, const Loader &ld,
+                                                uint32_t &acc_lo, uint32_t &acc_hi) {
+  uint64_t g = row0 * 32u + lane;
+  for (uint64_t i = 0; i < nrows; i++, g += stride * 32u) regroup_add_w8(ld.edge(s, g), acc_lo, acc_hi);
+}
+
+// Warp sums of the eight classes (fields widened to 16 bits: at most
+// 48 * 32 per class), emitted by lane 0.  For w = 8 the phase rotation is 0.
+template <typename Emit>
+__device__ __forceinline__ void regroup_emit_w8(uint32_t acc_lo, uint32_t acc_hi, unsigned lane,
+                                                Emit emit) {
+  const uint32_t s02 = __reduce_add_sync(kFull, acc_lo & 0x00ff00ffu);
+  const uint32_t s13 = __reduce_add_sync(kFull, (acc_lo >> 8) & 0x00ff00ffu);
+  const uint32_t s46 = __reduce_add_sync(kFull, acc_hi & 0x00ff00ffu);
+  const uint32_t s57 = __reduce_add_sync(kFull, (acc_hi >> 8) & 0x00ff00ffu);
+  if (lane == 0) {
+    emit(0u, (unsigned long long)(s02 & 0xffffu));
+    emit(1u, (unsigned long long)(s13 & 0xffffu));
+    emit(2u, (unsigned long long)(s02 >> 16));
+    emit(3u, (unsigned long long)(s13 >> 16));
+    emit(4u, (unsigned long long)(s46 & 0xffffu));
+    emit(5u, (unsigned long long)(s57 & 0xffffu));
+    emit(6u, (unsigned long long)(s46 >> 16));
+    emit(7u, (unsigned long long)(s57 >> 16));
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Fold (f_w, Section 4.4) with the phase rotation for unaligned starts: the
 // lane's counts of granule positions 32r + lane become counter
 // (32r + lane - rot) mod w.  For w <= 32 all four lanes r share one counter,

@@ -24,6 +24,7 @@ struct StreamParams {
   unsigned long long *counts;   // w counters (device)
   int w;
   uint32_t rot;                 // (8 * head) mod w
+  uint32_t regroup;             // w = 8 warps with <= 3 rows use the per-lane bit regroup
 };
 
 // Sources of a batched count (the template parameter SRC of the batch kernels).
@@ -43,6 +44,7 @@ struct BatchParams {
   const int *status;            // planning status (workspace)
   uint32_t item_rows;           // rows of 512 B per work item
   uint32_t grab;                // work items taken per atomic
+  uint32_t regroup;             // w = 8 items of <= 3 rows use the per-lane bit regroup
 };
 
 // One serving launch: up to kServeMax requests passed by value in the

@@ -95,9 +95,11 @@ extern "C" int pospopcnt_batch_noalloc(int w, uint64_t *counts, const void *base
   rc = scratch_address(c->device, &scratch);
   if (rc != POSPOP_OK) return rc;
   BatchTune bt;
+  uint32_t regroup;
   {
     std::lock_guard<std::mutex> g(c->mu);
     bt = c->tune.batch;
+    regroup = c->tune.regroup;
   }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   uint64_t *item_start = reinterpret_cast<uint64_t *>(scratch);
@@ -145,6 +147,7 @@ extern "C" int pospopcnt_batch_noalloc(int w, uint64_t *counts, const void *base
   bp.status = status;
   bp.item_rows = bt.item_rows;
   bp.grab = bt.grab;
+  bp.regroup = regroup;
   const Variant &v = batch_variant(bt.variant);
   int cps = bt.ctas_per_sm < c->occ_batch[bt.variant] ? bt.ctas_per_sm : c->occ_batch[bt.variant];
   if (cps < 1) cps = 1;

@@ -42,6 +42,7 @@ struct TuneTable {
   BatchTune batch;
   RoofTune roof;
   uint64_t max_rows_per_warp;   // single-array launch split (<= kMaxRowsPerWarp)
+  uint32_t regroup;             // w = 8 short sequences: 1 = per-lane bit regroup, 0 = transpose
   char source[240];             // where the table came from (copied with the table: no heap)
   void set_source(const char *s);
 };

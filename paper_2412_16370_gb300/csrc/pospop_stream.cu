@@ -43,17 +43,23 @@ __global__ void __launch_bounds__(BS, MINB) stream_kernel(StreamParams P) {
   const uint64_t mine = nr > gw ? (nr - gw + NW - 1) / NW : 0;
 
   const Xpose xk = make_xpose(lane);
-  uint32_t cnt[4] = {0u, 0u, 0u, 0u};
-  uint32_t cnt_odd[4] = {0u, 0u, 0u, 0u};
-  count_rows<DEPTH, HINT, PlainLoader<HINT>, PAR2>(to_span(P.s), P.row_begin + gw, NW, mine, lane,
-                                                   xk, cnt, PlainLoader<HINT>{}, cnt_odd);
   auto to_shared = [&](uint32_t j, unsigned long long v) {
     if (v) atomicAdd(&acc[j], v);
   };
-  if (PAR2)
-    fold_counts_256(cnt, cnt_odd, P.rot, lane, to_shared);
-  else
-    fold_counts(cnt, P.w, P.rot, lane, to_shared);
+  if (!PAR2 && P.regroup && P.w == 8 && mine <= 3) {   // warp-uniform choice
+    uint32_t lo = 0u, hi = 0u;
+    regroup_rows_w8(to_span(P.s), P.row_begin + gw, NW, mine, lane, PlainLoader<HINT>{}, lo, hi);
+    regroup_emit_w8(lo, hi, lane, to_shared);
+  } else {
+    uint32_t cnt[4] = {0u, 0u, 0u, 0u};
+    uint32_t cnt_odd[4] = {0u, 0u, 0u, 0u};
+    count_rows<DEPTH, HINT, PlainLoader<HINT>, PAR2>(to_span(P.s), P.row_begin + gw, NW, mine,
+                                                     lane, xk, cnt, PlainLoader<HINT>{}, cnt_odd);
+    if (PAR2)
+      fold_counts_256(cnt, cnt_odd, P.rot, lane, to_shared);
+    else
+      fold_counts(cnt, P.w, P.rot, lane, to_shared);
+  }
   __syncthreads();
   for (int j = threadIdx.x; j < P.w; j += BS) {
     const unsigned long long v = acc[j];

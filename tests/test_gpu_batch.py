@@ -188,3 +188,30 @@ def test_argument_errors(gpu):
     assert L.pospopcnt_batch(9, c.data_ptr(), base.data_ptr(), offs.data_ptr(), 2, None) == pp.POSPOP_EINVAL
     hoffs = np.zeros(3, dtype=np.uint64)
     assert L.pospopcnt_batch(8, c.data_ptr(), base.data_ptr(), hoffs.ctypes.data, 2, None) == pp.POSPOP_EPTR
+
+
+@pytest.mark.parametrize("item_rows", (1, 2, 3, 127))
+def test_regroup_short_path(gpu, orc, tune_override, item_rows):
+    """w = 8 work items of at most 3 rows through the per-lane bit regroup
+    (tune entry `short 1`), bit-exact; other widths keep the transpose flush."""
+    sizes = synth.log_uniform_sizes(3000, 1, 5000, seed=91)
+    sizes[::29] = 0
+    offs = synth.csr_offsets(sizes)
+    host = synth.random_bytes(int(offs[-1]), seed=92)
+    base = torch.empty(host.size + 32, dtype=torch.uint8, device=gpu)[3:3 + host.size]
+    base.copy_(torch.from_numpy(host))
+    offs_d = torch.from_numpy(offs.view(np.int64)).to(gpu)
+    tune_override(f"batch 512 1 16 1 1 {item_rows} 1\nshort 1\n")
+    assert "short 1" in pp.pospopcnt_tune_describe()
+    for w in (8, 16):
+        c = torch.zeros((len(sizes), w), dtype=torch.int64, device=gpu)
+        pp.pospopcnt_batch(w, c, base, offs_d)
+        assert np.array_equal(counts_np(c), orc.batch(w, host, offs)), (w, item_rows)
+    # one-hot bytes: each array's class histogram
+    oh = synth.one_hot_bytes(int(offs[-1]), 93)
+    base.copy_(torch.from_numpy(oh))
+    c = torch.zeros((len(sizes), 8), dtype=torch.int64, device=gpu)
+    pp.pospopcnt_batch(8, c, base, offs_d)
+    got = counts_np(c)
+    assert np.array_equal(got, orc.batch(8, oh, offs))
+    assert np.array_equal(got.sum(axis=1), sizes.astype(np.uint64))

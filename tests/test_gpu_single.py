@@ -279,3 +279,16 @@ def test_launch_split_overflow_guard(gpu, orc, tune_override):
     pp.pospopcnt_masked(32, c, words, nw, sel)
     torch.cuda.synchronize()
     assert np.array_equal(counts_np(c), orc.masked(32, host[:nw * W], nw, sel_h))
+
+
+def test_regroup_short_path_single(gpu, orc, tune_override):
+    """Single arrays whose warps get at most 3 rows, w = 8, through the
+    per-lane bit regroup (tune entry `short 1`)."""
+    lines = [f"stream {c} 128 4 16 1 1 {mr}" for c, mr in zip(range(5), (1, 2, 3, 3, 3))]
+    tune_override("\n".join(lines) + "\nshort 1\n")
+    for n in (1, 5, 16, 17, 511, 512, 513, 4 * 512 * 3 - 7, 4 * 512 * 3, 100003):
+        for off in (0, 7, 15):
+            host = synth.random_bytes(n, seed=n + off)
+            d = to_dev(host, gpu, align_pad=off)
+            for w in (8, 16):
+                assert np.array_equal(gpu_count(w, d), orc.bytes(w, host)), (n, off, w)
