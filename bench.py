@@ -368,11 +368,27 @@ def _e2e(args, pp, data, nbytes, world, dist):
         t = torch.tensor([dt], dtype=torch.float64, device=data.device)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         dt = float(t.item())
+    # the link's achievable read rate: the roofline read kernel on the same
+    # pinned host buffer (device time)
+    rsum = torch.zeros(1, dtype=torch.int64, device=data.device)
+    stream = torch.cuda.current_stream()
+    pp.pospopcnt_roofline_read(host, rsum, nbytes, stream)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    pp.pospopcnt_roofline_read(host, rsum, nbytes, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    link_gbs = nbytes / (e0.elapsed_time(e1) / 1e3) / 1e9
     del host
-    return {"value": round(world * nbytes * len(WIDTHS) * steps / dt / 1e9, 2), "unit": "GB/s",
+    value = world * nbytes * len(WIDTHS) * steps / dt / 1e9
+    return {"value": round(value, 2), "unit": "GB/s",
             "h2d_bytes_per_step": nbytes * len(WIDTHS),
             "d2h_bytes_per_step": 8 * sum(WIDTHS), "steps": steps,
-            "path": "pospopcnt_host on pinned host memory (read in place over NVLink-C2C)"}
+            "path": "pospopcnt_host on pinned host memory (read in place over NVLink-C2C)",
+            "link_read_roofline_GBps": round(link_gbs, 1),
+            "frac_of_link_read": round(value / world / link_gbs, 4)}
 
 
 def _batched(pp, synth, synth_device, dev, stream, large_gbs, hbm_peak, m=200000):

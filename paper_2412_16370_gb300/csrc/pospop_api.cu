@@ -365,7 +365,10 @@ StreamPlan plan_stream(const DevCtx &ctx, const TuneTable &t, uint64_t rows) {
   const StreamTune &st = t.stream[p.cls];
   p.variant = st.variant;
   const Variant &v = stream_variant(st.variant);
-  int cps = st.ctas_per_sm < ctx.occ_stream[st.variant] ? st.ctas_per_sm : ctx.occ_stream[st.variant];
+  // ctas_per_sm above the occupancy limit is allowed: the grid then runs in
+  // waves (measured on GB300: 2-4 waves of the grid-stride row schedule read
+  // about 1% faster than one)
+  int cps = st.ctas_per_sm;
   if (cps < 1) cps = 1;
   p.cps = cps;
   const uint64_t wpb = (uint64_t)v.bs / 32;
@@ -438,7 +441,7 @@ int launch_roofline_with(const DevCtx &ctx, const RoofTune &rt, const void *byte
   P.G = (E - A) >> 4;
   P.sum = sum;
   const Variant &v = roofline_variant(rt.variant);
-  int cps = rt.ctas_per_sm < ctx.occ_roof[rt.variant] ? rt.ctas_per_sm : ctx.occ_roof[rt.variant];
+  int cps = rt.ctas_per_sm;   // above the occupancy limit: waves, as for the count
   if (cps < 1) cps = 1;
   const uint64_t rows = (P.G + 31) >> 5;
   uint64_t grid = (rows + (v.bs / 32) - 1) / (v.bs / 32);
@@ -669,7 +672,12 @@ static int launch_select_with(const DevCtx &ctx, const TuneTable &t, int w,
   Q.nbytes = 4 * ((n + 31) / 32);
   Q.wlog = w == 8 ? 0u : w == 16 ? 1u : w == 32 ? 2u : 3u;
   const uint64_t R = (P.s.G + 31) >> 5;
-  const StreamPlan pl = plan_stream(ctx, t, R);
+  // the selection kernel is ALU-heavier than the plain count and runs best
+  // in a single wave (measured on GB300): cap the blocks per SM at occupancy
+  TuneTable ts = t;
+  StreamTune &st = ts.stream[size_class(R)];
+  if (st.ctas_per_sm > ctx.occ_stream[st.variant]) st.ctas_per_sm = ctx.occ_stream[st.variant];
+  const StreamPlan pl = plan_stream(ctx, ts, R);
   // the selection kernels come in the tune table's block shapes (flush depth
   // 16), four word sizes each; take the planned block shape
   const int shape = pick_shape(select_variant_count(), select_variant, 4, stream_variant(pl.variant));

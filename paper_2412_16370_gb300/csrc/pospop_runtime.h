@@ -24,7 +24,7 @@ constexpr uint64_t kMaxRowsPerWarp = uint64_t(1) << 26;  // u32 counters: 32 * 2
 
 struct StreamTune {
   int variant;              // index into the stream kernel table
-  int ctas_per_sm;          // resident blocks per SM wanted (capped by occupancy)
+  int ctas_per_sm;          // blocks per SM (above the occupancy limit the grid runs in waves)
   uint32_t min_rows;        // fewest rows a warp should get before the grid grows
 };
 struct BatchTune {

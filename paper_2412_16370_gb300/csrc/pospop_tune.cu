@@ -117,7 +117,7 @@ extern "C" int pospopcnt_autotune(size_t max_bytes, const char *path) {
     double best_ms = tm.time([&] { return launch_stream_with(*c, best, 16, counts, buf, nbytes, tm.s); });
     if (best_ms <= 0) best_ms = 1e30;
     for (int v = 0; v < stream_variant_count(); v++) {
-      for (int cps = 1; cps <= std::min(c->occ_stream[v], 4); cps++) {
+      for (int cps = 1; cps <= std::max(4, c->occ_stream[v]); cps++) {
         unsigned last_grid = 0;
         for (uint32_t mr : minrows_set) {
           cand = best;
@@ -180,7 +180,7 @@ extern "C" int pospopcnt_autotune(size_t max_bytes, const char *path) {
         tm.time([&] { return launch_roofline_with(*c, best.roof, buf, max_bytes, counts, tm.s); });
     if (best_ms <= 0) best_ms = 1e30;
     for (int v = 0; v < roofline_variant_count(); v++)
-      for (int cps = 1; cps <= std::min(c->occ_roof[v], 8); cps++) {
+      for (int cps = 1; cps <= 4 * c->occ_roof[v]; cps++) {
         const RoofTune rt{v, cps};
         const double ms = tm.time([&] {
           return launch_roofline_with(*c, rt, buf, max_bytes, counts, tm.s);
