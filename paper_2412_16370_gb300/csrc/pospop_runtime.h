@@ -63,7 +63,7 @@ struct Staging {
   cudaEvent_t copied[kStageBufs] = {nullptr, nullptr};
   cudaEvent_t consumed[kStageBufs] = {nullptr, nullptr};
   unsigned long long *dcounts = nullptr;
-  unsigned long long *hcounts = nullptr;   // pinned, 64 entries
+  unsigned long long *hcounts = nullptr;   // pinned, 256 entries
 };
 
 struct DevCtx {
