@@ -19,6 +19,8 @@ also carries:
 * short: microseconds per call for short unaligned arrays, one launch each,
   plain and graph-replayed;
 * cpu_baseline: the CPU oracle on the host cores on a bounded sample;
+* sweep: every w at 1 GiB and 8 GiB over Bernoulli(0.01/0.5/0.99) and
+  all-ones bits, each cell's counts checked;
 * clocks: SM clocks and throttle reasons sampled during the timed region.
 
 ``--impl reference`` times the CPU oracle on the same workload instead.
@@ -30,6 +32,7 @@ import argparse
 import hashlib
 import json
 import os
+import platform
 import subprocess
 import sys
 import threading
@@ -169,11 +172,40 @@ def _cpu_baseline(data_dev, budget_s: float = 4.0):
     for w in WIDTHS:
         orc.bytes_mt(w, host, cores)
     dt = time.perf_counter() - t0
+    # the same loop on one thread, on a sample of about a second
+    one = int(min(sample, max(1 << 20, rate / cores * 1.0 / len(WIDTHS))))
+    one -= one % 64
+    t0 = time.perf_counter()
+    for w in WIDTHS:
+        orc.bytes_mt(w, host[:one], 1)
+    dt1 = time.perf_counter() - t0
     del torch
     return {"value": round(sample * len(WIDTHS) / dt / 1e9, 4), "unit": "GB/s", "cores": cores,
             "kind": "oracle",
+            "one_thread_GBps": round(one * len(WIDTHS) / dt1 / 1e9, 4),
+            "cpu_model": _cpu_model(),
             "sample": f"first {sample >> 20} MiB of the 8 GiB array, counted once per w in "
-                      f"{{8,16,32,64}} with {cores} threads (Fig. 2 loop, -O2 -fno-tree-vectorize)"}
+                      f"{{8,16,32,64}} with {cores} threads (Fig. 2 loop, -O2 -fno-tree-vectorize); "
+                      f"one_thread_GBps: the first {one >> 20} MiB on one thread"}
+
+
+def _cpu_model():
+    """The host CPU's model name, from lscpu (or /proc/cpuinfo)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return platform.machine()
 
 
 def run_ours(args):
@@ -292,13 +324,15 @@ def run_ours(args):
         if rank == 0:
             for key, fn in (("batched", lambda: _batched(pp, synth, synth_device, dev, stream,
                                                          achieved, hbm_peak, m=args.batched_m)),
-                            ("short", lambda: _short(pp, synth, dev, stream)),
+                            ("short", lambda: _short(pp, synth, synth_device, dev, stream)),
                             ("serving", lambda: _serving(pp, synth, data, nbytes, achieved, dev)),
                             ("masked", lambda: _masked(pp, synth_device, data, nbytes, dev,
                                                        stream, achieved, hbm_peak)),
                             ("gather", lambda: _gather(pp, synth, data, nbytes, dev, stream,
                                                        achieved, hbm_peak)),
-                            ("cpu_baseline", lambda: _cpu_baseline(data))):
+                            ("cpu_baseline", lambda: _cpu_baseline(data)),
+                            ("sweep", lambda: _sweep(pp, synth_device, data, nbytes, stream,
+                                                     hbm_peak, 0 + rank))):
                 if not want(key):
                     continue
                 try:
@@ -489,13 +523,13 @@ def _batched(pp, synth, synth_device, dev, stream, large_gbs, hbm_peak, m=200000
             "one_hot_sums_ok": ok}
 
 
-def _short(pp, synth, dev, stream, n=2000):
+def _short(pp, synth, synth_device, dev, stream, n=2000):
     """Short unaligned arrays (log-uniform 1 B .. 64 KiB), one launch per array."""
     import torch
     sizes = synth.log_uniform_sizes(n, 1, 65536, seed=21)
     slot = 65536 + 32
     buf = torch.empty(slot * 64, dtype=torch.uint8, device=dev)
-    buf.random_(0, 256)
+    synth_device.random_(buf, 22)
     c = torch.zeros(64, dtype=torch.int64, device=dev)
     basep = buf.data_ptr()
     calls = [(WIDTHS[k % 4], basep + (k % 64) * slot + (k % 16), int(sizes[k])) for k in range(n)]
@@ -655,6 +689,46 @@ def _gather(pp, synth, data, nbytes, dev, stream, large_gbs, hbm_peak, m=100000)
             "frac_of_large_array": round(gbs / large_gbs, 4)}
 
 
+def _sweep(pp, synth_device, data, nbytes, stream, hbm_peak, seed):
+    """The large-array sweep: w x {1 GiB, 8 GiB} x Bernoulli(p) for p in
+    {0.01, 0.5, 0.99} plus all-ones, each cell timed like the headline launch
+    and its counts checked (all-ones: the closed form; Bernoulli: within 6
+    sigma of n*p).  The resident array is restored to the headline data."""
+    import torch
+    sizes = [z for z in (GIB, 8 * GIB) if z <= nbytes]
+    cells = []
+    ok = True
+    warm, reps = 3, 10
+    for p in (0.01, 0.5, 0.99, 1.0):
+        if p == 1.0:
+            synth_device.fill_(data, 0xFF, nbytes=sizes[-1], stream=stream)
+        else:
+            synth_device.bernoulli_(data, p, 7000 + int(p * 100), nbytes=sizes[-1], stream=stream)
+        for size in sizes:
+            for w in WIDTHS:
+                c = torch.zeros(w, dtype=torch.int64, device=data.device)
+                ms = _time_ms(lambda: pp.pospopcnt_async(w, c, data, size, stream), stream,
+                              reps=reps, warm=warm)
+                per = c.cpu().numpy().view(np.uint64).astype(np.float64) / (warm + reps)
+                words = size * 8 // w
+                if p == 1.0:
+                    good = bool(np.all(per == words))
+                else:
+                    good = bool(np.all(np.abs(per - words * p) <= 6 * np.sqrt(words * p * (1 - p))))
+                ok &= good
+                gbs = size / (ms / 1e3) / 1e9
+                cells.append({"w": w, "bytes": size, "p": "ones" if p == 1.0 else p,
+                              "GBps": round(gbs, 1), "frac_of_hbm_peak": round(gbs / hbm_peak, 4),
+                              "counts_ok": good})
+    synth_device.bernoulli_(data, 0.5, seed, stream=stream)
+    torch.cuda.synchronize()
+    fr = [c["frac_of_hbm_peak"] for c in cells]
+    return {"workload": "w in {8,16,32,64} x {1 GiB, 8 GiB} x Bernoulli(p), p in {0.01,0.5,0.99} "
+                        "plus all-ones; 10 launches per cell after 3 warm-up",
+            "min_frac_of_hbm_peak": min(fr), "max_frac_of_hbm_peak": max(fr),
+            "all_counts_ok": ok, "cells": cells}
+
+
 def run_reference(args):
     """The CPU oracle (the reference arm of this tier) on the same workload."""
     world, rank, _ = _dist()
@@ -684,7 +758,7 @@ def run_reference(args):
             "config": {"workload": WORKLOAD, "parallelism": "host cores",
                        "sample_bytes_per_step": sample * len(WIDTHS)},
             "cpu_baseline": {"value": round(value, 4), "unit": "GB/s", "cores": cores,
-                             "kind": "oracle", "sample": desc},
+                             "kind": "oracle", "sample": desc, "cpu_model": _cpu_model()},
             "e2e": {"value": round(value, 4), "unit": "GB/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -702,10 +776,11 @@ def main():
                     help="arrays in the batched section (200000 = the workload)")
     ap.add_argument("--ref-sample-mib", type=int, default=16)
     ap.add_argument("--quick", action="store_true",
-                    help="skip e2e, batched, short, serving and the cpu baseline")
+                    help="skip every section after the headline (e2e, batched, short, "
+                         "serving, masked, gather, cpu_baseline, sweep)")
     ap.add_argument("--sections", default="",
                     help="comma list of extra sections to run "
-                         "(e2e,batched,short,serving,masked,gather,cpu_baseline)")
+                         "(e2e,batched,short,serving,masked,gather,cpu_baseline,sweep)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")

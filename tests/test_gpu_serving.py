@@ -11,7 +11,7 @@ import pytest
 import torch
 
 from paper_2412_16370_gb300 import binding as pp
-from paper_2412_16370_gb300 import synth
+from paper_2412_16370_gb300 import synth, synth_device
 
 pytestmark = pytest.mark.gpu
 
@@ -22,7 +22,7 @@ MIB = 1 << 20
 def pool(gpu):
     n = 256 * MIB
     t = torch.empty(n + 64, dtype=torch.uint8, device=gpu)
-    t.random_(0, 256)
+    synth_device.random_(t, 2024)
     torch.cuda.synchronize()
     return t
 

@@ -13,7 +13,7 @@ import pytest
 import torch
 
 from paper_2412_16370_gb300 import binding as pp
-from paper_2412_16370_gb300 import synth
+from paper_2412_16370_gb300 import synth, synth_device
 
 pytestmark = pytest.mark.gpu
 
@@ -25,7 +25,7 @@ def _batch(dev, m, seed, hi=300000):
     sizes[::41] = 0
     offs = synth.csr_offsets(sizes)
     buf = torch.empty(int(offs[-1]) + 64, dtype=torch.uint8, device=dev)
-    buf.random_(0, 256)
+    synth_device.random_(buf, 500 + seed)
     base = buf[3:3 + int(offs[-1])]
     return base, torch.from_numpy(offs.view(np.int64)).to(dev)
 
