@@ -29,12 +29,14 @@ Under torchrun each rank runs an independent replica (weak scaling).
 from __future__ import annotations
 
 import argparse
+import contextlib
 import hashlib
 import json
 import os
 import platform
 import subprocess
 import sys
+import tempfile
 import threading
 import time
 
@@ -314,7 +316,21 @@ def run_ours(args):
     r1.record(stream)
     torch.cuda.synchronize()
     read_gbs = nbytes / (r0.elapsed_time(r1) / reps / 1e3) / 1e9
+    # the same read with the bytes staged in shared memory by cp.async.bulk
+    with _tune_entry(pp, "roofline", "roofline 256 2 1"):
+        rsum.zero_()
+        for _ in range(3):
+            pp.pospopcnt_roofline_read(data, rsum, nbytes, stream)
+        torch.cuda.synchronize()
+        r0.record(stream)
+        for _ in range(reps):
+            pp.pospopcnt_roofline_read(data, rsum, nbytes, stream)
+        r1.record(stream)
+        torch.cuda.synchronize()
+        bulk_gbs = nbytes / (r0.elapsed_time(r1) / reps / 1e3) / 1e9
+        bulk_ok = pp.pospopcnt_batch_status(stream) == pp.POSPOP_OK
 
+    tune_line = pp.pospopcnt_tune_describe().splitlines()[0]
     extra = {}
     sections = set(args.sections.split(",")) if args.sections else None
     want = (lambda k: sections is None or k in sections)
@@ -361,7 +377,7 @@ def run_ours(args):
                    "array_bytes": nbytes, "widths": list(WIDTHS),
                    "l2": "inputs (8 GiB) far larger than L2 (126 MB): no flush between steps",
                    "parallelism": f"replicas x{world}",
-                   "tune": pp.pospopcnt_tune_describe().splitlines()[0]},
+                   "tune": tune_line},
         "per_w": per_w,
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak,
                      "unit": "GB/s", "frac": round(achieved / hbm_peak, 4),
@@ -369,7 +385,10 @@ def run_ours(args):
                      "kernel": "pospop::stream_kernel (single-array count)",
                      "traffic_note": traffic_note},
         "read_roofline": {"GBps": round(read_gbs, 1), "frac_of_hbm_peak": round(read_gbs / hbm_peak, 4),
-                          "kernel": "pospop::roofline_kernel (sum of the input)"},
+                          "kernel": "pospop::roofline_kernel (sum of the input)",
+                          "bulk_staged_GBps": round(bulk_gbs, 1), "bulk_status_ok": bulk_ok,
+                          "bulk_kernel": "pospop::roofline_bulk_kernel<8,3> (cp.async.bulk into "
+                                         "shared memory, 3 x 8 KiB stages per warp)"},
         "gpu_launches": int(launches),
         "counts_consistent_across_w": consistent,
         "clocks": clocks,
@@ -523,6 +542,24 @@ def _batched(pp, synth, synth_device, dev, stream, large_gbs, hbm_peak, m=200000
             "one_hot_sums_ok": ok}
 
 
+@contextlib.contextmanager
+def _tune_entry(pp, kind, line):
+    """Run the body with the tune table's `kind` entry replaced by `line`."""
+    saved = pp.pospopcnt_tune_describe()
+    with tempfile.TemporaryDirectory() as td:
+        f = os.path.join(td, "tune.txt")
+        with open(f, "w") as fh:
+            fh.write("\n".join(l for l in saved.splitlines() if not l.startswith(kind)))
+            fh.write("\n" + line + "\n")
+        pp.pospopcnt_tune_load(f)
+        try:
+            yield
+        finally:
+            with open(f, "w") as fh:
+                fh.write(saved)
+            pp.pospopcnt_tune_load(f)
+
+
 def _short(pp, synth, synth_device, dev, stream, n=2000):
     """Short unaligned arrays (log-uniform 1 B .. 64 KiB), one launch per array."""
     import torch
@@ -546,6 +583,30 @@ def _short(pp, synth, synth_device, dev, stream, n=2000):
     torch.cuda.synchronize()
     wall = time.perf_counter() - t0
     dev_us = e0.elapsed_time(e1) * 1e3 / n
+
+    # the same calls straight through the C ABI (arguments prepared beforehand),
+    # with the tune table's programmatic dependent launch on, then off
+    L = pp.lib()
+    cp, sp = c.data_ptr(), stream.cuda_stream
+
+    def raw_loop():
+        bad = 0
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        e0.record(stream)
+        for w, p, s in calls:
+            bad |= L.pospopcnt_async(w, cp, p, s, sp)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if bad:
+            raise RuntimeError(pp.strerror(bad))
+        return e0.elapsed_time(e1) * 1e3 / n, (time.perf_counter() - t1) * 1e6 / n
+
+    raw_loop()
+    raw_dev, raw_host = raw_loop()
+    with _tune_entry(pp, "pdl", "pdl 0"):
+        raw_loop()
+        nopdl_dev, _ = raw_loop()
     # graph-replayed: the same launches captured once
     g = torch.cuda.CUDAGraph()
     s2 = torch.cuda.Stream()
@@ -565,7 +626,12 @@ def _short(pp, synth, synth_device, dev, stream, n=2000):
     return {"workload": f"{n} arrays, sizes log-uniform 1 B..64 KiB, start offsets 0..15, "
                         "w cycling 8/16/32/64, one launch each",
             "device_us_per_call": round(dev_us, 2), "host_us_per_call": round(wall * 1e6 / n, 2),
-            "graph_us_per_call": round(graph_us, 2)}
+            "c_abi_device_us_per_call": round(raw_dev, 2),
+            "c_abi_host_us_per_call": round(raw_host, 2),
+            "c_abi_device_us_per_call_pdl_off": round(nopdl_dev, 2),
+            "graph_us_per_call": round(graph_us, 2),
+            "note": "device_us/host_us: calls through the Python binding; c_abi_*: the same calls "
+                    "through the C entry point with prepared arguments"}
 
 
 def _serving(pp, synth, pool, pool_bytes, large_gbs, dev, loads=(0.3, 0.6, 0.9),

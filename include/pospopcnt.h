@@ -152,8 +152,11 @@ int pospopcnt_masked(int w, uint64_t *counts, const void *words, size_t n, const
 int pospopcnt_batch_noalloc(int w, uint64_t *counts, const void *base, const uint64_t *offsets,
                             size_t m, void *stream);
 
-/* Synchronise `stream` and return (then clear) the device-side status of
- * the last pospopcnt_batch call on it: POSPOP_OK or POSPOP_EINVAL. */
+/* Synchronise `stream` and return (then clear) the device-side status word of
+ * `stream`, set by the batched, gathered and roofline calls on it since it
+ * was last read: POSPOP_OK, POSPOP_EINVAL (decreasing offsets) or
+ * POSPOP_ETIMEDOUT (a staging wait of the bulk-copy roofline kernel
+ * expired). */
 int pospopcnt_batch_status(void *stream);
 
 /* Grow the workspace of `stream` so that batch calls with up to m_max
@@ -173,9 +176,13 @@ int pospopcnt_host(int w, uint64_t *counts, const void *bytes, size_t nbytes);
 /*
  * Roofline read kernel (the paper's "dummy" kernel of Section 5: it sums
  * the input and adds the sum to an output).  *sum (device, one uint64_t) +=
- * the sum of the 32-bit little-endian words of the 16-byte-aligned interior
- * of [bytes, bytes + nbytes).  It reads the input exactly like the counting
- * kernel and is the achievable-bandwidth reference for it.
+ * the exact sum (mod 2^64) of the 32-bit little-endian words of the
+ * 16-byte-aligned interior of [bytes, bytes + nbytes).  The tune table's
+ * `roofline` entry picks the form: direct loads exactly like the counting
+ * kernel's (load variants 0 and 1), or staging through shared memory with
+ * cp.async.bulk (load variant 2; an expired staging wait is reported by
+ * pospopcnt_batch_status).  It is the achievable-bandwidth reference for the
+ * counting kernels.
  */
 int pospopcnt_roofline_read(const void *bytes, size_t nbytes, uint64_t *sum, void *stream);
 

@@ -83,6 +83,7 @@ TuneTable default_tune() {
   t.roof = RoofTune{find_roof_variant(512, 1), 4};
   t.max_rows_per_warp = kMaxRowsPerWarp;
   t.regroup = 0;
+  t.pdl = 1;
   t.set_source("built-in defaults");
   return t;
 }
@@ -95,6 +96,8 @@ TuneTable default_tune() {
 //                                  several launches so that no warp takes more)
 //   short <0|1>                   (w = 8 sequences of <= 3 rows: 0 = transpose
 //                                  flush, 1 = per-lane bit regroup)
+//   pdl <0|1>                     (1 = programmatic dependent launch: a kernel's
+//                                  launch overlaps the previous kernel's run)
 int parse_tune(const char *text, TuneTable *out) {
   TuneTable t = default_tune();
   std::string s(text);
@@ -132,6 +135,10 @@ int parse_tune(const char *text, TuneTable *out) {
       unsigned rg;
       if (sscanf(line.c_str(), "%*s %u", &rg) != 1 || rg > 1) return POSPOP_EINVAL;
       t.regroup = rg;
+    } else if (strcmp(kind, "pdl") == 0) {
+      unsigned v;
+      if (sscanf(line.c_str(), "%*s %u", &v) != 1 || v > 1) return POSPOP_EINVAL;
+      t.pdl = v;
     } else if (strcmp(kind, "split") == 0) {
       unsigned long long mr;
       if (sscanf(line.c_str(), "%*s %llu", &mr) != 1 || mr < 1 || mr > kMaxRowsPerWarp)
@@ -178,6 +185,8 @@ std::string format_tune(const DevCtx &ctx, const TuneTable &t) {
   }
   snprintf(line, sizeof line, "# short <0 transpose | 1 per-lane regroup> (w = 8, <= 3 rows)\nshort %u\n",
            t.regroup);
+  s += line;
+  snprintf(line, sizeof line, "# pdl <0 | 1 programmatic dependent launch>\npdl %u\n", t.pdl);
   s += line;
   if (t.max_rows_per_warp != kMaxRowsPerWarp) {
     snprintf(line, sizeof line, "split %llu\n", (unsigned long long)t.max_rows_per_warp);
@@ -257,9 +266,12 @@ static int init_ctx(DevCtx &c, int device) {
     c.occ_batch[i] = n > 0 ? n : 1;
   }
   for (int i = 0; i < roofline_variant_count(); i++) {
+    const Variant &v = roofline_variant(i);
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, roofline_variant(i).fn,
-                                                      roofline_variant(i).bs, 0) != cudaSuccess) {
+    if ((v.smem > 0 && cudaFuncSetAttribute(v.fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            v.smem) != cudaSuccess) ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, v.fn, v.bs, (size_t)v.smem) !=
+            cudaSuccess) {
       cudaGetLastError();
       return POSPOP_ECUDA;
     }
@@ -357,6 +369,27 @@ static bool device_addressable(const void *p, int device, const void **devptr) {
 }
 
 // ---------------------------------------------------------------------------
+// Kernel launch, optionally as a programmatic dependent launch.
+// ---------------------------------------------------------------------------
+cudaError_t launch_kernel(const void *fn, dim3 grid, dim3 block, void **args, cudaStream_t stream,
+                          bool pdl, size_t smem) {
+  if (!pdl) return cudaLaunchKernel(fn, grid, block, args, smem, stream);
+  cudaLaunchConfig_t cfg;
+  memset(&cfg, 0, sizeof cfg);
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = stream;
+  cudaLaunchAttribute at[1];
+  memset(at, 0, sizeof at);
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelExC(&cfg, fn, args);
+}
+
+// ---------------------------------------------------------------------------
 // Single-array launches.
 // ---------------------------------------------------------------------------
 StreamPlan plan_stream(const DevCtx &ctx, const TuneTable &t, uint64_t rows) {
@@ -412,7 +445,8 @@ int launch_stream_with(const DevCtx &ctx, const TuneTable &t, int w, unsigned lo
     P.row_begin = rb;
     P.row_end = (R - rb > pl.rows_per_launch) ? rb + pl.rows_per_launch : R;
     void *args[] = {&P};
-    if (cudaLaunchKernel(v.fn, dim3(pl.grid), dim3(pl.block), args, 0, stream) != cudaSuccess) {
+    if (launch_kernel(v.fn, dim3(pl.grid), dim3(pl.block), args, stream, t.pdl != 0) !=
+        cudaSuccess) {
       cudaGetLastError();
       return POSPOP_ECUDA;
     }
@@ -432,7 +466,7 @@ int launch_stream(DevCtx &ctx, int w, unsigned long long *counts, const void *by
 }
 
 int launch_roofline_with(const DevCtx &ctx, const RoofTune &rt, const void *bytes, size_t nbytes,
-                         unsigned long long *sum, cudaStream_t stream) {
+                         unsigned long long *sum, int *status, cudaStream_t stream, bool pdl) {
   const uint64_t p0 = (uint64_t)bytes;
   const uint64_t A = (p0 + 15u) & ~15ull, E = (p0 + nbytes) & ~15ull;
   if (E <= A) return POSPOP_OK;
@@ -440,16 +474,21 @@ int launch_roofline_with(const DevCtx &ctx, const RoofTune &rt, const void *byte
   P.A = reinterpret_cast<const uint8_t *>(A);
   P.G = (E - A) >> 4;
   P.sum = sum;
+  P.status = status;
   const Variant &v = roofline_variant(rt.variant);
+  if (v.smem > 0 && !status) return POSPOP_EINVAL;
   int cps = rt.ctas_per_sm;   // above the occupancy limit: waves, as for the count
   if (cps < 1) cps = 1;
-  const uint64_t rows = (P.G + 31) >> 5;
-  uint64_t grid = (rows + (v.bs / 32) - 1) / (v.bs / 32);
+  // a warp's unit of work: a row of 32 granules (direct loads) or a chunk of
+  // 512 granules (bulk-copy staging)
+  const uint64_t units = v.smem > 0 ? (P.G + 511) >> 9 : (P.G + 31) >> 5;
+  uint64_t grid = (units + (v.bs / 32) - 1) / (v.bs / 32);
   const uint64_t max_grid = (uint64_t)ctx.sms * cps;
   if (grid > max_grid) grid = max_grid;
   if (grid < 1) grid = 1;
   void *args[] = {&P};
-  if (cudaLaunchKernel(v.fn, dim3((unsigned)grid), dim3(v.bs), args, 0, stream) != cudaSuccess) {
+  if (launch_kernel(v.fn, dim3((unsigned)grid), dim3(v.bs), args, stream, pdl, (size_t)v.smem) !=
+      cudaSuccess) {
     cudaGetLastError();
     return POSPOP_ECUDA;
   }
@@ -515,15 +554,16 @@ static int get_ws(DevCtx &ctx, cudaStream_t stream, size_t m, Workspace **out) {
   return POSPOP_OK;
 }
 
-static int launch_plan(const DevCtx &ctx, const PlanParams &pp, cudaStream_t stream) {
-  (void)ctx;
+// The three planning kernels; items_fn is plan_items_kernel for the
+// array source (CSR offsets or gathered regions).
+static int launch_plan(const void *items_fn, const PlanParams &pp, cudaStream_t stream, bool pdl) {
   PlanParams P = pp;
   void *args[] = {&P};
-  if (cudaLaunchKernel(plan_items_fn(), dim3(P.nblocks), dim3(kPlanThreads), args, 0, stream) !=
+  if (launch_kernel(items_fn, dim3(P.nblocks), dim3(kPlanThreads), args, stream, pdl) !=
           cudaSuccess ||
-      cudaLaunchKernel(plan_scan_fn(), dim3(1), dim3(kPlanThreads), args, 0, stream) !=
+      launch_kernel(plan_scan_fn(), dim3(1), dim3(kPlanThreads), args, stream, pdl) !=
           cudaSuccess ||
-      cudaLaunchKernel(plan_apply_fn(), dim3(P.nblocks), dim3(kPlanThreads), args, 0, stream) !=
+      launch_kernel(plan_apply_fn(), dim3(P.nblocks), dim3(kPlanThreads), args, stream, pdl) !=
           cudaSuccess) {
     cudaGetLastError();
     return POSPOP_ECUDA;
@@ -556,7 +596,7 @@ int launch_batch_with(DevCtx &ctx, const TuneTable &t, int w, unsigned long long
   pp.status = ws->status;
   pp.item_rows = t.batch.item_rows;
   pp.nblocks = (uint32_t)((m + kPlanChunk - 1) / kPlanChunk);
-  int rc = launch_plan(ctx, pp, stream);
+  int rc = launch_plan(plan_items_fn(), pp, stream, t.pdl != 0);
   if (rc != POSPOP_OK) return rc;
 
   BatchParams bp;
@@ -578,8 +618,8 @@ int launch_batch_with(DevCtx &ctx, const TuneTable &t, int w, unsigned long long
                                                                  : ctx.occ_batch[t.batch.variant];
   if (cps < 1) cps = 1;
   void *args[] = {&bp};
-  if (cudaLaunchKernel(v.fn, dim3((unsigned)(ctx.sms * cps)), dim3(v.bs), args, 0, stream) !=
-      cudaSuccess) {
+  if (launch_kernel(v.fn, dim3((unsigned)(ctx.sms * cps)), dim3(v.bs), args, stream,
+                    t.pdl != 0) != cudaSuccess) {
     cudaGetLastError();
     return POSPOP_ECUDA;
   }
@@ -614,16 +654,8 @@ static int launch_gather_with(DevCtx &ctx, const TuneTable &t, int w, unsigned l
   pp.status = ws->status;
   pp.item_rows = t.batch.item_rows;
   pp.nblocks = (uint32_t)((n + kPlanChunk - 1) / kPlanChunk);
-  void *pargs[] = {&pp};
-  if (cudaLaunchKernel(plan_items_gather_fn(), dim3(pp.nblocks), dim3(kPlanThreads), pargs, 0,
-                       stream) != cudaSuccess ||
-      cudaLaunchKernel(plan_scan_fn(), dim3(1), dim3(kPlanThreads), pargs, 0, stream) !=
-          cudaSuccess ||
-      cudaLaunchKernel(plan_apply_fn(), dim3(pp.nblocks), dim3(kPlanThreads), pargs, 0, stream) !=
-          cudaSuccess) {
-    cudaGetLastError();
-    return POSPOP_ECUDA;
-  }
+  const int prc = launch_plan(plan_items_gather_fn(), pp, stream, t.pdl != 0);
+  if (prc != POSPOP_OK) return prc;
   BatchParams bp;
   memset(&bp, 0, sizeof bp);
   bp.gptrs = ptrs;
@@ -641,12 +673,12 @@ static int launch_gather_with(DevCtx &ctx, const TuneTable &t, int w, unsigned l
   int cps = std::min(t.batch.ctas_per_sm, ctx.occ_batch[t.batch.variant]);
   if (cps < 1) cps = 1;
   void *bargs[] = {&bp};
-  if (cudaLaunchKernel(v.fn, dim3((unsigned)(ctx.sms * cps)), dim3(v.bs), bargs, 0, stream) !=
-      cudaSuccess) {
+  if (launch_kernel(v.fn, dim3((unsigned)(ctx.sms * cps)), dim3(v.bs), bargs, stream,
+                    t.pdl != 0) != cudaSuccess) {
     cudaGetLastError();
     return POSPOP_ECUDA;
   }
-  note_launches(4);
+  note_launches(1);
   return POSPOP_OK;
 }
 
@@ -687,7 +719,8 @@ static int launch_select_with(const DevCtx &ctx, const TuneTable &t, int w,
     P.row_begin = rb;
     P.row_end = (R - rb > pl.rows_per_launch) ? rb + pl.rows_per_launch : R;
     void *args[] = {&Q};
-    if (cudaLaunchKernel(v.fn, dim3(pl.grid), dim3(pl.block), args, 0, stream) != cudaSuccess) {
+    if (launch_kernel(v.fn, dim3(pl.grid), dim3(pl.block), args, stream, t.pdl != 0) !=
+        cudaSuccess) {
       cudaGetLastError();
       return POSPOP_ECUDA;
     }
@@ -964,7 +997,7 @@ int pospopcnt_batch_status(void *stream) {
     cudaGetLastError();
     return POSPOP_ECUDA;
   }
-  return h == 0 ? POSPOP_OK : POSPOP_EINVAL;
+  return h == 0 ? POSPOP_OK : h == POSPOP_ETIMEDOUT ? POSPOP_ETIMEDOUT : POSPOP_EINVAL;
 }
 
 int pospopcnt_reserve(size_t m_max, void *stream) {
@@ -995,13 +1028,27 @@ int pospopcnt_roofline_read(const void *bytes, size_t nbytes, uint64_t *sum, voi
   const void *db = nullptr, *ds = nullptr;
   if (!device_addressable(bytes, c->device, &db) || !device_addressable(sum, c->device, &ds))
     return POSPOP_EPTR;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
   RoofTune rt;
+  bool pdl;
+  int *status = nullptr;
   {
     std::lock_guard<std::mutex> g(c->mu);
     rt = c->tune.roof;
+    pdl = c->tune.pdl != 0;
+    if (roofline_variant(rt.variant).smem > 0) {   // bulk-copy form: the stream's status word
+      Workspace *ws = nullptr;
+      rc = get_ws(*c, s, 0, &ws);
+      if (rc != POSPOP_OK) return rc;
+      status = ws->status;
+    }
+  }
+  if (status && cudaMemsetAsync(status, 0, sizeof(int), s) != cudaSuccess) {
+    cudaGetLastError();
+    return POSPOP_ECUDA;
   }
   return launch_roofline_with(*c, rt, db, nbytes, (unsigned long long *)const_cast<void *>(ds),
-                              static_cast<cudaStream_t>(stream));
+                              status, s, pdl);
 }
 
 int pospopcnt_plan(int w, size_t nbytes, uint32_t plan[8]) {

@@ -13,6 +13,7 @@ namespace pospop {
 __global__ void __launch_bounds__(kPlanThreads) plan_scan_kernel(PlanParams P) {
   __shared__ uint64_t red[32];
   __shared__ uint64_t carry;
+  pdl_enter();
   if (threadIdx.x == 0) carry = 0;
   __syncthreads();
   for (uint32_t b0 = 0; b0 < P.nblocks; b0 += kPlanThreads) {
@@ -34,6 +35,7 @@ __global__ void __launch_bounds__(kPlanThreads) plan_scan_kernel(PlanParams P) {
 // item_start[a] = exclusive prefix sum of the per-array item counts.
 __global__ void __launch_bounds__(kPlanThreads) plan_apply_kernel(PlanParams P) {
   __shared__ uint64_t red[32];
+  pdl_enter();
   const uint64_t a0 = (uint64_t)blockIdx.x * kPlanChunk + (uint64_t)threadIdx.x * kPlanPerThread;
   uint64_t it[kPlanPerThread];
   uint64_t local = 0;

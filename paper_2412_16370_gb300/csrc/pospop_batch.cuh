@@ -77,6 +77,7 @@ __device__ __forceinline__ uint64_t block_inclusive_scan(uint64_t v, uint64_t *w
 template <int SRC>
 __global__ void __launch_bounds__(kPlanThreads) plan_items_kernel(PlanParams P) {
   __shared__ uint64_t red[32];
+  pdl_enter();
   const uint64_t a0 = (uint64_t)blockIdx.x * kPlanChunk + (uint64_t)threadIdx.x * kPlanPerThread;
   uint64_t local = 0;
   bool bad = false;
@@ -134,6 +135,7 @@ __global__ void __launch_bounds__(BS, MINB) batch_kernel(BatchParams P) {
   // Gathered regions all add into one counter array: accumulate per block in
   // shared memory, one atomic per counter per block at the end.
   __shared__ unsigned long long gacc[SRC == kSrcGather ? 64 : 1];
+  pdl_enter();
   if (SRC == kSrcGather) {
     if (threadIdx.x < 64) gacc[threadIdx.x] = 0ull;
     __syncthreads();

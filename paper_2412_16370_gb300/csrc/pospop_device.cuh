@@ -36,6 +36,21 @@ constexpr int kGranule = 16;               // bytes per granule (one uint4 per l
 constexpr int kRowBytes = 32 * kGranule;   // 512 bytes per warp row
 
 // ---------------------------------------------------------------------------
+// Programmatic dependent launch.  A kernel launched with programmatic stream
+// serialization may be scheduled while the kernel before it on the stream is
+// still running.  griddepcontrol.wait blocks until that kernel has completed
+// and its memory operations are visible, so every kernel below runs it before
+// touching global memory: stream order is kept exactly, and only the launch
+// itself overlaps the previous kernel.  griddepcontrol.launch_dependents then
+// lets the next such kernel be scheduled.  Without the launch attribute both
+// instructions have no effect.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void pdl_enter() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+// ---------------------------------------------------------------------------
 // Bit-parallel full adder (Section 3.1.1, Eq. 3): one lop3 per output.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ uint32_t lop3_parity(uint32_t a, uint32_t b, uint32_t c) {

@@ -103,6 +103,7 @@ struct RooflineParams {
   const uint8_t *A;             // 16-byte aligned
   uint64_t G;                   // whole granules
   unsigned long long *sum;
+  int *status;                  // bulk-copy form: set to POSPOP_ETIMEDOUT if a wait expires
 };
 
 // Kernel variant descriptor.  `fn` is the __global__ function to launch
@@ -113,6 +114,7 @@ struct Variant {
   int minb;     // __launch_bounds__ min blocks per SM
   int depth;    // 16 or 32 vectors per flush
   int hint;     // load variant
+  int smem;     // dynamic shared memory bytes per block
 };
 
 constexpr int kPlanThreads = 1024;

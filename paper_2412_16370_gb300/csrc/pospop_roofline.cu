@@ -1,0 +1,191 @@
+// pospop_roofline.cu -- the roofline read kernels (Section 5's "dummy"
+// kernel: sum the input and add the sum to an output), the achievable-read
+// reference for the counting kernels.
+//
+// Two ways to stream the same bytes:
+//  * roofline_kernel: the counting kernel's own loads (one 16-byte
+//    ld.global.nc per lane, 512-byte rows per warp, 16 rows in flight per
+//    thread) and row schedule, with an add in place of the counting;
+//  * roofline_bulk_kernel: the bytes are staged in shared memory by the
+//    copy engine (cp.async.bulk, one-dimensional TMA, completion counted on
+//    an mbarrier): each warp keeps a ring of S chunks of 8 KiB in flight and
+//    sums a chunk from shared memory once its barrier phase completes.
+// Both compute the exact sum of the 32-bit little-endian words.
+#include <cstdint>
+
+#include "pospop_device.cuh"
+#include "pospop_internal.h"
+#include "pospopcnt.h"
+
+namespace pospop {
+
+__device__ __forceinline__ unsigned long long sum_words(const V4 &v) {
+  return (unsigned long long)v.x[0] + v.x[1] + (unsigned long long)v.x[2] + v.x[3];
+}
+
+// ---------------------------------------------------------------------------
+// Direct loads.  Warp gw of NW reads rows gw, gw + NW, ... (rows of 32
+// granules), 16 rows per step.
+// ---------------------------------------------------------------------------
+template <int BS, int HINT>
+__global__ void __launch_bounds__(BS) roofline_kernel(RooflineParams P) {
+  pdl_enter();
+  constexpr unsigned WPB = BS / 32;
+  const unsigned lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+  const uint64_t NW = (uint64_t)gridDim.x * WPB;
+  const uint64_t R = (P.G + 31) >> 5;
+  const uint64_t Rfull = P.G >> 5;
+  unsigned long long sum = 0;
+  uint64_t row = (uint64_t)blockIdx.x * WPB + warp;
+  for (; row + 15 * NW < Rfull; row += 16 * NW) {
+    V4 v[16];
+#pragma unroll
+    for (int k = 0; k < 16; k++)
+      v[k] = ldg_granule<HINT>(P.A + ((row + k * NW) * 32 + lane) * kGranule);
+#pragma unroll
+    for (int k = 0; k < 16; k++) sum += sum_words(v[k]);
+  }
+  for (; row < R; row += NW) {
+    const uint64_t g = row * 32 + lane;
+    if (g < P.G) sum += sum_words(ldg_granule<HINT>(P.A + g * kGranule));
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) sum += __shfl_xor_sync(kFull, sum, off);
+  if (lane == 0 && sum) atomicAdd(P.sum, sum);
+}
+
+// ---------------------------------------------------------------------------
+// Bulk-copy staging.
+// ---------------------------------------------------------------------------
+constexpr uint32_t kBulkChunk = 8192;                  // bytes per chunk = 512 granules
+constexpr long long kBulkWaitCycles = 1ll << 31;       // about a second at 2 GHz
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+}
+
+// Expect `bytes` on the barrier's current phase (this thread's arrival), then
+// copy them from global to shared memory; the copy completes the bytes.
+// dst, src and bytes are multiples of 16.
+__device__ __forceinline__ void bulk_copy(uint32_t dst, const void *src, uint32_t bytes,
+                                          uint32_t bar) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          dst),
+      "l"(src), "r"(bytes), "r"(bar)
+      : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(done)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+
+// Wait for the barrier phase with the given parity to complete; false if it
+// has not after kBulkWaitCycles.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  const long long t0 = clock64();
+  while (!mbar_try(bar, parity))
+    if (clock64() - t0 > kBulkWaitCycles) return false;
+  return true;
+}
+
+template <int NW, int S>
+__global__ void __launch_bounds__(NW * 32, 1) roofline_bulk_kernel(RooflineParams P) {
+  extern __shared__ __align__(128) uint8_t smem[];
+  pdl_enter();
+  const unsigned lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+  uint8_t *ring = smem + (size_t)warp * S * kBulkChunk;
+  uint64_t *bars = reinterpret_cast<uint64_t *>(smem + (size_t)NW * S * kBulkChunk) + warp * S;
+  const uint64_t TW = (uint64_t)gridDim.x * NW;
+  const uint64_t gw = (uint64_t)blockIdx.x * NW + warp;
+  const uint64_t nch = (P.G + 511) >> 9;
+  // granules in chunk c (512 except for the last)
+  auto granules = [&](uint64_t c) -> uint32_t {
+    const uint64_t left = P.G - (c << 9);
+    return (uint32_t)(left < 512 ? left : 512);
+  };
+  if (lane == 0) {
+    for (int k = 0; k < S; k++) mbar_init(smem_addr(bars + k));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    for (int k = 0; k < S; k++) {
+      const uint64_t c = gw + (uint64_t)k * TW;
+      if (c < nch)
+        bulk_copy(smem_addr(ring + k * kBulkChunk), P.A + c * kBulkChunk, granules(c) * 16u,
+                  smem_addr(bars + k));
+    }
+  }
+  __syncwarp();
+  unsigned long long sum = 0;
+  uint64_t it = 0;
+  bool timed_out = false;
+  for (uint64_t c = gw; c < nch; c += TW, it++) {
+    const int k = (int)(it % S);
+    // warp-uniform: every lane leaves together if any lane's wait expired
+    if (!__all_sync(kFull, mbar_wait(smem_addr(bars + k), (uint32_t)((it / S) & 1u)))) {
+      timed_out = true;
+      break;
+    }
+    const uint32_t ng = granules(c);
+    const uint4 *v = reinterpret_cast<const uint4 *>(ring + k * kBulkChunk);
+#pragma unroll 4
+    for (uint32_t g = lane; g < ng; g += 32) {
+      const uint4 x = v[g];
+      sum += (unsigned long long)x.x + x.y + (unsigned long long)x.z + x.w;
+    }
+    __syncwarp();   // every lane has read the stage before it is refilled
+    const uint64_t nx = c + (uint64_t)S * TW;
+    if (lane == 0 && nx < nch) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      bulk_copy(smem_addr(ring + k * kBulkChunk), P.A + nx * kBulkChunk, granules(nx) * 16u,
+                smem_addr(bars + k));
+    }
+  }
+  if (timed_out) {
+    // report, then wait (bounded again) for this warp's copies still in
+    // flight so that none lands after the block has left
+    if (lane == 0 && P.status) atomicExch(P.status, POSPOP_ETIMEDOUT);
+    for (uint64_t j = 0, c = gw + it * TW; j < (uint64_t)S && c < nch; j++, c += TW)
+      (void)mbar_wait(smem_addr(bars + (int)((it + j) % S)), (uint32_t)(((it + j) / S) & 1u));
+    return;
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) sum += __shfl_xor_sync(kFull, sum, off);
+  if (lane == 0 && sum) atomicAdd(P.sum, sum);
+}
+
+template <int NW, int S>
+constexpr int bulk_smem() {
+  return NW * S * (int)kBulkChunk + NW * S * 8;
+}
+
+// ---------------------------------------------------------------------------
+// Variant table.  Load variant (hint) 0/1: direct loads without/with the L2
+// 256-byte prefetch hint; 2: bulk-copy staging (dynamic shared memory).
+// ---------------------------------------------------------------------------
+#define POSPOP_RV(BS, H) \
+  Variant{reinterpret_cast<const void *>(&roofline_kernel<BS, H>), BS, 1, 0, H, 0}
+#define POSPOP_RB(NW, S)                                                                   \
+  Variant{reinterpret_cast<const void *>(&roofline_bulk_kernel<NW, S>), NW * 32, 1, 0, 2, \
+          bulk_smem<NW, S>()}
+
+static const Variant kRoof[] = {POSPOP_RV(256, 0), POSPOP_RV(256, 1),  POSPOP_RV(512, 0),
+                                POSPOP_RV(512, 1), POSPOP_RV(1024, 0), POSPOP_RV(1024, 1),
+                                POSPOP_RB(8, 3),   POSPOP_RB(4, 3)};
+
+int roofline_variant_count() { return (int)(sizeof(kRoof) / sizeof(kRoof[0])); }
+const Variant &roofline_variant(int i) { return kRoof[i]; }
+
+}  // namespace pospop

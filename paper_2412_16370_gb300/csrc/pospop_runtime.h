@@ -43,6 +43,7 @@ struct TuneTable {
   RoofTune roof;
   uint64_t max_rows_per_warp;   // single-array launch split (<= kMaxRowsPerWarp)
   uint32_t regroup;             // w = 8 short sequences: 1 = per-lane bit regroup, 0 = transpose
+  uint32_t pdl;                 // 1 = launch with programmatic stream serialization
   char source[240];             // where the table came from (copied with the table: no heap)
   void set_source(const char *s);
 };
@@ -112,9 +113,16 @@ int launch_stream(DevCtx &ctx, int w, unsigned long long *counts, const void *by
                   size_t nbytes, cudaStream_t stream);
 int launch_batch_with(DevCtx &ctx, const TuneTable &t, int w, unsigned long long *counts,
                       const void *base, const uint64_t *offsets, size_t m, cudaStream_t stream);
+// status: a device int the bulk-copy form sets to POSPOP_ETIMEDOUT when a
+// staging wait expires (required for that form, ignored by the others).
 int launch_roofline_with(const DevCtx &ctx, const RoofTune &rt, const void *bytes, size_t nbytes,
-                         unsigned long long *sum, cudaStream_t stream);
+                         unsigned long long *sum, int *status, cudaStream_t stream, bool pdl);
 
 void note_launches(uint64_t n);
+
+// cudaLaunchKernel, or with pdl set, the same launch with programmatic stream
+// serialization (the kernel waits for its predecessor in pdl_enter()).
+cudaError_t launch_kernel(const void *fn, dim3 grid, dim3 block, void **args, cudaStream_t stream,
+                          bool pdl, size_t smem = 0);
 
 }  // namespace pospop

@@ -13,6 +13,7 @@ namespace pospop {
 template <int BS, int MINB, int DEPTH, int HINT, int WLOG>
 __global__ void __launch_bounds__(BS, MINB) select_kernel(SelectParams Q) {
   __shared__ unsigned long long acc[64];
+  pdl_enter();
   const StreamParams &P = Q.sp;
   const unsigned lane = threadIdx.x & 31u;
   const unsigned warp = threadIdx.x >> 5;

@@ -1,5 +1,5 @@
 // pospop_stream.cu -- the sm_103a single-array kernel of the positional
-// population count and the roofline read kernel.
+// population count.
 //
 // The per-thread algorithm is the paper's (arXiv 2412.16370, Section 4:
 // CSA_15 head reduction, CSA_16+4 main loop, a16 accumulation, final
@@ -31,6 +31,7 @@ __device__ __forceinline__ Span to_span(const SpanH &h) {
 template <int BS, int MINB, int DEPTH, int HINT, bool PAR2 = false>
 __global__ void __launch_bounds__(BS, MINB) stream_kernel(StreamParams P) {
   __shared__ unsigned long long acc[256];
+  pdl_enter();
   const unsigned lane = threadIdx.x & 31u;
   const unsigned warp = threadIdx.x >> 5;
   for (int j = threadIdx.x; j < 256; j += BS) acc[j] = 0ull;
@@ -68,48 +69,10 @@ __global__ void __launch_bounds__(BS, MINB) stream_kernel(StreamParams P) {
 }
 
 // ---------------------------------------------------------------------------
-// Roofline read kernel (Section 5's "dummy" kernel: sum the input, add the
-// sum to the output).  Same row schedule and loads as stream_kernel, with a
-// plain add in place of the counting.
-// ---------------------------------------------------------------------------
-template <int BS, int HINT>
-__global__ void __launch_bounds__(BS) roofline_kernel(RooflineParams P) {
-  constexpr unsigned WPB = BS / 32;
-  const unsigned lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
-  const uint64_t NW = (uint64_t)gridDim.x * WPB;
-  const uint64_t R = (P.G + 31) >> 5;
-  const uint64_t Rfull = P.G >> 5;
-  unsigned long long sum = 0;
-  uint64_t row = (uint64_t)blockIdx.x * WPB + warp;
-  for (; row + 15 * NW < Rfull; row += 16 * NW) {
-    V4 v[16];
-#pragma unroll
-    for (int k = 0; k < 16; k++)
-      v[k] = ldg_granule<HINT>(P.A + ((row + k * NW) * 32 + lane) * kGranule);
-    uint32_t s32 = 0;
-#pragma unroll
-    for (int k = 0; k < 16; k++) s32 += v[k].x[0] + v[k].x[1] + v[k].x[2] + v[k].x[3];
-    sum += s32;  // may wrap in 32 bits per group; the sum is a sink, not a result
-  }
-  for (; row < R; row += NW) {
-    const uint64_t g = row * 32 + lane;
-    if (g < P.G) {
-      const V4 v = ldg_granule<HINT>(P.A + g * kGranule);
-      sum += (unsigned long long)v.x[0] + v.x[1] + v.x[2] + v.x[3];
-    }
-  }
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) sum += __shfl_xor_sync(kFull, sum, off);
-  if (lane == 0 && sum) atomicAdd(P.sum, sum);
-}
-
-// ---------------------------------------------------------------------------
 // Variant tables (every variant fits 128 registers per thread, no spills).
 // ---------------------------------------------------------------------------
 #define POSPOP_SV(BS, MINB, D, H) \
   Variant{reinterpret_cast<const void *>(&stream_kernel<BS, MINB, D, H>), BS, MINB, D, H}
-#define POSPOP_RV(BS, H) \
-  Variant{reinterpret_cast<const void *>(&roofline_kernel<BS, H>), BS, 1, 0, H}
 #define POSPOP_FAMILY(M)                                                  \
   M(256, 2, 16, 0), M(256, 2, 16, 1), M(256, 2, 32, 0), M(256, 2, 32, 1), \
   M(512, 1, 16, 0), M(512, 1, 16, 1), M(512, 1, 32, 0), M(512, 1, 32, 1), \
@@ -122,14 +85,10 @@ static const Variant kStream[] = {POSPOP_FAMILY(POSPOP_SV)};
   Variant{reinterpret_cast<const void *>(&stream_kernel<BS, MINB, 16, H, true>), BS, MINB, 16, H}
 static const Variant kStream256[] = {POSPOP_SV256(512, 1, 0), POSPOP_SV256(512, 1, 1),
                                      POSPOP_SV256(256, 2, 1), POSPOP_SV256(128, 4, 1)};
-static const Variant kRoof[] = {POSPOP_RV(256, 0), POSPOP_RV(256, 1), POSPOP_RV(512, 0),
-                                POSPOP_RV(512, 1), POSPOP_RV(1024, 0), POSPOP_RV(1024, 1)};
 
 int stream_variant_count() { return (int)(sizeof(kStream) / sizeof(kStream[0])); }
 int stream256_variant_count() { return (int)(sizeof(kStream256) / sizeof(kStream256[0])); }
 const Variant &stream256_variant(int i) { return kStream256[i]; }
 const Variant &stream_variant(int i) { return kStream[i]; }
-int roofline_variant_count() { return (int)(sizeof(kRoof) / sizeof(kRoof[0])); }
-const Variant &roofline_variant(int i) { return kRoof[i]; }
 
 }  // namespace pospop

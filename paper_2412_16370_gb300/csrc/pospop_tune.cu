@@ -175,22 +175,34 @@ extern "C" int pospopcnt_autotune(size_t max_bytes, const char *path) {
   }
 
   // --- roofline read kernel -------------------------------------------------
-  {
-    double best_ms =
-        tm.time([&] { return launch_roofline_with(*c, best.roof, buf, max_bytes, counts, tm.s); });
-    if (best_ms <= 0) best_ms = 1e30;
+  // (the bulk-copy form reports an expired staging wait in *dstatus; such a
+  // candidate is never chosen)
+  int *dstatus = nullptr;
+  if (cudaMalloc(&dstatus, sizeof(int)) == cudaSuccess &&
+      cudaMemset(dstatus, 0, sizeof(int)) == cudaSuccess) {
+    auto status_ok = [&] {
+      int h = -1;
+      return cudaMemcpy(&h, dstatus, sizeof(int), cudaMemcpyDeviceToHost) == cudaSuccess && h == 0;
+    };
+    double best_ms = tm.time([&] {
+      return launch_roofline_with(*c, best.roof, buf, max_bytes, counts, dstatus, tm.s,
+                                  best.pdl != 0);
+    });
+    if (best_ms <= 0 || !status_ok()) best_ms = 1e30;
     for (int v = 0; v < roofline_variant_count(); v++)
       for (int cps = 1; cps <= 4 * c->occ_roof[v]; cps++) {
         const RoofTune rt{v, cps};
         const double ms = tm.time([&] {
-          return launch_roofline_with(*c, rt, buf, max_bytes, counts, tm.s);
+          return launch_roofline_with(*c, rt, buf, max_bytes, counts, dstatus, tm.s, best.pdl != 0);
         });
+        if (!status_ok()) break;
         if (ms > 0 && ms < 0.99 * best_ms) {
           best_ms = ms;
           best.roof = rt;
         }
       }
   }
+  if (dstatus) cudaFree(dstatus);
 
   cudaStreamSynchronize(tm.s);
   if (doff) cudaFree(doff);
