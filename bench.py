@@ -644,7 +644,9 @@ def _serving(pp, synth, pool, pool_bytes, large_gbs, dev, loads=(0.3, 0.6, 0.9),
     mean = (hi - lo) / math.log((hi + 1) / lo)      # mean of the log-uniform size
     out = {"workload": "Poisson arrivals; w uniform in {8,16,32,64}; sizes log-uniform "
                        "64 B..256 MiB at uniform offsets of the resident 8 GiB array",
-           "mem_budget_bytes": budget, "max_inflight": 4096, "batch_streams": 8, "loads": []}
+           "mem_budget_bytes": budget, "max_inflight": 4096, "batch_streams_per_size_class": 8,
+           "size_classes": "below 1 MiB / 16 MiB / 128 MiB / above, on prioritised streams",
+           "loads": []}
     for k, load in enumerate(loads):
         rate = load * large_gbs * 1e9 / mean
         n = max(100, int(rate * duration_s))

@@ -225,11 +225,16 @@ int pospopcnt_graph_destroy(void *graph);
  *
  * A request is admitted when the input bytes of all admitted, unfinished
  * requests plus its own fit `mem_budget` and fewer than `max_inflight` are
- * admitted; admitted requests are gathered into one launch as soon as one of
- * the server's `max_batches` streams is free, so requests arriving while
- * others run are counted in the next batch while earlier batches are still
- * on the device.  Each result is the same as the request's single-array
- * count.  Waits are bounded by the caller's timeouts.
+ * admitted.  Admitted requests fall into size classes (below 1 MiB, 16 MiB,
+ * 128 MiB, and above; as many classes as the device has stream priority
+ * levels, at most four), and each class has `max_batches` streams with a
+ * priority that falls as the class grows.  A class's admitted requests are
+ * gathered into one batch (at most 1024 requests) as soon as one of its
+ * streams is free, so requests arriving while others run are counted in the
+ * next batch while earlier batches are still on the device, and blocks of a
+ * smaller class run before waiting blocks of a larger one.  Each result is
+ * the same as the request's single-array count.  Waits are bounded by the
+ * caller's timeouts.
  * ---------------------------------------------------------------------------
  */
 typedef struct pospop_server pospop_server;

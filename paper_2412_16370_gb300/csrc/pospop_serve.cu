@@ -7,8 +7,16 @@
 // free; admitted requests that are not yet on the GPU are gathered into one
 // batch as soon as one of the server's batch streams is free, so requests
 // that arrive while others run are counted in the next batch, overlapping on
-// the device with the batches already in flight.  A batch is one launch of
-// serve_kernel (pospop_desc.cu) per kServeMax requests: the requests and
+// the device with the batches already in flight.  Requests fall into size
+// classes (below 1 MiB, 16 MiB, 128 MiB, and above), each served by its own
+// batch streams with a stream priority that falls as the class grows, and
+// the counting grids are not persistent (one work item per warp, so blocks
+// retire every few microseconds): whenever a block of a large request's
+// batch retires, the block scheduler hands the SM to pending blocks of a
+// smaller class first.  This approximates shortest-remaining-first at the
+// granularity of work items, which keeps small requests' latency low under
+// load without starving large ones (a class is FIFO within itself).  A batch
+// is one launch of serve_kernel (pospop_desc.cu) per kServeMax requests: the requests and
 // their work-item prefix sums, planned on the host (it knows every
 // request's address and length), travel in the kernel's parameter block, so
 // a batch is a launch and an event and nothing else.  Each request slot's
@@ -58,7 +66,22 @@ struct Batch {
   unsigned int seq = 0;
   std::vector<Request *> reqs;          // null once completed
   bool busy = false;
+  int level = 0;                        // size class served by this batch's stream
 };
+
+// Size classes: request bytes below kClassBound[k] (and not below the bound
+// before) go to class k; the last class takes the rest.
+constexpr int kServeClasses = 4;
+constexpr size_t kClassBound[kServeClasses - 1] = {size_t(1) << 20, size_t(16) << 20,
+                                                   size_t(128) << 20};
+constexpr size_t kBatchCap = 1024;      // requests per batch (4 launches of kServeMax)
+constexpr uint64_t kMaxServeGrid = uint64_t(1) << 20;
+
+int request_class(size_t nbytes, int levels) {
+  int k = 0;
+  while (k < kServeClasses - 1 && nbytes >= kClassBound[k]) k++;
+  return k < levels ? k : levels - 1;
+}
 
 }  // namespace
 }  // namespace pospop
@@ -67,6 +90,7 @@ struct pospop_server {
   pospop::DevCtx *ctx = nullptr;
   size_t budget = 0;
   int max_inflight = 0;
+  int levels = 1;                           // size classes in use (by stream priorities)
   std::vector<pospop::Batch> batches;
 
   std::mutex mu;
@@ -107,10 +131,7 @@ int launch_batch(pospop_server &srv, Batch &b, const BatchTune &bt) {
   b.seq = b.seq + 1 == 0 ? 1 : b.seq + 1;
   const uint32_t ir = bt.item_rows;
   const Variant &v = serve_variant(bt.variant);
-  int cps = std::min(bt.ctas_per_sm, srv.ctx->occ_batch[bt.variant]);
-  if (cps < 1) cps = 1;
   const uint64_t wpb = (uint64_t)v.bs / 32;
-  const uint64_t max_grid = (uint64_t)srv.ctx->sms * (uint64_t)cps;
   static thread_local ServeParams P;   // about 8 KiB: not on the loop thread's stack
   for (int k0 = 0; k0 < n; k0 += kServeMax) {
     const int cnt = std::min(kServeMax, n - k0);
@@ -143,8 +164,11 @@ int launch_batch(pospop_server &srv, Batch &b, const BatchTune &bt) {
     P.item_start[cnt] = items;
     P.total = items;
     if (items == 0) continue;
+    // one work item per warp: blocks retire as their items finish, so a
+    // smaller class's pending blocks can take the SM (the grid-stride loop
+    // in the kernel covers any cap)
     uint64_t grid = (items + wpb - 1) / wpb;
-    if (grid > max_grid) grid = max_grid;
+    if (grid > kMaxServeGrid) grid = kMaxServeGrid;
     void *args[] = {&P};
     if (cudaLaunchKernel(v.fn, dim3((unsigned)grid), dim3(v.bs), args, 0, b.s) != cudaSuccess) {
       cudaGetLastError();
@@ -251,17 +275,28 @@ void serve_loop(pospop_server *srv) {
         srv->admitted.push_back(r);
         progress = true;
       }
-      // 3. everything admitted goes into the next free batch
-      for (Batch &b : srv->batches) {
-        if (b.busy || srv->admitted.empty()) continue;
-        std::vector<Request *> reqs;
-        while (!srv->admitted.empty() && (int)reqs.size() < srv->max_inflight) {
-          reqs.push_back(srv->admitted.front());
-          srv->admitted.pop_front();
+      // 3. admitted requests go, by size class and in admission order, into
+      //    the next free batch of their class
+      if (!srv->admitted.empty()) {
+        Batch *free_b[kServeClasses] = {nullptr, nullptr, nullptr, nullptr};
+        for (Batch &b : srv->batches)
+          if (!b.busy && !free_b[b.level]) free_b[b.level] = &b;
+        std::vector<Request *> take[kServeClasses];
+        std::deque<Request *> keep;
+        for (Request *r : srv->admitted) {
+          const int k = request_class(r->nbytes, srv->levels);
+          if (free_b[k] && take[k].size() < kBatchCap)
+            take[k].push_back(r);
+          else
+            keep.push_back(r);
         }
-        b.busy = true;
-        to_launch.emplace_back(&b, std::move(reqs));
-        progress = true;
+        srv->admitted.swap(keep);
+        for (int k = 0; k < kServeClasses; k++) {
+          if (take[k].empty()) continue;
+          free_b[k]->busy = true;
+          to_launch.emplace_back(free_b[k], std::move(take[k]));
+          progress = true;
+        }
       }
       const bool busy = std::any_of(srv->batches.begin(), srv->batches.end(),
                                     [](const Batch &b) { return b.busy; });
@@ -378,11 +413,24 @@ int pospop_server_create(size_t mem_budget, int max_inflight, int max_batches,
   srv->ctx = c;
   srv->budget = mem_budget;
   srv->max_inflight = max_inflight;
-  srv->batches.resize((size_t)max_batches);
-  for (Batch &b : srv->batches) {
-    const size_t cbytes = 64 * sizeof(unsigned long long) * (size_t)max_inflight;
-    const size_t fbytes = sizeof(unsigned int) * (size_t)max_inflight;
-    if (cudaStreamCreateWithFlags(&b.s, cudaStreamNonBlocking) != cudaSuccess ||
+  // one size class per stream priority level (at most kServeClasses), each
+  // with max_batches batch streams; class 0 (the smallest requests) gets the
+  // greatest priority
+  int least = 0, greatest = 0;
+  if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess) {
+    cudaGetLastError();
+    least = greatest = 0;
+  }
+  srv->levels = std::max(1, std::min(kServeClasses, least - greatest + 1));
+  srv->batches.resize((size_t)max_batches * (size_t)srv->levels);
+  const size_t slots = std::min((size_t)max_inflight, kBatchCap);
+  for (size_t i = 0; i < srv->batches.size(); i++) {
+    Batch &b = srv->batches[i];
+    b.level = (int)(i / (size_t)max_batches);
+    const int prio = greatest + b.level;   // numerically lower = higher priority
+    const size_t cbytes = 64 * sizeof(unsigned long long) * slots;
+    const size_t fbytes = sizeof(unsigned int) * slots;
+    if (cudaStreamCreateWithPriority(&b.s, cudaStreamNonBlocking, prio) != cudaSuccess ||
         cudaEventCreateWithFlags(&b.done, cudaEventDisableTiming) != cudaSuccess ||
         cudaMalloc(&b.dcounts, cbytes) != cudaSuccess ||
         cudaMalloc(&b.ddone, fbytes) != cudaSuccess ||

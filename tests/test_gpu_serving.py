@@ -153,3 +153,33 @@ def test_errors_and_bounded_waits(gpu, pool):
         assert not res[:8].any() and (res[8:] == 7).all()
     finally:
         pp.pospop_server_destroy(srv)
+
+
+def test_small_requests_overtake_large_ones(gpu, pool):
+    """Size classes on prioritised streams: small requests that arrive while a
+    large batch runs finish long before it does."""
+    lo_prio, hi_prio = torch.cuda.Stream.priority_range()
+    if lo_prio == hi_prio:
+        pytest.skip("device has a single stream priority level")
+    nb, ns = 32, 64
+    w = np.concatenate([np.full(nb, 16), np.full(ns, 8)]).astype(np.int32)
+    nbytes = np.concatenate([np.full(nb, 128 * MIB), np.full(ns, 16384)]).astype(np.uint64)
+    offs = np.concatenate([np.arange(nb) % 2 * 64 * MIB,
+                           (np.arange(ns) * 16411) % (128 * MIB)]).astype(np.uint64)
+    arrival = np.concatenate([np.zeros(nb), 200_000 + np.arange(ns) * 5000]).astype(np.int64)
+    srv = pp.pospop_server_create(64 << 30, 4096, 4)
+    try:
+        results = np.zeros((nb + ns, 64), dtype=np.uint64)
+        recs = pp.pospop_server_run_trace(srv, arrival, w, pool.data_ptr() + offs, nbytes, results)
+    finally:
+        pp.pospop_server_destroy(srv)
+    assert (recs["status"] == 0).all()
+    solo = _solo(pool, w, nbytes, offs)
+    for k in range(nb + ns):
+        assert np.array_equal(results[k, :w[k]], solo[k, :w[k]]), k
+    t0 = int(recs["t_submit_ns"].min())
+    big_done = int(recs["t_done_ns"][:nb].max())
+    small_done = recs["t_done_ns"][nb:].astype(np.int64)
+    small_lat = small_done - recs["t_submit_ns"][nb:].astype(np.int64)
+    assert small_done.max() < big_done
+    assert np.median(small_lat) < 0.25 * (big_done - t0)
