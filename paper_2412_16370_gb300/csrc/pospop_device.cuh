@@ -257,16 +257,21 @@ __device__ __forceinline__ V4 load_granule_masked(const Span &s, uint64_t g) {
 }
 
 // ---------------------------------------------------------------------------
-// Loader policies.  count_rows fetches granules through a loader: `fast`
-// for granules known to lie wholly inside the span, `edge` for any granule
-// (bytes outside the span read as zero).  PlainLoader is the plain count;
-// SelectLoader (below) also applies a word-selection bitmap.
+// Loader policies.  count_rows fetches granules through a loader: `group16`
+// for a CSA group of 16 rows known to lie wholly inside the span, `edge` for
+// any granule (bytes outside the span read as zero).  PlainLoader is the
+// plain count; SelectLoader (below) also applies a word-selection bitmap.
 // ---------------------------------------------------------------------------
 template <int HINT>
 struct PlainLoader {
-  __device__ __forceinline__ V4 fast(const uint8_t *p, uint64_t) const { return ldg_granule<HINT>(p); }
   __device__ __forceinline__ V4 edge(const Span &s, uint64_t g) const {
     return load_granule_masked<HINT>(s, g);
+  }
+  // 16 interior granules: row k at ptr + k * pstep (granule g + k * gstride).
+  __device__ __forceinline__ void group16(V4 (&v)[16], const uint8_t *ptr, uint64_t pstep, uint64_t,
+                                          uint64_t) const {
+#pragma unroll
+    for (int k = 0; k < 16; k++) v[k] = ldg_granule<HINT>(ptr + (uint64_t)k * pstep);
   }
 };
 
@@ -331,10 +336,10 @@ __device__ __forceinline__ uint32_t lane_mask(uint32_t bits, int r) {
   } else if (WLOG == 1) {   // w = 16: bit k of the pair -> 16-bit half k
     const uint32_t t = ((bits >> (2 * r)) & 0x3u) * 0x40008000u;
     asm("prmt.b32 %0, %1, 0, 0xBB99;" : "=r"(e) : "r"(t));
-  } else if (WLOG == 2) {   // w = 32: one bit per lane
-    e = 0u - ((bits >> r) & 1u);
+  } else if (WLOG == 2) {   // w = 32: one bit per lane, sign-extended by bfe
+    asm("bfe.s32 %0, %1, %2, 1;" : "=r"(e) : "r"(bits), "r"(r));
   } else {                  // w = 64: one bit per two lanes
-    e = 0u - ((bits >> (r >> 1)) & 1u);
+    asm("bfe.s32 %0, %1, %2, 1;" : "=r"(e) : "r"(bits), "r"(r >> 1));
   }
   return e;
 }
@@ -345,29 +350,35 @@ __device__ __forceinline__ void apply_selection(V4 &v, uint32_t bits) {
   for (int r = 0; r < 4; r++) v.x[r] &= lane_mask<WLOG>(bits, r);
 }
 
-// Selection bits of an interior granule (not granule 0, not in the last
-// row): all its words lie inside the span, so the window needs no clipping,
-// and both bitmap words are read unconditionally (the second index clamped
-// to the last word) -- no control flow between a group's loads.
-template <int WLOG>
-__device__ __forceinline__ uint32_t interior_selection(const Selection &m, uint64_t g) {
-  constexpr uint32_t CNT = 16u >> WLOG;
-  const uint64_t lo = g * CNT - m.h;
-  const uint64_t q = lo >> 5;
-  const uint64_t last = (m.nbytes >> 2) - 1;
-  const uint32_t *b32 = reinterpret_cast<const uint32_t *>(m.bits);
-  const uint32_t w0 = __ldg(b32 + q);
-  const uint32_t w1 = __ldg(b32 + (q + 1 < last ? q + 1 : last));
-  return __funnelshift_r(w0, w1, (uint32_t)lo & 31u) & ((1u << CNT) - 1u);
-}
-
 template <int HINT, int WLOG>
 struct SelectLoader {
   Selection m;
-  __device__ __forceinline__ V4 fast(const uint8_t *p, uint64_t g) const {
-    V4 v = ldg_granule<HINT>(p);
-    apply_selection<WLOG>(v, interior_selection<WLOG>(m, g));
-    return v;
+  // 16 interior granules g + k * gstride (not granule 0, not in the last
+  // row): every selection window lies inside the span, so none needs
+  // clipping.  Consecutive rows' windows lie stride * CNT bitmap words apart
+  // at the same bit offset (gstride * CNT is a multiple of 32), so the window
+  // address is one add per row and the offset and the straddle test are
+  // shared by the group.  The second bitmap word is read only where a window
+  // straddles into it (a predicated load); it then holds bits of the span's
+  // words, so it lies inside the bitmap.  With a 16-byte-aligned start no
+  // window straddles.
+  __device__ __forceinline__ void group16(V4 (&v)[16], const uint8_t *ptr, uint64_t pstep,
+                                          uint64_t g, uint64_t gstride) const {
+    constexpr uint32_t CNT = 16u >> WLOG;
+#pragma unroll
+    for (int k = 0; k < 16; k++) v[k] = ldg_granule<HINT>(ptr + (uint64_t)k * pstep);
+    const uint64_t lo = g * CNT - m.h;
+    const uint32_t sh = (uint32_t)lo & 31u;
+    const bool straddle = sh + CNT > 32u;
+    const uint32_t *w = reinterpret_cast<const uint32_t *>(m.bits) + (lo >> 5);
+    const uint64_t wstep = (gstride >> 5) * CNT;
+#pragma unroll
+    for (int k = 0; k < 16; k++) {
+      const uint32_t *wk = w + (uint64_t)k * wstep;
+      const uint32_t w0 = __ldg(wk);
+      const uint32_t w1 = straddle ? __ldg(wk + 1) : 0u;
+      apply_selection<WLOG>(v[k], __funnelshift_r(w0, w1, sh));
+    }
   }
   __device__ __forceinline__ V4 edge(const Span &s, uint64_t g) const {
     V4 v = load_granule_masked<HINT>(s, g);
@@ -429,9 +440,7 @@ __device__ __forceinline__ void count_rows(const Span &s, uint64_t row0, uint64_
       {
         V4 v[16];
         if (interior) {
-#pragma unroll
-          for (int k = 0; k < 16; k++)
-            v[k] = ld.fast(ptr + (uint64_t)k * pstep, g + (uint64_t)k * gstride);
+          ld.group16(v, ptr, pstep, g, gstride);
         } else {
 #pragma unroll
           for (int k = 0; k < 16; k++) v[k] = ld.edge(s, g + (uint64_t)k * gstride);
@@ -441,9 +450,7 @@ __device__ __forceinline__ void count_rows(const Span &s, uint64_t row0, uint64_
       {
         V4 v[16];
         if (interior) {
-#pragma unroll
-          for (int k = 0; k < 16; k++)
-            v[k] = ld.fast(ptr + (uint64_t)(16 + k) * pstep, g + (uint64_t)(16 + k) * gstride);
+          ld.group16(v, ptr + 16u * pstep, pstep, g + 16u * gstride, gstride);
         } else {
 #pragma unroll
           for (int k = 0; k < 16; k++) v[k] = ld.edge(s, g + (uint64_t)(16 + k) * gstride);
@@ -461,8 +468,7 @@ __device__ __forceinline__ void count_rows(const Span &s, uint64_t row0, uint64_
     const bool interior = full && first_row >= 1 && row0 + (i + 15) * stride + 1 < R;
     V4 v[16];
     if (interior) {
-#pragma unroll
-      for (int k = 0; k < 16; k++) v[k] = ld.fast(ptr + (uint64_t)k * pstep, g + (uint64_t)k * gstride);
+      ld.group16(v, ptr, pstep, g, gstride);
     } else {
       // Tail (Section 4.6): rows past the sequence and bytes past the end are zero.
 #pragma unroll
