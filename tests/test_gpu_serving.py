@@ -161,7 +161,7 @@ def test_small_requests_overtake_large_ones(gpu, pool):
     lo_prio, hi_prio = torch.cuda.Stream.priority_range()
     if lo_prio == hi_prio:
         pytest.skip("device has a single stream priority level")
-    nb, ns = 32, 64
+    nb, ns = 64, 64        # 8 GiB of large requests (about 1.1 ms), small ones at 0.2..0.52 ms
     w = np.concatenate([np.full(nb, 16), np.full(ns, 8)]).astype(np.int32)
     nbytes = np.concatenate([np.full(nb, 128 * MIB), np.full(ns, 16384)]).astype(np.uint64)
     offs = np.concatenate([np.arange(nb) % 2 * 64 * MIB,
