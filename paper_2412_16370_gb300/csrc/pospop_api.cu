@@ -2,8 +2,9 @@
 // include/pospopcnt.h): argument checks, per-device contexts, workspaces,
 // launch planning, the host-memory path and CUDA graphs.
 //
-// Every count runs in the sm_103a kernels of pospop_stream.cu and
-// pospop_batch.cu; this file only validates, plans and enqueues.
+// Every count runs in the sm_103a kernels (pospop_stream.cu, pospop_batch.cu,
+// pospop_gather.cu, pospop_select.cu, pospop_roofline.cu); this file only
+// validates, plans and enqueues.
 #include <dlfcn.h>
 
 #include <algorithm>
