@@ -677,8 +677,14 @@ def _serving(pp, synth, pool, pool_bytes, large_gbs, dev, loads=(0.3, 0.6, 0.9),
             "bytes": total, "GBps": round(gbs, 1), "frac_of_large_array": round(gbs / large_gbs, 4),
             "p50_us": round(float(np.percentile(lat_us, 50)), 1),
             "p99_us": round(float(np.percentile(lat_us, 99)), 1),
+            "p99_us_below_1MiB": _pct(lat_us[r["nbytes"] < (1 << 20)], 99),
+            "p99_us_from_128MiB": _pct(lat_us[r["nbytes"] >= (128 << 20)], 99),
             "status_ok": bool((recs["status"] == 0).all()), "results_match_solo": bool(same)})
     return out
+
+
+def _pct(a, q):
+    return round(float(np.percentile(a, q)), 1) if a.size else None
 
 
 def _oracle_rate(fn, nbytes_fn, budget_s=2.0):
