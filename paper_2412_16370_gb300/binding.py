@@ -90,6 +90,9 @@ COMPLETION_DTYPE = [("id", "<u8"), ("status", "<i4"), ("w", "<i4"), ("nbytes", "
 def lib():
     """The loaded library (raises if it has not been built)."""
     global _lib
+    loaded = _lib
+    if loaded is not None:       # set once, never cleared: no lock on the hot path
+        return loaded
     with _lock:
         if _lib is None:
             if not os.path.exists(LIB_PATH):

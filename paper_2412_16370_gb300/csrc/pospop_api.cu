@@ -30,8 +30,10 @@ static bool valid_w(int w) {
   return w == 1 || w == 2 || w == 4 || w == 8 || w == 16 || w == 32 || w == 64;
 }
 
-// The single-array forms also take the wider folds.
+// The single-array forms also take the wider folds; the batched and gathered
+// forms the one without a second parity class (w = 128).
 static bool valid_w_single(int w) { return valid_w(w) || w == 128 || w == 256; }
+static bool valid_w_multi(int w) { return valid_w(w) || w == 128; }
 
 // Index in a kernel family (stride `step`) of the variant launched with the
 // same block shape as `want` -- a kernel must be launched with the block size
@@ -908,10 +910,10 @@ int pospopcnt_u64(uint64_t counts[64], const uint64_t *words, size_t n) {
 
 int pospopcnt_batch(int w, uint64_t *counts, const void *base, const uint64_t *offsets, size_t m,
                     void *stream) {
-  if (!valid_w(w)) return POSPOP_EINVAL;
+  if (!valid_w_multi(w)) return POSPOP_EINVAL;
   if (m == 0) return POSPOP_OK;
   if (!counts || !base || !offsets) return POSPOP_EINVAL;
-  if (m > (SIZE_MAX / 8) / 64 - 1) return POSPOP_ERANGE;
+  if (m > (SIZE_MAX / 8) / 128 - 1) return POSPOP_ERANGE;
   int rc = POSPOP_OK;
   DevCtx *c = current_ctx(&rc);
   if (!c) return rc;
@@ -931,10 +933,10 @@ int pospopcnt_batch(int w, uint64_t *counts, const void *base, const uint64_t *o
 
 int pospopcnt_gather(int w, uint64_t *counts, const uint64_t *ptrs, const uint64_t *lens,
                      size_t n, void *stream) {
-  if (!valid_w(w)) return POSPOP_EINVAL;
+  if (!valid_w_multi(w)) return POSPOP_EINVAL;
   if (n == 0) return POSPOP_OK;
   if (!counts || !ptrs || !lens) return POSPOP_EINVAL;
-  if (n > (SIZE_MAX / 8) / 64 - 1) return POSPOP_ERANGE;
+  if (n > (SIZE_MAX / 8) / 128 - 1) return POSPOP_ERANGE;
   int rc = POSPOP_OK;
   DevCtx *c = current_ctx(&rc);
   if (!c) return rc;

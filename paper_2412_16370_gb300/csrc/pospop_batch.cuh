@@ -134,10 +134,10 @@ template <int SRC, int BS, int MINB, int DEPTH, int HINT>
 __global__ void __launch_bounds__(BS, MINB) batch_kernel(BatchParams P) {
   // Gathered regions all add into one counter array: accumulate per block in
   // shared memory, one atomic per counter per block at the end.
-  __shared__ unsigned long long gacc[SRC == kSrcGather ? 64 : 1];
+  __shared__ unsigned long long gacc[SRC == kSrcGather ? 128 : 1];
   pdl_enter();
   if (SRC == kSrcGather) {
-    if (threadIdx.x < 64) gacc[threadIdx.x] = 0ull;
+    if (threadIdx.x < 128) gacc[threadIdx.x] = 0ull;   // every block shape has >= 128 threads
     __syncthreads();
   }
   if (*P.status != 0) return;   // planning rejected the offsets: change nothing

@@ -130,13 +130,13 @@ def test_short_sweep_back_to_back(gpu, orc):
         assert np.array_equal(counts_np(c), orc.batch(w, host, offs)), w
 
 
-def test_sub_byte_widths(gpu, orc):
+def test_sub_byte_and_wide_widths(gpu, orc):
     sizes = synth.log_uniform_sizes(500, 1, 100000, seed=5)
     offs = synth.csr_offsets(sizes)
     host = synth.random_bytes(int(offs[-1]), seed=6)
     base = torch.from_numpy(host).to(gpu)
     offs_d = torch.from_numpy(offs.view(np.int64)).to(gpu)
-    for w in (1, 2, 4):
+    for w in (1, 2, 4, 128):
         c = torch.zeros((len(sizes), w), dtype=torch.int64, device=gpu)
         pp.pospopcnt_batch(w, c, base, offs_d)
         assert np.array_equal(counts_np(c), orc.batch(w, host, offs)), w
@@ -186,6 +186,7 @@ def test_argument_errors(gpu):
     assert L.pospopcnt_batch(8, c.data_ptr(), base.data_ptr(), offs.data_ptr(), 0, None) == 0
     assert L.pospopcnt_batch(8, None, base.data_ptr(), offs.data_ptr(), 2, None) == pp.POSPOP_EINVAL
     assert L.pospopcnt_batch(9, c.data_ptr(), base.data_ptr(), offs.data_ptr(), 2, None) == pp.POSPOP_EINVAL
+    assert L.pospopcnt_batch(256, c.data_ptr(), base.data_ptr(), offs.data_ptr(), 2, None) == pp.POSPOP_EINVAL
     hoffs = np.zeros(3, dtype=np.uint64)
     assert L.pospopcnt_batch(8, c.data_ptr(), base.data_ptr(), hoffs.ctypes.data, 2, None) == pp.POSPOP_EPTR
 
