@@ -156,39 +156,43 @@ def _profile_traffic(nbytes: int):
                                                  "to this launch's input bytes")
 
 
-def _cpu_baseline(data_dev, budget_s: float = 4.0):
-    """The oracle as it stands, all host cores, on a bounded sample of the array."""
+def _cpu_baseline(data_dev, budget_s: float = 12.0, runs: int = 5):
+    """The oracle as it stands on a bounded sample of the array: all host
+    cores and one thread, each the median of `runs` timed passes (every pass
+    counts the sample once per w)."""
     import torch
     import oracle
     orc = oracle.load()
     cores = os.cpu_count() or 1
     probe = 16 << 20
     host = data_dev[:probe].cpu().numpy()
+    orc.bytes_mt(16, host, cores)                     # warm-up
     t0 = time.perf_counter()
     orc.bytes_mt(16, host, cores)
     rate = probe / max(time.perf_counter() - t0, 1e-6)
-    sample = int(min(GIB, max(probe, rate * budget_s / len(WIDTHS))))
+    # about budget_s for all runs on all cores, and a fifth of that on one thread
+    sample = int(min(GIB, max(probe, rate * budget_s / (runs * len(WIDTHS)))))
     sample -= sample % 64
     host = data_dev[:sample].cpu().numpy()
-    t0 = time.perf_counter()
-    for w in WIDTHS:
-        orc.bytes_mt(w, host, cores)
-    dt = time.perf_counter() - t0
-    # the same loop on one thread, on a sample of about a second
-    one = int(min(sample, max(1 << 20, rate / cores * 1.0 / len(WIDTHS))))
+    one = int(min(sample, max(1 << 20, rate / cores * budget_s / 5 / (runs * len(WIDTHS)))))
     one -= one % 64
-    t0 = time.perf_counter()
-    for w in WIDTHS:
-        orc.bytes_mt(w, host[:one], 1)
-    dt1 = time.perf_counter() - t0
+
+    def timed(nbytes, threads):
+        t1 = time.perf_counter()
+        for w in WIDTHS:
+            orc.bytes_mt(w, host[:nbytes], threads)
+        return nbytes * len(WIDTHS) / (time.perf_counter() - t1) / 1e9
+
+    all_cores = float(np.median([timed(sample, cores) for _ in range(runs)]))
+    one_thread = float(np.median([timed(one, 1) for _ in range(runs)]))
     del torch
-    return {"value": round(sample * len(WIDTHS) / dt / 1e9, 4), "unit": "GB/s", "cores": cores,
-            "kind": "oracle",
-            "one_thread_GBps": round(one * len(WIDTHS) / dt1 / 1e9, 4),
+    return {"value": round(all_cores, 4), "unit": "GB/s", "cores": cores, "kind": "oracle",
+            "one_thread_GBps": round(one_thread, 4),
             "cpu_model": _cpu_model(),
             "sample": f"first {sample >> 20} MiB of the 8 GiB array, counted once per w in "
-                      f"{{8,16,32,64}} with {cores} threads (Fig. 2 loop, -O2 -fno-tree-vectorize); "
-                      f"one_thread_GBps: the first {one >> 20} MiB on one thread"}
+                      f"{{8,16,32,64}} with {cores} threads, median of {runs} runs after a "
+                      f"warm-up (Fig. 2 loop, -O2 -fno-tree-vectorize); one_thread_GBps: the "
+                      f"first {one >> 20} MiB on one thread, median of {runs} runs"}
 
 
 def _cpu_model():
