@@ -703,10 +703,20 @@ def _oracle_rate(fn, nbytes_fn, budget_s=2.0):
     return round(done / (time.perf_counter() - t0) / 1e9, 4)
 
 
-def _time_ms(fn, stream, reps=10, warm=3):
+def _time_ms(fn, stream, reps=10, warm=3, warm_s=0.1, calls=None):
+    """Mean ms per call over `reps` calls after at least `warm` calls and
+    `warm_s` seconds of warm-up (a section that follows seconds of host-only
+    work, such as an oracle timing, otherwise starts on an idle GPU that has
+    not come back to full clocks).  If `calls` is a list, the total number of
+    calls made is appended to it."""
     import torch
-    for _ in range(warm):
+    t0 = time.perf_counter()
+    done = 0
+    while done < warm or time.perf_counter() - t0 < warm_s:
         fn()
+        done += 1
+        if done % 8 == 0:
+            torch.cuda.synchronize()
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -715,6 +725,8 @@ def _time_ms(fn, stream, reps=10, warm=3):
         fn()
     e1.record(stream)
     torch.cuda.synchronize()
+    if calls is not None:
+        calls.append(done + reps)
     return e0.elapsed_time(e1) / reps
 
 
@@ -785,9 +797,10 @@ def _sweep(pp, synth_device, data, nbytes, stream, hbm_peak, seed):
         for size in sizes:
             for w in WIDTHS:
                 c = torch.zeros(w, dtype=torch.int64, device=data.device)
+                ncalls = []
                 ms = _time_ms(lambda: pp.pospopcnt_async(w, c, data, size, stream), stream,
-                              reps=reps, warm=warm)
-                per = c.cpu().numpy().view(np.uint64).astype(np.float64) / (warm + reps)
+                              reps=reps, warm=warm, calls=ncalls)
+                per = c.cpu().numpy().view(np.uint64).astype(np.float64) / ncalls[0]
                 words = size * 8 // w
                 if p == 1.0:
                     good = bool(np.all(per == words))
@@ -802,7 +815,8 @@ def _sweep(pp, synth_device, data, nbytes, stream, hbm_peak, seed):
     torch.cuda.synchronize()
     fr = [c["frac_of_hbm_peak"] for c in cells]
     return {"workload": "w in {8,16,32,64} x {1 GiB, 8 GiB} x Bernoulli(p), p in {0.01,0.5,0.99} "
-                        "plus all-ones; 10 launches per cell after 3 warm-up",
+                        "plus all-ones; 10 launches per cell after at least 3 warm-up launches "
+                        "and 0.1 s",
             "min_frac_of_hbm_peak": min(fr), "max_frac_of_hbm_peak": max(fr),
             "all_counts_ok": ok, "cells": cells}
 
