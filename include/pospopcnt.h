@@ -20,10 +20,10 @@
  *     one counter array).  Zero them first for a fresh count.
  *   - Widths.  w is 8, 16, 32 or 64 (the paper's f_8 .. f_64, Section 5).
  *     The byte-length, batch, gather and serving forms also accept w = 1, 2,
- *     4 (w = 1 is the ordinary population count); pospopcnt_async and
- *     pospopcnt_host also the wider folds w = 128 and 256, and the batch and
- *     gather forms w = 128 (Section 4's general maximum word size; counters
- *     then hold 128 or 256 entries per array).
+ *     4 (w = 1 is the ordinary population count); pospopcnt_async,
+ *     pospopcnt_host and the batch and gather forms also the wider folds
+ *     w = 128 and 256 (Section 4's general maximum word size; counters then
+ *     hold 128 or 256 entries per array).
  *   - Memory.  Unless a function says otherwise, pointers are DEVICE
  *     pointers of the current CUDA device (cudaMalloc, PyTorch tensors,
  *     cudaMallocManaged or pinned host memory that the device can address).

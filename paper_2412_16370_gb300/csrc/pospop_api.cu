@@ -30,10 +30,9 @@ static bool valid_w(int w) {
   return w == 1 || w == 2 || w == 4 || w == 8 || w == 16 || w == 32 || w == 64;
 }
 
-// The single-array forms also take the wider folds; the batched and gathered
-// forms the one without a second parity class (w = 128).
+// The single-array, batched and gathered forms also take the wider folds.
 static bool valid_w_single(int w) { return valid_w(w) || w == 128 || w == 256; }
-static bool valid_w_multi(int w) { return valid_w(w) || w == 128; }
+static bool valid_w_multi(int w) { return valid_w_single(w); }
 
 // Index in a kernel family (stride `step`) of the variant launched with the
 // same block shape as `want` -- a kernel must be launched with the block size
@@ -616,7 +615,13 @@ int launch_batch_with(DevCtx &ctx, const TuneTable &t, int w, unsigned long long
   bp.item_rows = t.batch.item_rows;
   bp.grab = t.batch.grab;
   bp.regroup = t.regroup;
-  const Variant &v = batch_variant(t.batch.variant);
+  const Variant *vp = &batch_variant(t.batch.variant);
+  if (w == 256) {   // the two-parity kernel with the tuned block shape
+    const int pick = pick_shape(batch256_variant_count(), batch256_variant, 1, *vp);
+    if (pick < 0) return POSPOP_EINVAL;
+    vp = &batch256_variant(pick);
+  }
+  const Variant &v = *vp;
   int cps = t.batch.ctas_per_sm < ctx.occ_batch[t.batch.variant] ? t.batch.ctas_per_sm
                                                                  : ctx.occ_batch[t.batch.variant];
   if (cps < 1) cps = 1;
@@ -672,7 +677,13 @@ static int launch_gather_with(DevCtx &ctx, const TuneTable &t, int w, unsigned l
   bp.item_rows = t.batch.item_rows;
   bp.grab = t.batch.grab;
   bp.regroup = t.regroup;
-  const Variant &v = gather_variant(t.batch.variant);
+  const Variant *vp = &gather_variant(t.batch.variant);
+  if (w == 256) {   // the two-parity kernel with the tuned block shape
+    const int pick = pick_shape(gather256_variant_count(), gather256_variant, 1, *vp);
+    if (pick < 0) return POSPOP_EINVAL;
+    vp = &gather256_variant(pick);
+  }
+  const Variant &v = *vp;
   int cps = std::min(t.batch.ctas_per_sm, ctx.occ_batch[t.batch.variant]);
   if (cps < 1) cps = 1;
   void *bargs[] = {&bp};
@@ -913,7 +924,7 @@ int pospopcnt_batch(int w, uint64_t *counts, const void *base, const uint64_t *o
   if (!valid_w_multi(w)) return POSPOP_EINVAL;
   if (m == 0) return POSPOP_OK;
   if (!counts || !base || !offsets) return POSPOP_EINVAL;
-  if (m > (SIZE_MAX / 8) / 128 - 1) return POSPOP_ERANGE;
+  if (m > (SIZE_MAX / 8) / 256 - 1) return POSPOP_ERANGE;
   int rc = POSPOP_OK;
   DevCtx *c = current_ctx(&rc);
   if (!c) return rc;
@@ -936,7 +947,7 @@ int pospopcnt_gather(int w, uint64_t *counts, const uint64_t *ptrs, const uint64
   if (!valid_w_multi(w)) return POSPOP_EINVAL;
   if (n == 0) return POSPOP_OK;
   if (!counts || !ptrs || !lens) return POSPOP_EINVAL;
-  if (n > (SIZE_MAX / 8) / 128 - 1) return POSPOP_ERANGE;
+  if (n > (SIZE_MAX / 8) / 256 - 1) return POSPOP_ERANGE;
   int rc = POSPOP_OK;
   DevCtx *c = current_ctx(&rc);
   if (!c) return rc;

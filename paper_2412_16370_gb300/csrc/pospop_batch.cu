@@ -58,8 +58,15 @@ __global__ void __launch_bounds__(kPlanThreads) plan_apply_kernel(PlanParams P) 
 
 static const Variant kBatch[] = {POSPOP_FAMILY(POSPOP_BV)};
 
+#define POSPOP_BV256(BS, MINB, D, H)                                                         \
+  Variant{reinterpret_cast<const void *>(&batch_kernel<kSrcCsr, BS, MINB, D, H, true>), BS, \
+          MINB, D, H}
+static const Variant kBatch256[] = {POSPOP_FAMILY256(POSPOP_BV256)};
+
 int batch_variant_count() { return (int)(sizeof(kBatch) / sizeof(kBatch[0])); }
 const Variant &batch_variant(int i) { return kBatch[i]; }
+int batch256_variant_count() { return (int)(sizeof(kBatch256) / sizeof(kBatch256[0])); }
+const Variant &batch256_variant(int i) { return kBatch256[i]; }
 
 const void *plan_items_fn() { return reinterpret_cast<const void *>(&plan_items_kernel<kSrcCsr>); }
 const void *plan_scan_fn() { return reinterpret_cast<const void *>(&plan_scan_kernel); }

@@ -130,14 +130,16 @@ __device__ __forceinline__ uint64_t find_array(const uint64_t *__restrict__ item
   return lo;
 }
 
-template <int SRC, int BS, int MINB, int DEPTH, int HINT>
+// PAR2: w = 256, where a word spans two granules (the two-parity flush).
+template <int SRC, int BS, int MINB, int DEPTH, int HINT, bool PAR2 = false>
 __global__ void __launch_bounds__(BS, MINB) batch_kernel(BatchParams P) {
   // Gathered regions all add into one counter array: accumulate per block in
   // shared memory, one atomic per counter per block at the end.
-  __shared__ unsigned long long gacc[SRC == kSrcGather ? 128 : 1];
+  constexpr int kAcc = SRC == kSrcGather ? (PAR2 ? 256 : 128) : 1;
+  __shared__ unsigned long long gacc[kAcc];
   pdl_enter();
   if (SRC == kSrcGather) {
-    if (threadIdx.x < 128) gacc[threadIdx.x] = 0ull;   // every block shape has >= 128 threads
+    for (int j = threadIdx.x; j < kAcc; j += BS) gacc[j] = 0ull;
     __syncthreads();
   }
   if (*P.status != 0) return;   // planning rejected the offsets: change nothing
@@ -171,7 +173,7 @@ __global__ void __launch_bounds__(BS, MINB) batch_kernel(BatchParams P) {
       const uint64_t r0 = k * P.item_rows;
       const uint64_t r1 = (r0 + P.item_rows < R) ? r0 + P.item_rows : R;
       unsigned long long *out = r.out;
-      if (P.regroup && r.w == 8 && r1 - r0 <= 3) {
+      if (!PAR2 && P.regroup && r.w == 8 && r1 - r0 <= 3) {
         uint32_t lo = 0u, hi = 0u;
         regroup_rows_w8(s, r0, 1, r1 - r0, lane, PlainLoader<HINT>{}, lo, hi);
         if (SRC == kSrcGather)
@@ -185,23 +187,39 @@ __global__ void __launch_bounds__(BS, MINB) batch_kernel(BatchParams P) {
         continue;
       }
       uint32_t cnt[4] = {0u, 0u, 0u, 0u};
-      count_rows<DEPTH, HINT>(s, r0, 1, r1 - r0, lane, xk, cnt, PlainLoader<HINT>{});
-      if (SRC == kSrcGather) {
-        fold_counts(cnt, r.w, rot, lane, [&](uint32_t j, unsigned long long v) {
-          if (v) atomicAdd(&gacc[j], v);
-        });
+      uint32_t cnt_odd[4] = {0u, 0u, 0u, 0u};
+      // an item starts at an even granule (row r0 of a 16-byte-aligned span),
+      // so lane parity is granule parity, as the two-parity flush requires
+      count_rows<DEPTH, HINT, PlainLoader<HINT>, PAR2>(s, r0, 1, r1 - r0, lane, xk, cnt,
+                                                       PlainLoader<HINT>{}, cnt_odd);
+      auto to_gacc = [&](uint32_t j, unsigned long long v) {
+        if (v) atomicAdd(&gacc[j], v);
+      };
+      auto to_out = [&](uint32_t j, unsigned long long v) {
+        if (v) atomicAdd(out + j, v);
+      };
+      if (PAR2) {
+        if (SRC == kSrcGather)
+          fold_counts_256(cnt, cnt_odd, rot, lane, to_gacc);
+        else
+          fold_counts_256(cnt, cnt_odd, rot, lane, to_out);
       } else {
-        fold_counts(cnt, r.w, rot, lane, [&](uint32_t j, unsigned long long v) {
-          if (v) atomicAdd(out + j, v);
-        });
+        if (SRC == kSrcGather)
+          fold_counts(cnt, r.w, rot, lane, to_gacc);
+        else
+          fold_counts(cnt, r.w, rot, lane, to_out);
       }
     }
   }
   if (SRC == kSrcGather) {
     __syncthreads();
-    if ((int)threadIdx.x < P.w && gacc[threadIdx.x]) atomicAdd(P.counts + threadIdx.x, gacc[threadIdx.x]);
+    for (int j = threadIdx.x; j < P.w; j += BS)
+      if (gacc[j]) atomicAdd(P.counts + j, gacc[j]);
   }
 }
+
+// w = 256 variants: the tune table's launch shapes, flush depth 16.
+#define POSPOP_FAMILY256(M) M(512, 1, 16, 0), M(512, 1, 16, 1), M(256, 2, 16, 1), M(128, 4, 16, 1)
 
 #define POSPOP_FAMILY(M)                                                  \
   M(256, 2, 16, 0), M(256, 2, 16, 1), M(256, 2, 32, 0), M(256, 2, 32, 1), \

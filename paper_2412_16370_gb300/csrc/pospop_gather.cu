@@ -14,8 +14,15 @@ namespace pospop {
 
 static const Variant kGather[] = {POSPOP_FAMILY(POSPOP_GV)};
 
+#define POSPOP_GV256(BS, MINB, D, H)                                                            \
+  Variant{reinterpret_cast<const void *>(&batch_kernel<kSrcGather, BS, MINB, D, H, true>), BS, \
+          MINB, D, H}
+static const Variant kGather256[] = {POSPOP_FAMILY256(POSPOP_GV256)};
+
 int gather_variant_count() { return (int)(sizeof(kGather) / sizeof(kGather[0])); }
 const Variant &gather_variant(int i) { return kGather[i]; }
+int gather256_variant_count() { return (int)(sizeof(kGather256) / sizeof(kGather256[0])); }
+const Variant &gather256_variant(int i) { return kGather256[i]; }
 
 const void *plan_items_gather_fn() {
   return reinterpret_cast<const void *>(&plan_items_kernel<kSrcGather>);

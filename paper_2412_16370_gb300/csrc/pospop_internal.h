@@ -127,6 +127,8 @@ int stream256_variant_count();
 const Variant &stream256_variant(int i);
 int batch_variant_count();
 const Variant &batch_variant(int i);
+int batch256_variant_count();
+const Variant &batch256_variant(int i);
 int roofline_variant_count();
 const Variant &roofline_variant(int i);
 
@@ -134,6 +136,8 @@ int serve_variant_count();
 const Variant &serve_variant(int i);
 int gather_variant_count();
 const Variant &gather_variant(int i);
+int gather256_variant_count();
+const Variant &gather256_variant(int i);
 int select_variant_count();
 const Variant &select_variant(int i);
 const void *plan_items_gather_fn();

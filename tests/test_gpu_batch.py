@@ -136,7 +136,7 @@ def test_sub_byte_and_wide_widths(gpu, orc):
     host = synth.random_bytes(int(offs[-1]), seed=6)
     base = torch.from_numpy(host).to(gpu)
     offs_d = torch.from_numpy(offs.view(np.int64)).to(gpu)
-    for w in (1, 2, 4, 128):
+    for w in (1, 2, 4, 128, 256):
         c = torch.zeros((len(sizes), w), dtype=torch.int64, device=gpu)
         pp.pospopcnt_batch(w, c, base, offs_d)
         assert np.array_equal(counts_np(c), orc.batch(w, host, offs)), w
@@ -186,7 +186,7 @@ def test_argument_errors(gpu):
     assert L.pospopcnt_batch(8, c.data_ptr(), base.data_ptr(), offs.data_ptr(), 0, None) == 0
     assert L.pospopcnt_batch(8, None, base.data_ptr(), offs.data_ptr(), 2, None) == pp.POSPOP_EINVAL
     assert L.pospopcnt_batch(9, c.data_ptr(), base.data_ptr(), offs.data_ptr(), 2, None) == pp.POSPOP_EINVAL
-    assert L.pospopcnt_batch(256, c.data_ptr(), base.data_ptr(), offs.data_ptr(), 2, None) == pp.POSPOP_EINVAL
+    assert L.pospopcnt_batch(512, c.data_ptr(), base.data_ptr(), offs.data_ptr(), 2, None) == pp.POSPOP_EINVAL
     hoffs = np.zeros(3, dtype=np.uint64)
     assert L.pospopcnt_batch(8, c.data_ptr(), base.data_ptr(), hoffs.ctypes.data, 2, None) == pp.POSPOP_EPTR
 
@@ -216,3 +216,24 @@ def test_regroup_short_path(gpu, orc, tune_override, item_rows):
     got = counts_np(c)
     assert np.array_equal(got, orc.batch(8, oh, offs))
     assert np.array_equal(got.sum(axis=1), sizes.astype(np.uint64))
+
+
+def test_w256_every_tune_shape(gpu, orc, tune_override):
+    """w = 256 (a word spans two granules) through the two-parity batch kernel,
+    for every block shape and item size the tune table may choose."""
+    sizes = synth.log_uniform_sizes(300, 1, 200000, seed=55)
+    sizes[::23] = 0
+    offs = synth.csr_offsets(sizes)
+    host = synth.random_bytes(int(offs[-1]), seed=56)
+    base = torch.empty(host.size + 32, dtype=torch.uint8, device=gpu)[3:3 + host.size]
+    base.copy_(torch.from_numpy(host))
+    offs_d = torch.from_numpy(offs.view(np.int64)).to(gpu)
+    exp = orc.batch(256, host, offs)
+    for bs, minb in ((256, 2), (512, 1), (128, 4)):
+        for depth in (16, 32):
+            for hint in (0, 1):
+                for item_rows in (1, 31, 127):
+                    tune_override(f"batch {bs} {minb} {depth} {hint} 1 {item_rows} 1\n")
+                    c = torch.zeros((len(sizes), 256), dtype=torch.int64, device=gpu)
+                    pp.pospopcnt_batch(256, c, base, offs_d)
+                    assert np.array_equal(counts_np(c), exp), (bs, depth, hint, item_rows)

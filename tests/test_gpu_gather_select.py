@@ -58,7 +58,7 @@ def test_gather_matches_oracle(gpu, orc):
     for m, hi, seed in ((1, 1000, 1), (37, 5000, 2), (3000, 1 << 20, 3)):
         starts, lens = _regions(m, seed, span, hi)
         regions = [host[s:s + n] for s, n in zip(starts, lens)]
-        for w in (1, 8, 16, 32, 64, 128):
+        for w in (1, 8, 16, 32, 64, 128, 256):
             assert np.array_equal(_gather_gpu(w, buf, starts, lens), orc.gather(w, regions)), (m, w)
 
 
@@ -87,12 +87,13 @@ def test_gather_every_variant(gpu, orc, tune_override):
     host = buf.cpu().numpy()
     starts, lens = _regions(400, 9, span, 200000)
     regions = [host[s:s + n] for s, n in zip(starts, lens)]
-    exp = {w: orc.gather(w, regions) for w in WORD_W}
+    widths = WORD_W + (256,)
+    exp = {w: orc.gather(w, regions) for w in widths}
     for bs, minb in ((256, 2), (512, 1), (128, 4)):
         for depth in (16, 32):
             for item_rows in (1, 15, 31, 127):
                 tune_override(f"batch {bs} {minb} {depth} 1 1 {item_rows} 2\n")
-                for w in WORD_W:
+                for w in widths:
                     assert np.array_equal(_gather_gpu(w, buf, starts, lens), exp[w]), \
                         (bs, depth, item_rows, w)
 
