@@ -139,7 +139,8 @@ int pospopcnt_masked(int w, uint64_t *counts, const void *words, size_t n, const
  * memory belongs to another allocator.  The paper has no counterpart; this
  * is a property of this library's batching.
  *
- * Same arguments, kernels and results as pospopcnt_batch, but the work plan
+ * Same arguments (w from 1 to 64), kernels and results as pospopcnt_batch,
+ * but the work plan
  * lives in a fixed array of the library's own device image (about 513 KiB,
  * held by every GPU that loads the library until the process exits) instead
  * of a cudaMalloc'ed workspace: no call allocates or frees anything.  Limit:
