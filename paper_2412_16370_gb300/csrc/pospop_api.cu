@@ -86,6 +86,7 @@ TuneTable default_tune() {
   t.max_rows_per_warp = kMaxRowsPerWarp;
   t.regroup = 0;
   t.pdl = 1;
+  t.staged = 1;
   t.set_source("built-in defaults");
   return t;
 }
@@ -100,6 +101,8 @@ TuneTable default_tune() {
 //                                  flush, 1 = per-lane bit regroup)
 //   pdl <0|1>                     (1 = programmatic dependent launch: a kernel's
 //                                  launch overlaps the previous kernel's run)
+//   staged <0|1>                  (1 = selected counts of 16-byte-aligned spans
+//                                  stage their input in shared memory by bulk copies)
 int parse_tune(const char *text, TuneTable *out) {
   TuneTable t = default_tune();
   std::string s(text);
@@ -141,6 +144,10 @@ int parse_tune(const char *text, TuneTable *out) {
       unsigned v;
       if (sscanf(line.c_str(), "%*s %u", &v) != 1 || v > 1) return POSPOP_EINVAL;
       t.pdl = v;
+    } else if (strcmp(kind, "staged") == 0) {
+      unsigned v;
+      if (sscanf(line.c_str(), "%*s %u", &v) != 1 || v > 1) return POSPOP_EINVAL;
+      t.staged = v;
     } else if (strcmp(kind, "split") == 0) {
       unsigned long long mr;
       if (sscanf(line.c_str(), "%*s %llu", &mr) != 1 || mr < 1 || mr > kMaxRowsPerWarp)
@@ -189,6 +196,9 @@ std::string format_tune(const DevCtx &ctx, const TuneTable &t) {
            t.regroup);
   s += line;
   snprintf(line, sizeof line, "# pdl <0 | 1 programmatic dependent launch>\npdl %u\n", t.pdl);
+  s += line;
+  snprintf(line, sizeof line, "# staged <0 | 1 bulk-copy staging for selected counts>\nstaged %u\n",
+           t.staged);
   s += line;
   if (t.max_rows_per_warp != kMaxRowsPerWarp) {
     snprintf(line, sizeof line, "split %llu\n", (unsigned long long)t.max_rows_per_warp);
@@ -278,6 +288,18 @@ static int init_ctx(DevCtx &c, int device) {
       return POSPOP_ECUDA;
     }
     c.occ_roof[i] = n > 0 ? n : 1;
+  }
+  for (int i = 0; i < select_staged_variant_count(); i++) {
+    const Variant &v = select_staged_variant(i);
+    int n = 0;
+    if (cudaFuncSetAttribute(v.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, v.smem) !=
+            cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, v.fn, v.bs, (size_t)v.smem) !=
+            cudaSuccess) {
+      cudaGetLastError();
+      n = 0;   // the staged form is then not used
+    }
+    c.occ_select_staged[i] = n;
   }
   c.device = device;
   c.sms = sms;
@@ -696,7 +718,7 @@ static int launch_gather_with(DevCtx &ctx, const TuneTable &t, int w, unsigned l
   return POSPOP_OK;
 }
 
-static int launch_select_with(const DevCtx &ctx, const TuneTable &t, int w,
+static int launch_select_with(DevCtx &ctx, const TuneTable &t, int w,
                               unsigned long long *counts, const void *words, size_t n,
                               const void *select, cudaStream_t stream) {
   const uint64_t W = (uint64_t)w / 8;
@@ -717,7 +739,45 @@ static int launch_select_with(const DevCtx &ctx, const TuneTable &t, int w,
   Q.nbits = n;
   Q.nbytes = 4 * ((n + 31) / 32);
   Q.wlog = w == 8 ? 0u : w == 16 ? 1u : w == 32 ? 2u : 3u;
+  Q.nstaged = 0;
+  Q.status = nullptr;
   const uint64_t R = (P.s.G + 31) >> 5;
+  // Staged form: a 16-byte-aligned span and bitmap, and enough whole chunks
+  // (16 rows wholly inside the span, partial last granule excluded) to give
+  // every warp of the grid at least two.
+  {
+    const Variant &sv = select_staged_variant((int)Q.wlog);
+    const uint64_t warps = (uint64_t)ctx.sms * (uint64_t)(sv.bs / 32);
+    const uint64_t chunks = (P.s.G - (P.s.tail < 16 ? 1 : 0)) / 512;
+    if (t.staged && P.s.head == 0 && ((uintptr_t)select & 15u) == 0 &&
+        ctx.occ_select_staged[Q.wlog] >= 1 && chunks >= 2 * warps &&
+        chunks / warps < (uint64_t(1) << 22)) {   // u32 lane counters: 512 per chunk
+      int *status = nullptr;
+      {
+        std::lock_guard<std::mutex> g(ctx.mu);
+        Workspace *ws = nullptr;
+        const int rc = get_ws(ctx, stream, 0, &ws);
+        if (rc != POSPOP_OK) return rc;
+        status = ws->status;
+      }
+      if (cudaMemsetAsync(status, 0, sizeof(int), stream) != cudaSuccess) {
+        cudaGetLastError();
+        return POSPOP_ECUDA;
+      }
+      Q.nstaged = chunks;
+      Q.status = status;
+      P.row_begin = 0;
+      P.row_end = R;
+      void *args[] = {&Q};
+      if (launch_kernel(sv.fn, dim3(ctx.sms), dim3(sv.bs), args, stream, t.pdl != 0,
+                        (size_t)sv.smem) != cudaSuccess) {
+        cudaGetLastError();
+        return POSPOP_ECUDA;
+      }
+      note_launches(1);
+      return POSPOP_OK;
+    }
+  }
   // the selection kernel is ALU-heavier than the plain count and runs best
   // in a single wave (measured on GB300): cap the blocks per SM at occupancy
   TuneTable ts = t;

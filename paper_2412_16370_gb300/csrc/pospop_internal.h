@@ -97,6 +97,8 @@ struct SelectParams {
   uint64_t nbits;               // words
   uint64_t nbytes;              // readable bitmap bytes
   uint32_t wlog;                // log2 of the word size in bytes
+  uint64_t nstaged;             // staged form: chunks of 16 rows staged in shared memory
+  int *status;                  // staged form: set to POSPOP_ETIMEDOUT if a wait expires
 };
 
 struct RooflineParams {
@@ -138,6 +140,8 @@ int gather_variant_count();
 const Variant &gather_variant(int i);
 int gather256_variant_count();
 const Variant &gather256_variant(int i);
+int select_staged_variant_count();
+const Variant &select_staged_variant(int wlog);
 int select_variant_count();
 const Variant &select_variant(int i);
 const void *plan_items_gather_fn();

@@ -13,6 +13,7 @@
 // Both compute the exact sum of the 32-bit little-endian words.
 #include <cstdint>
 
+#include "pospop_bulk.cuh"
 #include "pospop_device.cuh"
 #include "pospop_internal.h"
 #include "pospopcnt.h"
@@ -57,51 +58,6 @@ __global__ void __launch_bounds__(BS) roofline_kernel(RooflineParams P) {
 // ---------------------------------------------------------------------------
 // Bulk-copy staging.
 // ---------------------------------------------------------------------------
-constexpr uint32_t kBulkChunk = 8192;                  // bytes per chunk = 512 granules
-constexpr long long kBulkWaitCycles = 1ll << 31;       // about a second at 2 GHz
-
-__device__ __forceinline__ uint32_t smem_addr(const void *p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(uint32_t bar) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
-}
-
-// Expect `bytes` on the barrier's current phase (this thread's arrival), then
-// copy them from global to shared memory; the copy completes the bytes.
-// dst, src and bytes are multiples of 16.
-__device__ __forceinline__ void bulk_copy(uint32_t dst, const void *src, uint32_t bytes,
-                                          uint32_t bar) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
-               : "memory");
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-          dst),
-      "l"(src), "r"(bytes), "r"(bar)
-      : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
-  uint32_t done;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n}"
-      : "=r"(done)
-      : "r"(bar), "r"(parity)
-      : "memory");
-  return done != 0;
-}
-
-// Wait for the barrier phase with the given parity to complete; false if it
-// has not after kBulkWaitCycles.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-  const long long t0 = clock64();
-  while (!mbar_try(bar, parity))
-    if (clock64() - t0 > kBulkWaitCycles) return false;
-  return true;
-}
-
 template <int NW, int S>
 __global__ void __launch_bounds__(NW * 32, 1) roofline_bulk_kernel(RooflineParams P) {
   extern __shared__ __align__(128) uint8_t smem[];

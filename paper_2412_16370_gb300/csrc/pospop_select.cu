@@ -7,6 +7,8 @@
 #include <cstdint>
 
 #include "pospop_batch.cuh"
+#include "pospop_bulk.cuh"
+#include "pospopcnt.h"
 
 namespace pospop {
 
@@ -45,6 +47,143 @@ __global__ void __launch_bounds__(BS, MINB) select_kernel(SelectParams Q) {
     if (v) atomicAdd(&P.counts[threadIdx.x], v);
   }
 }
+
+// ---------------------------------------------------------------------------
+// Staged form, for a span that starts on a 16-byte boundary.  The selected
+// count does about half again the plain count's arithmetic per byte, so with
+// its loads in registers a warp issues the next group's loads late and DRAM
+// idles.  Here the copy engine keeps the bytes in flight instead: each warp
+// owns a ring of S stages in shared memory, one CSA group (16 rows, 8 KiB of
+// words) plus its 64 * CNT bytes of selection bits per stage, both filled by
+// bulk copies (cp.async.bulk) that complete one mbarrier phase.  Chunk c is
+// rows 16c .. 16c + 15; warps take chunks c = gw, gw + TW, ... below
+// Q.nstaged (chunks wholly inside the span), and warp 0 counts the remaining
+// rows with count_rows.  With a 16-byte-aligned start a granule's selection
+// window never straddles a bitmap word.
+// ---------------------------------------------------------------------------
+constexpr int kStagedWarps = 8;
+constexpr int kStagedDepth = 3;
+
+template <int WLOG>
+__host__ __device__ constexpr uint32_t staged_stage_bytes() {
+  return kBulkChunk + 64u * (16u >> WLOG);
+}
+
+template <int WLOG>
+constexpr int staged_smem() {
+  return kStagedWarps * kStagedDepth * (int)staged_stage_bytes<WLOG>() +
+         kStagedWarps * kStagedDepth * 8;
+}
+
+template <int NW, int S, int WLOG>
+__global__ void __launch_bounds__(NW * 32, 1) select_staged_kernel(SelectParams Q) {
+  constexpr uint32_t CNT = 16u >> WLOG;                // selection bits per granule
+  constexpr uint32_t kSel = 64u * CNT;                 // selection bytes per chunk
+  constexpr uint32_t kStage = staged_stage_bytes<WLOG>();
+  extern __shared__ __align__(128) uint8_t smem[];
+  __shared__ unsigned long long acc[64];
+  pdl_enter();
+  const StreamParams &P = Q.sp;
+  const unsigned lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+  if (threadIdx.x < 64) acc[threadIdx.x] = 0ull;
+  __syncthreads();
+
+  uint8_t *ring = smem + (size_t)warp * S * kStage;
+  uint64_t *bars = reinterpret_cast<uint64_t *>(smem + (size_t)NW * S * kStage) + warp * S;
+  const uint64_t TW = (uint64_t)gridDim.x * NW;
+  const uint64_t gw = (uint64_t)blockIdx.x * NW + warp;
+  const uint64_t nch = Q.nstaged;
+  Span s;
+  s.A = P.s.A;
+  s.G = P.s.G;
+  s.head = P.s.head;
+  s.tail = P.s.tail;
+  const Xpose xk = make_xpose(lane);
+  uint32_t cnt[4] = {0u, 0u, 0u, 0u};
+
+  auto fill = [&](int k, uint64_t c) {   // lane 0 only
+    const uint32_t bar = smem_addr(bars + k);
+    mbar_expect(bar, kStage);
+    bulk_copy_tx(smem_addr(ring + k * kStage), s.A + c * kBulkChunk, kBulkChunk, bar);
+    bulk_copy_tx(smem_addr(ring + k * kStage + kBulkChunk), Q.bits + c * kSel, kSel, bar);
+  };
+  if (lane == 0) {
+    for (int k = 0; k < S; k++) mbar_init(smem_addr(bars + k));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    for (int k = 0; k < S; k++)
+      if (gw + (uint64_t)k * TW < nch) fill(k, gw + (uint64_t)k * TW);
+  }
+  __syncwarp();
+
+  Planes p;
+  p.a1 = p.a2 = p.a4 = p.a8 = v4_zero();
+  uint64_t it = 0;
+  bool timed_out = false;
+  for (uint64_t c = gw; c < nch; c += TW, it++) {
+    const int k = (int)(it % S);
+    if (!__all_sync(kFull, mbar_wait(smem_addr(bars + k), (uint32_t)((it / S) & 1u)))) {
+      timed_out = true;
+      break;
+    }
+    const uint4 *d = reinterpret_cast<const uint4 *>(ring + k * kStage);
+    const uint32_t *sel = reinterpret_cast<const uint32_t *>(ring + k * kStage + kBulkChunk);
+    V4 v[16];
+#pragma unroll
+    for (int r = 0; r < 16; r++) {
+      const uint4 x = d[r * 32 + lane];
+      v[r] = V4{{x.x, x.y, x.z, x.w}};
+      const uint32_t bit = (uint32_t)(r * 32 + lane) * CNT;
+      apply_selection<WLOG>(v[r], sel[bit >> 5] >> (bit & 31u));
+    }
+    __syncwarp();   // every lane has read the stage before it is refilled
+    const uint64_t nx = c + (uint64_t)S * TW;
+    if (lane == 0 && nx < nch) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      fill(k, nx);
+    }
+    flush_plane<4>(cnt, csa16(p, v), xk);
+  }
+  if (timed_out) {
+    // report, then wait (bounded again) for this warp's copies still in
+    // flight so that none lands after the block has left; the block still
+    // meets at the barrier below
+    if (lane == 0 && Q.status) atomicExch(Q.status, POSPOP_ETIMEDOUT);
+    for (uint64_t j = 0, c = gw + it * TW; j < (uint64_t)S && c < nch; j++, c += TW)
+      (void)mbar_wait(smem_addr(bars + (int)((it + j) % S)), (uint32_t)(((it + j) / S) & 1u));
+  }
+  // final accumulation of the staged chunks (Section 4.5)
+  flush_plane<3>(cnt, p.a8, xk);
+  flush_plane<2>(cnt, p.a4, xk);
+  flush_plane<1>(cnt, p.a2, xk);
+  flush_plane<0>(cnt, p.a1, xk);
+  // rows after the staged chunks: the span's end (partial granule, rows
+  // past the last whole group)
+  if (gw == 0) {
+    const uint64_t r0 = 16u * nch, R = span_rows(s);
+    if (R > r0) {
+      SelectLoader<0, WLOG> ld;
+      ld.m = Selection{Q.bits, Q.nbits, Q.nbytes, 0u};
+      count_rows<16, 0>(s, r0, 1, R - r0, lane, xk, cnt, ld);
+    }
+  }
+  fold_counts(cnt, P.w, P.rot, lane, [&](uint32_t j, unsigned long long v) {
+    if (v) atomicAdd(&acc[j], v);
+  });
+  __syncthreads();
+  if ((int)threadIdx.x < P.w) {
+    const unsigned long long v = acc[threadIdx.x];
+    if (v) atomicAdd(&P.counts[threadIdx.x], v);
+  }
+}
+
+#define POSPOP_SELS(WL)                                                                         \
+  Variant{reinterpret_cast<const void *>(&select_staged_kernel<kStagedWarps, kStagedDepth, WL>), \
+          kStagedWarps * 32, 1, 16, 0, staged_smem<WL>()}
+static const Variant kSelectStaged[] = {POSPOP_SELS(0), POSPOP_SELS(1), POSPOP_SELS(2),
+                                        POSPOP_SELS(3)};
+
+int select_staged_variant_count() { return 4; }
+const Variant &select_staged_variant(int wlog) { return kSelectStaged[wlog]; }
 
 // Variants: the launch shapes the tune table uses (flush depth 16), each
 // specialised for the four word sizes; index = 4 * shape + log2(W).

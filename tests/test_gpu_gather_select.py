@@ -213,3 +213,30 @@ def test_masked_and_wide_every_tune_shape(gpu, orc, tune_override):
                 pp.pospopcnt_async(256, c, words)
                 torch.cuda.synchronize()
                 assert np.array_equal(counts_np(c), exp256), (bs, depth, hint)
+
+
+@pytest.mark.parametrize("w", WORD_W)
+def test_masked_staged_form(gpu, orc, tune_override, w):
+    """Selected counts of 16-byte-aligned spans large enough for the staged
+    form (bulk copies into shared memory, at least two 16-row chunks per warp
+    of the grid), with ragged ends, against the oracle and against the
+    register form (tune entry `staged 0`); a bitmap that is 4- but not
+    16-byte aligned takes the register form."""
+    W = w // 8
+    base_tune = pp.pospopcnt_tune_describe()
+    keep = "\n".join(l for l in base_tune.splitlines() if not l.startswith("staged"))
+    for extra, seed in ((0, 1), (3, 2), ((1 << 20) // W + 1, 3)):
+        n = (24 << 20) // W + extra
+        words_h = synth.random_bytes(n * W, seed=seed * 10 + w)
+        sel_h = synth.random_bytes(4 * ((n + 31) // 32), seed=seed * 10 + w + 1)
+        words = _dev_bytes(words_h, gpu, 0)
+        assert words.data_ptr() % 16 == 0
+        exp = orc.masked(w, words_h, n, sel_h)
+        sel16 = _dev_bytes(sel_h, gpu, 0)
+        sel4 = _dev_bytes(sel_h, gpu, 4)
+        assert sel16.data_ptr() % 16 == 0 and sel4.data_ptr() % 16 == 4
+        for staged in (1, 0):
+            tune_override(keep + f"\nstaged {staged}\n")
+            assert np.array_equal(_masked_gpu(w, words, n, sel16), exp), (n, staged)
+            assert np.array_equal(_masked_gpu(w, words, n, sel4), exp), (n, staged)
+        assert pp.pospopcnt_batch_status() == pp.POSPOP_OK
