@@ -86,7 +86,7 @@ TuneTable default_tune() {
   t.max_rows_per_warp = kMaxRowsPerWarp;
   t.regroup = 0;
   t.pdl = 1;
-  t.staged = 1;
+  t.staged = 3;   // 16 warps x 1 stage: measured fastest on GB300
   t.set_source("built-in defaults");
   return t;
 }
@@ -101,8 +101,10 @@ TuneTable default_tune() {
 //                                  flush, 1 = per-lane bit regroup)
 //   pdl <0|1>                     (1 = programmatic dependent launch: a kernel's
 //                                  launch overlaps the previous kernel's run)
-//   staged <0|1>                  (1 = selected counts of 16-byte-aligned spans
-//                                  stage their input in shared memory by bulk copies)
+//   staged <0|k>                  (k > 0: selected counts of 16-byte-aligned spans
+//                                  stage their input in shared memory by bulk copies,
+//                                  ring shape k: 1 = 8 warps x 3 stages, 2 = 12 x 2,
+//                                  3 = 16 x 1; 0 = loads into registers)
 int parse_tune(const char *text, TuneTable *out) {
   TuneTable t = default_tune();
   std::string s(text);
@@ -146,7 +148,8 @@ int parse_tune(const char *text, TuneTable *out) {
       t.pdl = v;
     } else if (strcmp(kind, "staged") == 0) {
       unsigned v;
-      if (sscanf(line.c_str(), "%*s %u", &v) != 1 || v > 1) return POSPOP_EINVAL;
+      if (sscanf(line.c_str(), "%*s %u", &v) != 1 || (int)v > select_staged_variant_count() / 4)
+        return POSPOP_EINVAL;
       t.staged = v;
     } else if (strcmp(kind, "split") == 0) {
       unsigned long long mr;
@@ -197,7 +200,8 @@ std::string format_tune(const DevCtx &ctx, const TuneTable &t) {
   s += line;
   snprintf(line, sizeof line, "# pdl <0 | 1 programmatic dependent launch>\npdl %u\n", t.pdl);
   s += line;
-  snprintf(line, sizeof line, "# staged <0 | 1 bulk-copy staging for selected counts>\nstaged %u\n",
+  snprintf(line, sizeof line,
+           "# staged <0 registers | k bulk-copy staging ring shape> (selected counts)\nstaged %u\n",
            t.staged);
   s += line;
   if (t.max_rows_per_warp != kMaxRowsPerWarp) {
@@ -746,11 +750,12 @@ static int launch_select_with(DevCtx &ctx, const TuneTable &t, int w,
   // (16 rows wholly inside the span, partial last granule excluded) to give
   // every warp of the grid at least two.
   {
-    const Variant &sv = select_staged_variant((int)Q.wlog);
+    const int si = t.staged ? 4 * ((int)t.staged - 1) + (int)Q.wlog : 0;
+    const Variant &sv = select_staged_variant(si);
     const uint64_t warps = (uint64_t)ctx.sms * (uint64_t)(sv.bs / 32);
     const uint64_t chunks = (P.s.G - (P.s.tail < 16 ? 1 : 0)) / 512;
     if (t.staged && P.s.head == 0 && ((uintptr_t)select & 15u) == 0 &&
-        ctx.occ_select_staged[Q.wlog] >= 1 && chunks >= 2 * warps &&
+        ctx.occ_select_staged[si] >= 1 && chunks >= 2 * warps &&
         chunks / warps < (uint64_t(1) << 22)) {   // u32 lane counters: 512 per chunk
       int *status = nullptr;
       {

@@ -141,7 +141,7 @@ const Variant &gather_variant(int i);
 int gather256_variant_count();
 const Variant &gather256_variant(int i);
 int select_staged_variant_count();
-const Variant &select_staged_variant(int wlog);
+const Variant &select_staged_variant(int i);
 int select_variant_count();
 const Variant &select_variant(int i);
 const void *plan_items_gather_fn();

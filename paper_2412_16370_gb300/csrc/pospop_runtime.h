@@ -44,7 +44,8 @@ struct TuneTable {
   uint64_t max_rows_per_warp;   // single-array launch split (<= kMaxRowsPerWarp)
   uint32_t regroup;             // w = 8 short sequences: 1 = per-lane bit regroup, 0 = transpose
   uint32_t pdl;                 // 1 = launch with programmatic stream serialization
-  uint32_t staged;              // 1 = selected counts of aligned spans stage input via bulk copies
+  uint32_t staged;              // selected counts of aligned spans: 0 = registers, k > 0 =
+                                // bulk-copy staging with ring shape k - 1
   char source[240];             // where the table came from (copied with the table: no heap)
   void set_source(const char *s);
 };
@@ -80,7 +81,7 @@ struct DevCtx {
   int occ_stream[64] = {0};
   int occ_batch[64] = {0};
   int occ_roof[16] = {0};
-  int occ_select_staged[4] = {0};
+  int occ_select_staged[16] = {0};
 };
 
 // Returns the context of the current device, setting it up if needed, or

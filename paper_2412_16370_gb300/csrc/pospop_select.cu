@@ -61,18 +61,14 @@ __global__ void __launch_bounds__(BS, MINB) select_kernel(SelectParams Q) {
 // rows with count_rows.  With a 16-byte-aligned start a granule's selection
 // window never straddles a bitmap word.
 // ---------------------------------------------------------------------------
-constexpr int kStagedWarps = 8;
-constexpr int kStagedDepth = 3;
-
 template <int WLOG>
 __host__ __device__ constexpr uint32_t staged_stage_bytes() {
   return kBulkChunk + 64u * (16u >> WLOG);
 }
 
-template <int WLOG>
+template <int NW, int S, int WLOG>
 constexpr int staged_smem() {
-  return kStagedWarps * kStagedDepth * (int)staged_stage_bytes<WLOG>() +
-         kStagedWarps * kStagedDepth * 8;
+  return NW * S * (int)staged_stage_bytes<WLOG>() + NW * S * 8;
 }
 
 template <int NW, int S, int WLOG>
@@ -176,14 +172,20 @@ __global__ void __launch_bounds__(NW * 32, 1) select_staged_kernel(SelectParams 
   }
 }
 
-#define POSPOP_SELS(WL)                                                                         \
-  Variant{reinterpret_cast<const void *>(&select_staged_kernel<kStagedWarps, kStagedDepth, WL>), \
-          kStagedWarps * 32, 1, 16, 0, staged_smem<WL>()}
-static const Variant kSelectStaged[] = {POSPOP_SELS(0), POSPOP_SELS(1), POSPOP_SELS(2),
-                                        POSPOP_SELS(3)};
+// Ring shapes (warps per block, stages per warp), each for the four word
+// sizes; index = 4 * shape + log2(W).  `depth` records the stages.
+#define POSPOP_SELS(NW, S, WL)                                                          \
+  Variant{reinterpret_cast<const void *>(&select_staged_kernel<NW, S, WL>), NW * 32, 1, S, \
+          0, staged_smem<NW, S, WL>()}
+#define POSPOP_SELS4(NW, S) \
+  POSPOP_SELS(NW, S, 0), POSPOP_SELS(NW, S, 1), POSPOP_SELS(NW, S, 2), POSPOP_SELS(NW, S, 3)
+static const Variant kSelectStaged[] = {POSPOP_SELS4(8, 3), POSPOP_SELS4(12, 2),
+                                        POSPOP_SELS4(16, 1)};
 
-int select_staged_variant_count() { return 4; }
-const Variant &select_staged_variant(int wlog) { return kSelectStaged[wlog]; }
+int select_staged_variant_count() {
+  return (int)(sizeof(kSelectStaged) / sizeof(kSelectStaged[0]));
+}
+const Variant &select_staged_variant(int i) { return kSelectStaged[i]; }
 
 // Variants: the launch shapes the tune table uses (flush depth 16), each
 // specialised for the four word sizes; index = 4 * shape + log2(W).

@@ -219,9 +219,9 @@ def test_masked_and_wide_every_tune_shape(gpu, orc, tune_override):
 def test_masked_staged_form(gpu, orc, tune_override, w):
     """Selected counts of 16-byte-aligned spans large enough for the staged
     form (bulk copies into shared memory, at least two 16-row chunks per warp
-    of the grid), with ragged ends, against the oracle and against the
-    register form (tune entry `staged 0`); a bitmap that is 4- but not
-    16-byte aligned takes the register form."""
+    of the grid), with ragged ends, for every ring shape and the register
+    form (tune entry `staged k`), against the oracle; a bitmap that is 4- but
+    not 16-byte aligned takes the register form."""
     W = w // 8
     base_tune = pp.pospopcnt_tune_describe()
     keep = "\n".join(l for l in base_tune.splitlines() if not l.startswith("staged"))
@@ -235,7 +235,7 @@ def test_masked_staged_form(gpu, orc, tune_override, w):
         sel16 = _dev_bytes(sel_h, gpu, 0)
         sel4 = _dev_bytes(sel_h, gpu, 4)
         assert sel16.data_ptr() % 16 == 0 and sel4.data_ptr() % 16 == 4
-        for staged in (1, 0):
+        for staged in (1, 2, 3, 0):   # the three ring shapes, then the register form
             tune_override(keep + f"\nstaged {staged}\n")
             assert np.array_equal(_masked_gpu(w, words, n, sel16), exp), (n, staged)
             assert np.array_equal(_masked_gpu(w, words, n, sel4), exp), (n, staged)
