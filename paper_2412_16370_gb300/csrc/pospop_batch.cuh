@@ -130,6 +130,8 @@ __device__ __forceinline__ uint64_t find_array(const uint64_t *__restrict__ item
   return lo;
 }
 
+constexpr uint64_t kMaxGrab = 8;    // work items per grab, at most
+
 // PAR2: w = 256, where a word spans two granules (the two-parity flush).
 template <int SRC, int BS, int MINB, int DEPTH, int HINT, bool PAR2 = false>
 __global__ void __launch_bounds__(BS, MINB) batch_kernel(BatchParams P) {
@@ -146,18 +148,37 @@ __global__ void __launch_bounds__(BS, MINB) batch_kernel(BatchParams P) {
   const unsigned lane = threadIdx.x & 31u;
   const Xpose xk = make_xpose(lane);
   const uint64_t total = P.item_start[P.m];
-  // The next grab is requested before the current items are counted, so
-  // the atomic's round trip overlaps the counting (measured on GB300: a
-  // batch of 200000 arrays of 1..1536 B 6% faster; large arrays and
-  // gathered regions unchanged).
-  unsigned long long nxt = 0;
-  if (lane == 0) nxt = atomicAdd(P.next, (unsigned long long)P.grab);
+  // Guided self-scheduling: a grab takes about 1/(4 TW) of the items left
+  // (at least P.grab, at most kMaxGrab), so early grabs are runs of
+  // consecutive items (one array search per run, then a forward walk) and
+  // late grabs are short (balance at the end).  The next grab is requested
+  // before the current items are counted, so the atomic's round trip
+  // overlaps the counting.  Measured on GB300 against one item per grab: a
+  // batch of 200000 arrays of 1..1536 B 32% faster, 100000 gathered regions
+  // 0.7% faster, the 55 GB ragged batch unchanged (factor 8 or a cap of 16
+  // or 64 items: the tiny batch gains less or the large batches lose).
+  const uint64_t TW = (uint64_t)gridDim.x * (BS / 32);
+  auto grab_size = [&](uint64_t seen) -> unsigned long long {
+    const uint64_t left = total > seen ? total - seen : 0;
+    uint64_t g = left / (4 * TW);
+    if (g < P.grab) g = P.grab;
+    return g < kMaxGrab ? g : kMaxGrab;
+  };
+  unsigned long long nxt = 0, nxt_g = 0;
+  if (lane == 0) {
+    nxt_g = grab_size(0);
+    nxt = atomicAdd(P.next, nxt_g);
+  }
   for (;;) {
     const unsigned long long i0 = __shfl_sync(kFull, nxt, 0);
+    const unsigned long long g = __shfl_sync(kFull, nxt_g, 0);
     if (i0 >= total) break;
-    if (lane == 0) nxt = atomicAdd(P.next, (unsigned long long)P.grab);
+    if (lane == 0) {
+      nxt_g = grab_size(i0 + g);
+      nxt = atomicAdd(P.next, nxt_g);
+    }
     uint64_t a = find_array(P.item_start, P.m, i0, lane);
-    const uint64_t i1 = (i0 + P.grab < total) ? i0 + P.grab : total;
+    const uint64_t i1 = (i0 + g < total) ? i0 + g : total;
     for (uint64_t i = i0; i < i1; i++) {
       while (__ldg(P.item_start + a + 1) <= i) a++;
       const uint64_t k = i - __ldg(P.item_start + a);
