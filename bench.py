@@ -16,6 +16,8 @@ also carries:
   input, every step's input crosses the CPU-GPU link, counts read back);
 * batched: the ragged one-hot batch (200000 uint8 arrays, log-uniform
   1 B .. 4 MiB, about 55 GB), one batched call vs one launch per array;
+* plain: the 1 MiB w = 16 configuration, GPU microseconds per call and
+  the oracle's time;
 * short: microseconds per call for short unaligned arrays, one launch each,
   plain and graph-replayed;
 * cpu_baseline: the CPU oracle on the host cores on a bounded sample;
@@ -344,6 +346,7 @@ def run_ours(args):
         if rank == 0:
             for key, fn in (("batched", lambda: _batched(pp, synth, synth_device, dev, stream,
                                                          achieved, hbm_peak, m=args.batched_m)),
+                            ("plain", lambda: _plain(pp, synth_device, dev, stream)),
                             ("short", lambda: _short(pp, synth, synth_device, dev, stream)),
                             ("serving", lambda: _serving(pp, synth, data, nbytes, achieved, dev)),
                             ("masked", lambda: _masked(pp, synth_device, data, nbytes, dev,
@@ -470,6 +473,21 @@ def _batched(pp, synth, synth_device, dev, stream, large_gbs, hbm_peak, m=200000
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / reps
     ok = bool(np.array_equal(c.sum(dim=1).cpu().numpy(), (reps + 3) * sizes))
+    # the same call captured once into a CUDA graph and replayed
+    gs = torch.cuda.Stream()
+    graph = pp.pospopcnt_batch_graph_create(8, c, base, offs_d, m, gs)
+    try:
+        for _ in range(3):
+            pp.pospopcnt_graph_launch(graph, gs)
+        gs.synchronize()
+        e0.record(gs)
+        for _ in range(reps):
+            pp.pospopcnt_graph_launch(graph, gs)
+        e1.record(gs)
+        gs.synchronize()
+        ms_graph = e0.elapsed_time(e1) / reps
+    finally:
+        pp.pospopcnt_graph_destroy(graph)
     # one launch per array
     c.zero_()
     basep = base.data_ptr()
@@ -538,12 +556,44 @@ def _batched(pp, synth, synth_device, dev, stream, large_gbs, hbm_peak, m=200000
             "workload": f"{m} one-hot uint8 arrays (Zipf(1.1) over 8 classes), sizes log-uniform "
                         "1 B..4 MiB, back to back (unaligned starts), w=8",
             "bytes": total, "GBps": round(gbs, 1), "ms": round(ms, 3),
+            "graph_replay_ms": round(ms_graph, 3),
             "frac_of_large_array": round(gbs / large_gbs, 4),
             "frac_of_hbm_peak": round(gbs / hbm_peak, 4),
             "per_array_launches": {"GBps": round(total / (ms_per / 1e3) / 1e9, 1),
                                    "ms": round(ms_per, 1), "host_wall_s": round(wall, 2)},
             "speedup_vs_per_array": round(ms_per / ms, 1),
             "one_hot_sums_ok": ok}
+
+
+def _plain(pp, synth_device, dev, stream):
+    """The plain configuration: 524288 uint16 words (1 MiB) of Bernoulli(0.5)
+    bits from seed 0, 16-byte aligned, w = 16: GPU time per call (queued back
+    to back, and the synchronous Fig. 2 form) next to the oracle's."""
+    import torch
+    n = 524288
+    words = torch.empty(2 * n, dtype=torch.uint8, device=dev)
+    synth_device.random_(words, 0)
+    c = torch.zeros(16, dtype=torch.int64, device=dev)
+    ms = _time_ms(lambda: pp.pospopcnt_async(16, c, words, 2 * n, stream), stream, reps=200)
+    torch.cuda.synchronize()
+    for _ in range(20):
+        pp.pospopcnt_u16(c, words, n)
+    t0 = time.perf_counter()
+    for _ in range(200):
+        pp.pospopcnt_u16(c, words, n)
+    sync_us = (time.perf_counter() - t0) / 200 * 1e6
+    import oracle
+    orc = oracle.load()
+    host = words.cpu().numpy()
+    ora = _oracle_rate(lambda: orc.typed(16, host.view(np.uint16)), lambda: host.size, budget_s=1.0)
+    one = torch.zeros(16, dtype=torch.int64, device=dev)
+    pp.pospopcnt_u16(one, words, n)
+    ok = bool(np.array_equal(one.cpu().numpy().view(np.uint64), orc.typed(16, host.view(np.uint16))))
+    return {"workload": "524288 uint16 words (1 MiB), Bernoulli(0.5) bits, seed 0, 16-byte aligned, w=16",
+            "device_us_per_call": round(ms * 1e3, 2), "GBps": round(2 * n / (ms / 1e3) / 1e9, 1),
+            "sync_call_us": round(sync_us, 2),
+            "oracle_ms_per_call": round(2 * n / (ora * 1e9) * 1e3, 3), "oracle_GBps": ora,
+            "oracle_sample": "the whole array, 1 thread (Fig. 2 loop)", "counts_ok": ok}
 
 
 @contextlib.contextmanager
@@ -868,11 +918,11 @@ def main():
                     help="arrays in the batched section (200000 = the workload)")
     ap.add_argument("--ref-sample-mib", type=int, default=16)
     ap.add_argument("--quick", action="store_true",
-                    help="skip every section after the headline (e2e, batched, short, "
-                         "serving, masked, gather, cpu_baseline, sweep)")
+                    help="skip every section after the headline (e2e, batched, plain, "
+                         "short, serving, masked, gather, cpu_baseline, sweep)")
     ap.add_argument("--sections", default="",
                     help="comma list of extra sections to run "
-                         "(e2e,batched,short,serving,masked,gather,cpu_baseline,sweep)")
+                         "(e2e,batched,plain,short,serving,masked,gather,cpu_baseline,sweep)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
