@@ -179,10 +179,50 @@ __global__ void __launch_bounds__(BS, MINB) batch_kernel(BatchParams P) {
     }
     uint64_t a = find_array(P.item_start, P.m, i0, lane);
     const uint64_t i1 = (i0 + g < total) ? i0 + g : total;
+    // Metadata window: lane j holds item_start and the start (and, gathered,
+    // the length) of array a + j, read by one warp-wide load each, so the
+    // grab's items find their arrays with a ballot instead of a chain of
+    // dependent loads per item (arrays a .. a + 30 are covered; an item of a
+    // later array takes the per-item loads).
+    const uint64_t a_win = a;
+    const uint64_t wj = a_win + lane;
+    const uint64_t win_start = wj <= P.m ? __ldg(P.item_start + wj) : ~0ull;
+    uint64_t win_lo = 0, win_len = 0;
+    if (wj <= P.m) {
+      if (SRC == kSrcGather) {
+        if (wj < P.m) {
+          win_lo = __ldg(P.gptrs + wj);
+          win_len = __ldg(P.glens + wj);
+        }
+      } else {
+        win_lo = __ldg(P.offsets + wj);
+      }
+    }
     for (uint64_t i = i0; i < i1; i++) {
-      while (__ldg(P.item_start + a + 1) <= i) a++;
-      const uint64_t k = i - __ldg(P.item_start + a);
-      const ArrayRef r = array_ref<SRC>(P, a);
+      const unsigned in = __ballot_sync(kFull, win_start <= i);
+      const int j = __popc(in) - 1;   // window arrays with item_start <= i form a prefix
+      ArrayRef r;
+      uint64_t k;
+      if (j < 31) {
+        a = a_win + (uint64_t)j;
+        k = i - __shfl_sync(kFull, win_start, j);
+        const uint64_t lo = __shfl_sync(kFull, win_lo, j);
+        if (SRC == kSrcGather) {
+          r.s = lo;
+          r.e = lo + __shfl_sync(kFull, win_len, j);
+          r.out = P.counts;
+        } else {
+          const uint64_t hi = __shfl_sync(kFull, win_lo, j + 1);
+          r.s = (uint64_t)P.base + lo;
+          r.e = (uint64_t)P.base + hi;
+          r.out = P.counts + a * (uint64_t)P.w;
+        }
+        r.w = P.w;
+      } else {
+        while (__ldg(P.item_start + a + 1) <= i) a++;
+        k = i - __ldg(P.item_start + a);
+        r = array_ref<SRC>(P, a);
+      }
       Span s;
       const uint64_t A = r.s & ~15ull;
       s.A = reinterpret_cast<const uint8_t *>(A);
