@@ -849,7 +849,7 @@ static int host_count(DevCtx &ctx, int w, uint64_t *counts, const void *bytes, s
     cudaGetLastError();
     return POSPOP_ECUDA;
   }
-  const bool staged = kb == kPageable || getenv("POSPOP_HOST_STAGED") != nullptr;
+  const bool staged = kb == kPageable;
   if (!staged) {
     // Pinned memory: the kernel reads it in place over the CPU-GPU link.
     rc = launch_stream_with(ctx, t, w, st.dcounts, dev_bytes, nbytes, st.comp);
