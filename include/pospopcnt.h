@@ -198,11 +198,14 @@ int pospopcnt_roofline_read(const void *bytes, size_t nbytes, uint64_t *sum, voi
 int pospopcnt_plan(int w, size_t nbytes, uint32_t plan[8]);
 
 /*
- * Tune table.  pospopcnt_autotune times every launch candidate for each
- * size class on the current device (allocating a scratch buffer of up to
- * max_bytes), installs the fastest, and, if path is not NULL, writes the
- * table there.  pospopcnt_tune_load installs a table written earlier;
- * pospopcnt_tune_describe writes a one-line-per-class summary into buf.
+ * Tune table.  A device starts with the table in the file named by the
+ * environment variable POSPOP_TUNE_FILE, else pospopcnt_tune.txt next to
+ * the library, else built-in defaults.  pospopcnt_autotune times every launch
+ * candidate for each size class on the current device (allocating a scratch
+ * buffer of up to max_bytes), installs the fastest, and, if path is not
+ * NULL, writes the table there.  pospopcnt_tune_load installs a table
+ * written earlier; pospopcnt_tune_describe writes the current table, in the
+ * same text format, into buf.
  */
 int pospopcnt_autotune(size_t max_bytes, const char *path);
 int pospopcnt_tune_load(const char *path);
