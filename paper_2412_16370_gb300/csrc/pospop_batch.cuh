@@ -106,11 +106,12 @@ __global__ void __launch_bounds__(kPlanThreads) plan_items_kernel(PlanParams P) 
 }
 
 // ---------------------------------------------------------------------------
-// Persistent counting.  Warps take `grab` consecutive work items per
-// atomic, find the first item's array with a 32-way warp search over
-// item_start, then walk forward.  Each item is a contiguous run of rows of
-// one array, counted with the per-thread algorithm and added to that
-// array's counters.
+// Persistent counting.  Warps take runs of consecutive work items per
+// atomic (guided: longer runs while much work is left), find the first
+// item's array with a 32-way warp search over item_start, and look the
+// run's other items up in a window of 32 arrays' metadata.  Each item is a
+// contiguous run of rows of one array, counted with the per-thread
+// algorithm and added to that array's counters.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ uint64_t find_array(const uint64_t *__restrict__ item_start, uint64_t m,
                                                uint64_t i, unsigned lane) {
