@@ -743,19 +743,30 @@ static int launch_select_with(DevCtx &ctx, const TuneTable &t, int w,
   Q.nbits = n;
   Q.nbytes = 4 * ((n + 31) / 32);
   Q.wlog = w == 8 ? 0u : w == 16 ? 1u : w == 32 ? 2u : 3u;
+  Q.chunk0 = 0;
   Q.nstaged = 0;
+  Q.sel_bytes = 0;
   Q.status = nullptr;
   const uint64_t R = (P.s.G + 31) >> 5;
-  // Staged form: a 16-byte-aligned span and bitmap, and enough whole chunks
-  // (16 rows wholly inside the span, partial last granule excluded) to give
-  // every warp of the grid at least two.
+  // Staged form: a 16-byte-aligned bitmap and enough chunks wholly inside
+  // the span (16 rows; not chunk 0 when the span starts inside a granule,
+  // not the partial last granule, and none whose bitmap bytes, rounded out
+  // to 16-byte blocks, pass the readable bitmap) to give every warp of the
+  // grid at least two.
   {
     const int si = t.staged ? 4 * ((int)t.staged - 1) + (int)Q.wlog : 0;
     const Variant &sv = select_staged_variant(si);
     const uint64_t warps = (uint64_t)ctx.sms * (uint64_t)(sv.bs / 32);
-    const uint64_t chunks = (P.s.G - (P.s.tail < 16 ? 1 : 0)) / 512;
-    if (t.staged && P.s.head == 0 && ((uintptr_t)select & 15u) == 0 &&
-        ctx.occ_select_staged[si] >= 1 && chunks >= 2 * warps &&
+    const uint64_t CNT = 16u >> Q.wlog;
+    const uint64_t h = P.s.head >> Q.wlog;
+    const uint64_t chunk0 = P.s.head ? 1 : 0;
+    const uint32_t sel_bytes = (uint32_t)(64 * CNT + (h ? 16 : 0));
+    uint64_t chunks = (P.s.G - (P.s.tail < 16 ? 1 : 0)) / 512;
+    while (chunks > chunk0 &&
+           (((chunks - 1) * 512 * CNT - h) >> 7) * 16 + sel_bytes > Q.nbytes)
+      chunks--;
+    if (t.staged && ((uintptr_t)select & 15u) == 0 && ctx.occ_select_staged[si] >= 1 &&
+        chunks >= chunk0 + 2 * warps &&
         chunks / warps < (uint64_t(1) << 22)) {   // u32 lane counters: 512 per chunk
       int *status = nullptr;
       {
@@ -769,7 +780,9 @@ static int launch_select_with(DevCtx &ctx, const TuneTable &t, int w,
         cudaGetLastError();
         return POSPOP_ECUDA;
       }
+      Q.chunk0 = chunk0;
       Q.nstaged = chunks;
+      Q.sel_bytes = sel_bytes;
       Q.status = status;
       P.row_begin = 0;
       P.row_end = R;

@@ -97,7 +97,9 @@ struct SelectParams {
   uint64_t nbits;               // words
   uint64_t nbytes;              // readable bitmap bytes
   uint32_t wlog;                // log2 of the word size in bytes
-  uint64_t nstaged;             // staged form: chunks of 16 rows staged in shared memory
+  uint64_t chunk0;              // staged form: chunks [chunk0, nstaged) of 16 rows are staged
+  uint64_t nstaged;             //   in shared memory (the others are counted from registers)
+  uint32_t sel_bytes;           // staged form: bitmap bytes copied per chunk
   int *status;                  // staged form: set to POSPOP_ETIMEDOUT if a wait expires
 };
 

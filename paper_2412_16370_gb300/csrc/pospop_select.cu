@@ -49,21 +49,24 @@ __global__ void __launch_bounds__(BS, MINB) select_kernel(SelectParams Q) {
 }
 
 // ---------------------------------------------------------------------------
-// Staged form, for a span that starts on a 16-byte boundary.  The selected
+// Staged form (a 16-byte-aligned bitmap).  The selected
 // count does about half again the plain count's arithmetic per byte, so with
 // its loads in registers a warp issues the next group's loads late and DRAM
 // idles.  Here the copy engine keeps the bytes in flight instead: each warp
 // owns a ring of S stages in shared memory, one CSA group (16 rows, 8 KiB of
 // words) plus its 64 * CNT bytes of selection bits per stage, both filled by
 // bulk copies (cp.async.bulk) that complete one mbarrier phase.  Chunk c is
-// rows 16c .. 16c + 15; warps take chunks c = gw, gw + TW, ... below
-// Q.nstaged (chunks wholly inside the span), and warp 0 counts the remaining
-// rows with count_rows.  With a 16-byte-aligned start a granule's selection
-// window never straddles a bitmap word.
+// rows 16c .. 16c + 15; warps take chunks c = chunk0 + gw, + TW, ... below
+// Q.nstaged (chunks wholly inside the span: chunk 0 only when the span
+// starts on a 16-byte boundary), and warp 0 counts the remaining rows with
+// count_rows.  A chunk's selection bits start h bits (h = words before the
+// start in granule 0) before a multiple of 512 * CNT bits, so the copy takes
+// the 16-byte-aligned bytes around them (one 16-byte block more when h > 0)
+// and every chunk's bits sit at the same offset in the stage.
 // ---------------------------------------------------------------------------
 template <int WLOG>
 __host__ __device__ constexpr uint32_t staged_stage_bytes() {
-  return kBulkChunk + 64u * (16u >> WLOG);
+  return kBulkChunk + 64u * (16u >> WLOG) + 16u;
 }
 
 template <int NW, int S, int WLOG>
@@ -97,17 +100,22 @@ __global__ void __launch_bounds__(NW * 32, 1) select_staged_kernel(SelectParams 
   const Xpose xk = make_xpose(lane);
   uint32_t cnt[4] = {0u, 0u, 0u, 0u};
 
+  const uint32_t h = P.s.head >> WLOG;                // words before the start in granule 0
+  const uint32_t sel_off = (128u - (h & 127u)) & 127u;  // bit offset of a chunk's bits in its copy
   auto fill = [&](int k, uint64_t c) {   // lane 0 only
     const uint32_t bar = smem_addr(bars + k);
-    mbar_expect(bar, kStage);
+    mbar_expect(bar, kBulkChunk + Q.sel_bytes);
     bulk_copy_tx(smem_addr(ring + k * kStage), s.A + c * kBulkChunk, kBulkChunk, bar);
-    bulk_copy_tx(smem_addr(ring + k * kStage + kBulkChunk), Q.bits + c * kSel, kSel, bar);
+    const uint64_t first_bit = c * (512u * CNT) - h;
+    bulk_copy_tx(smem_addr(ring + k * kStage + kBulkChunk), Q.bits + (first_bit >> 7) * 16u,
+                 Q.sel_bytes, bar);
   };
+  const uint64_t c0 = Q.chunk0 + gw;
   if (lane == 0) {
     for (int k = 0; k < S; k++) mbar_init(smem_addr(bars + k));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     for (int k = 0; k < S; k++)
-      if (gw + (uint64_t)k * TW < nch) fill(k, gw + (uint64_t)k * TW);
+      if (c0 + (uint64_t)k * TW < nch) fill(k, c0 + (uint64_t)k * TW);
   }
   __syncwarp();
 
@@ -115,7 +123,7 @@ __global__ void __launch_bounds__(NW * 32, 1) select_staged_kernel(SelectParams 
   p.a1 = p.a2 = p.a4 = p.a8 = v4_zero();
   uint64_t it = 0;
   bool timed_out = false;
-  for (uint64_t c = gw; c < nch; c += TW, it++) {
+  for (uint64_t c = c0; c < nch; c += TW, it++) {
     const int k = (int)(it % S);
     if (!__all_sync(kFull, mbar_wait(smem_addr(bars + k), (uint32_t)((it / S) & 1u)))) {
       timed_out = true;
@@ -128,8 +136,12 @@ __global__ void __launch_bounds__(NW * 32, 1) select_staged_kernel(SelectParams 
     for (int r = 0; r < 16; r++) {
       const uint4 x = d[r * 32 + lane];
       v[r] = V4{{x.x, x.y, x.z, x.w}};
-      const uint32_t bit = (uint32_t)(r * 32 + lane) * CNT;
-      apply_selection<WLOG>(v[r], sel[bit >> 5] >> (bit & 31u));
+      const uint32_t bit = sel_off + (uint32_t)(r * 32 + lane) * CNT;
+      const uint32_t sh = bit & 31u;
+      // a window straddles into the next word only when h is not a multiple
+      // of CNT; that word's bits then lie inside the copy
+      const uint32_t w1 = (sh + CNT > 32u) ? sel[(bit >> 5) + 1] : 0u;
+      apply_selection<WLOG>(v[r], __funnelshift_r(sel[bit >> 5], w1, sh));
     }
     __syncwarp();   // every lane has read the stage before it is refilled
     const uint64_t nx = c + (uint64_t)S * TW;
@@ -144,7 +156,7 @@ __global__ void __launch_bounds__(NW * 32, 1) select_staged_kernel(SelectParams 
     // flight so that none lands after the block has left; the block still
     // meets at the barrier below
     if (lane == 0 && Q.status) atomicExch(Q.status, POSPOP_ETIMEDOUT);
-    for (uint64_t j = 0, c = gw + it * TW; j < (uint64_t)S && c < nch; j++, c += TW)
+    for (uint64_t j = 0, c = c0 + it * TW; j < (uint64_t)S && c < nch; j++, c += TW)
       (void)mbar_wait(smem_addr(bars + (int)((it + j) % S)), (uint32_t)(((it + j) / S) & 1u));
   }
   // final accumulation of the staged chunks (Section 4.5)
@@ -152,15 +164,16 @@ __global__ void __launch_bounds__(NW * 32, 1) select_staged_kernel(SelectParams 
   flush_plane<2>(cnt, p.a4, xk);
   flush_plane<1>(cnt, p.a2, xk);
   flush_plane<0>(cnt, p.a1, xk);
-  // rows after the staged chunks: the span's end (partial granule, rows
-  // past the last whole group)
+  // rows outside the staged chunks: the span's start (chunk 0 when the
+  // span starts inside a granule) and end (partial granule, rows past the
+  // last staged group)
   if (gw == 0) {
-    const uint64_t r0 = 16u * nch, R = span_rows(s);
-    if (R > r0) {
-      SelectLoader<0, WLOG> ld;
-      ld.m = Selection{Q.bits, Q.nbits, Q.nbytes, 0u};
-      count_rows<16, 0>(s, r0, 1, R - r0, lane, xk, cnt, ld);
-    }
+    SelectLoader<0, WLOG> ld;
+    ld.m = Selection{Q.bits, Q.nbits, Q.nbytes, h};
+    const uint64_t R = span_rows(s);
+    if (Q.chunk0 > 0) count_rows<16, 0>(s, 0, 1, 16u * Q.chunk0, lane, xk, cnt, ld);
+    const uint64_t r0 = 16u * nch;
+    if (R > r0) count_rows<16, 0>(s, r0, 1, R - r0, lane, xk, cnt, ld);
   }
   fold_counts(cnt, P.w, P.rot, lane, [&](uint32_t j, unsigned long long v) {
     if (v) atomicAdd(&acc[j], v);

@@ -217,26 +217,27 @@ def test_masked_and_wide_every_tune_shape(gpu, orc, tune_override):
 
 @pytest.mark.parametrize("w", WORD_W)
 def test_masked_staged_form(gpu, orc, tune_override, w):
-    """Selected counts of 16-byte-aligned spans large enough for the staged
-    form (bulk copies into shared memory, at least two 16-row chunks per warp
-    of the grid), with ragged ends, for every ring shape and the register
-    form (tune entry `staged k`), against the oracle; a bitmap that is 4- but
-    not 16-byte aligned takes the register form."""
+    """Selected counts large enough for the staged form (bulk copies into
+    shared memory, at least two 16-row chunks per warp of the grid), with
+    16-byte-aligned and word-aligned starts and ragged ends, for every ring
+    shape and the register form (tune entry `staged k`), against the oracle;
+    a bitmap that is 4- but not 16-byte aligned takes the register form."""
     W = w // 8
     base_tune = pp.pospopcnt_tune_describe()
     keep = "\n".join(l for l in base_tune.splitlines() if not l.startswith("staged"))
-    for extra, seed in ((0, 1), (3, 2), ((1 << 20) // W + 1, 3)):
+    for extra, seed, pad in ((0, 1, 0), (3, 2, 0), ((1 << 20) // W + 1, 3, 0),
+                             (5, 4, W), (0, 5, 16 - W)):
         n = (24 << 20) // W + extra
         words_h = synth.random_bytes(n * W, seed=seed * 10 + w)
         sel_h = synth.random_bytes(4 * ((n + 31) // 32), seed=seed * 10 + w + 1)
-        words = _dev_bytes(words_h, gpu, 0)
-        assert words.data_ptr() % 16 == 0
+        words = _dev_bytes(words_h, gpu, pad)   # pad > 0: the start is inside a granule
+        assert words.data_ptr() % 16 == pad
         exp = orc.masked(w, words_h, n, sel_h)
         sel16 = _dev_bytes(sel_h, gpu, 0)
         sel4 = _dev_bytes(sel_h, gpu, 4)
         assert sel16.data_ptr() % 16 == 0 and sel4.data_ptr() % 16 == 4
         for staged in (1, 2, 3, 0):   # the three ring shapes, then the register form
             tune_override(keep + f"\nstaged {staged}\n")
-            assert np.array_equal(_masked_gpu(w, words, n, sel16), exp), (n, staged)
-            assert np.array_equal(_masked_gpu(w, words, n, sel4), exp), (n, staged)
+            assert np.array_equal(_masked_gpu(w, words, n, sel16), exp), (n, pad, staged)
+            assert np.array_equal(_masked_gpu(w, words, n, sel4), exp), (n, pad, staged)
         assert pp.pospopcnt_batch_status() == pp.POSPOP_OK
