@@ -746,27 +746,34 @@ static int launch_select_with(DevCtx &ctx, const TuneTable &t, int w,
   Q.chunk0 = 0;
   Q.nstaged = 0;
   Q.sel_bytes = 0;
+  Q.sel_base = nullptr;
+  Q.sel_bit0 = 0;
   Q.status = nullptr;
   const uint64_t R = (P.s.G + 31) >> 5;
-  // Staged form: a 16-byte-aligned bitmap and enough chunks wholly inside
-  // the span (16 rows; not chunk 0 when the span starts inside a granule,
-  // not the partial last granule, and none whose bitmap bytes, rounded out
-  // to 16-byte blocks, pass the readable bitmap) to give every warp of the
-  // grid at least two.
+  // Staged form: enough chunks wholly inside the span (16 rows; not chunk 0
+  // when the span or the bitmap starts inside a 16-byte block, not the
+  // partial last granule, and none whose bitmap bytes, rounded out to
+  // 16-byte blocks, pass the end of the readable bitmap) to give every warp
+  // of the grid at least two.  A chunk from 1 on never reads bitmap bytes
+  // before the bitmap's start (its bits start at least 512 * CNT - h >= 128
+  // bits in).
   {
     const int si = t.staged ? 4 * ((int)t.staged - 1) + (int)Q.wlog : 0;
     const Variant &sv = select_staged_variant(si);
     const uint64_t warps = (uint64_t)ctx.sms * (uint64_t)(sv.bs / 32);
     const uint64_t CNT = 16u >> Q.wlog;
-    const uint64_t h = P.s.head >> Q.wlog;
-    const uint64_t chunk0 = P.s.head ? 1 : 0;
-    const uint32_t sel_bytes = (uint32_t)(64 * CNT + (h ? 16 : 0));
+    const int64_t h = (int64_t)(P.s.head >> Q.wlog);
+    const uint64_t mb = (uintptr_t)select & 15u;       // bitmap bytes past a 16-byte block
+    const int64_t bit0 = (int64_t)(8 * mb) - h;
+    const uint64_t chunk0 = (P.s.head || mb) ? 1 : 0;
+    const uint32_t sel_bytes = (uint32_t)(64 * CNT + ((bit0 & 127) ? 16 : 0));
+    const uint64_t readable_end = mb + Q.nbytes;       // from the 16-byte-aligned base
     uint64_t chunks = (P.s.G - (P.s.tail < 16 ? 1 : 0)) / 512;
     while (chunks > chunk0 &&
-           (((chunks - 1) * 512 * CNT - h) >> 7) * 16 + sel_bytes > Q.nbytes)
+           ((uint64_t)((int64_t)((chunks - 1) * 512 * CNT) + bit0) >> 7) * 16 + sel_bytes >
+               readable_end)
       chunks--;
-    if (t.staged && ((uintptr_t)select & 15u) == 0 && ctx.occ_select_staged[si] >= 1 &&
-        chunks >= chunk0 + 2 * warps &&
+    if (t.staged && ctx.occ_select_staged[si] >= 1 && chunks >= chunk0 + 2 * warps &&
         chunks / warps < (uint64_t(1) << 22)) {   // u32 lane counters: 512 per chunk
       int *status = nullptr;
       {
@@ -783,6 +790,8 @@ static int launch_select_with(DevCtx &ctx, const TuneTable &t, int w,
       Q.chunk0 = chunk0;
       Q.nstaged = chunks;
       Q.sel_bytes = sel_bytes;
+      Q.sel_base = static_cast<const uint8_t *>(select) - mb;
+      Q.sel_bit0 = bit0;
       Q.status = status;
       P.row_begin = 0;
       P.row_end = R;

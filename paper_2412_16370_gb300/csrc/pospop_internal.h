@@ -100,6 +100,8 @@ struct SelectParams {
   uint64_t chunk0;              // staged form: chunks [chunk0, nstaged) of 16 rows are staged
   uint64_t nstaged;             //   in shared memory (the others are counted from registers)
   uint32_t sel_bytes;           // staged form: bitmap bytes copied per chunk
+  const uint8_t *sel_base;      // staged form: the bitmap rounded down to 16 bytes
+  int64_t sel_bit0;             // staged form: bit of sel_base where chunk 0's bits start
   int *status;                  // staged form: set to POSPOP_ETIMEDOUT if a wait expires
 };
 

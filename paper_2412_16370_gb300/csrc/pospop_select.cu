@@ -49,7 +49,7 @@ __global__ void __launch_bounds__(BS, MINB) select_kernel(SelectParams Q) {
 }
 
 // ---------------------------------------------------------------------------
-// Staged form (a 16-byte-aligned bitmap).  The selected
+// Staged form.  The selected
 // count does about half again the plain count's arithmetic per byte, so with
 // its loads in registers a warp issues the next group's loads late and DRAM
 // idles.  Here the copy engine keeps the bytes in flight instead: each warp
@@ -58,11 +58,12 @@ __global__ void __launch_bounds__(BS, MINB) select_kernel(SelectParams Q) {
 // bulk copies (cp.async.bulk) that complete one mbarrier phase.  Chunk c is
 // rows 16c .. 16c + 15; warps take chunks c = chunk0 + gw, + TW, ... below
 // Q.nstaged (chunks wholly inside the span: chunk 0 only when the span
-// starts on a 16-byte boundary), and warp 0 counts the remaining rows with
-// count_rows.  A chunk's selection bits start h bits (h = words before the
-// start in granule 0) before a multiple of 512 * CNT bits, so the copy takes
-// the 16-byte-aligned bytes around them (one 16-byte block more when h > 0)
-// and every chunk's bits sit at the same offset in the stage.
+// starts on a 16-byte boundary and the bitmap on a 16-byte boundary), and
+// warp 0 counts the remaining rows with count_rows.  Chunk c's selection
+// bits start at bit sel_bit0 + 512 * CNT * c of the bitmap's 16-byte-aligned
+// base, so the copy takes the 16-byte blocks around them (one block more
+// when they do not start on a block) and every chunk's bits sit at the same
+// offset in the stage.
 // ---------------------------------------------------------------------------
 template <int WLOG>
 __host__ __device__ constexpr uint32_t staged_stage_bytes() {
@@ -101,13 +102,14 @@ __global__ void __launch_bounds__(NW * 32, 1) select_staged_kernel(SelectParams 
   uint32_t cnt[4] = {0u, 0u, 0u, 0u};
 
   const uint32_t h = P.s.head >> WLOG;                // words before the start in granule 0
-  const uint32_t sel_off = (128u - (h & 127u)) & 127u;  // bit offset of a chunk's bits in its copy
+  // bit offset of a chunk's bits in its copy (512 * CNT is a multiple of 128)
+  const uint32_t sel_off = (uint32_t)((uint64_t)Q.sel_bit0 & 127u);
   auto fill = [&](int k, uint64_t c) {   // lane 0 only
     const uint32_t bar = smem_addr(bars + k);
     mbar_expect(bar, kBulkChunk + Q.sel_bytes);
     bulk_copy_tx(smem_addr(ring + k * kStage), s.A + c * kBulkChunk, kBulkChunk, bar);
-    const uint64_t first_bit = c * (512u * CNT) - h;
-    bulk_copy_tx(smem_addr(ring + k * kStage + kBulkChunk), Q.bits + (first_bit >> 7) * 16u,
+    const uint64_t first_bit = (uint64_t)((int64_t)(c * (512u * CNT)) + Q.sel_bit0);
+    bulk_copy_tx(smem_addr(ring + k * kStage + kBulkChunk), Q.sel_base + (first_bit >> 7) * 16u,
                  Q.sel_bytes, bar);
   };
   const uint64_t c0 = Q.chunk0 + gw;

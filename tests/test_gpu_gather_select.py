@@ -220,8 +220,8 @@ def test_masked_staged_form(gpu, orc, tune_override, w):
     """Selected counts large enough for the staged form (bulk copies into
     shared memory, at least two 16-row chunks per warp of the grid), with
     16-byte-aligned and word-aligned starts and ragged ends, for every ring
-    shape and the register form (tune entry `staged k`), against the oracle;
-    a bitmap that is 4- but not 16-byte aligned takes the register form."""
+    shape and the register form (tune entry `staged k`), against the oracle,
+    with bitmaps on and 4 bytes past a 16-byte boundary."""
     W = w // 8
     base_tune = pp.pospopcnt_tune_describe()
     keep = "\n".join(l for l in base_tune.splitlines() if not l.startswith("staged"))
