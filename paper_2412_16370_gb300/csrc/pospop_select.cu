@@ -78,8 +78,7 @@ constexpr int staged_smem() {
 template <int NW, int S, int WLOG>
 __global__ void __launch_bounds__(NW * 32, 1) select_staged_kernel(SelectParams Q) {
   constexpr uint32_t CNT = 16u >> WLOG;                // selection bits per granule
-  constexpr uint32_t kSel = 64u * CNT;                 // selection bytes per chunk
-  constexpr uint32_t kStage = staged_stage_bytes<WLOG>();
+  constexpr uint32_t kStage = staged_stage_bytes<WLOG>();  // 16-byte multiple
   extern __shared__ __align__(128) uint8_t smem[];
   __shared__ unsigned long long acc[64];
   pdl_enter();
@@ -140,8 +139,9 @@ __global__ void __launch_bounds__(NW * 32, 1) select_staged_kernel(SelectParams 
       v[r] = V4{{x.x, x.y, x.z, x.w}};
       const uint32_t bit = sel_off + (uint32_t)(r * 32 + lane) * CNT;
       const uint32_t sh = bit & 31u;
-      // a window straddles into the next word only when h is not a multiple
-      // of CNT; that word's bits then lie inside the copy
+      // a window straddles into the next word only when the chunk's bit
+      // offset is not a multiple of CNT; that word's bits then lie inside
+      // the copy
       const uint32_t w1 = (sh + CNT > 32u) ? sel[(bit >> 5) + 1] : 0u;
       apply_selection<WLOG>(v[r], __funnelshift_r(sel[bit >> 5], w1, sh));
     }
