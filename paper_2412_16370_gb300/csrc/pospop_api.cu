@@ -178,9 +178,8 @@ std::string format_tune(const DevCtx &ctx, const TuneTable &t) {
     cudaGetLastError();
     snprintf(prop.name, sizeof(prop.name), "unknown");
   }
-  snprintf(line, sizeof line, "# pospopcnt tune table: %s, %d SMs (%s)\n", prop.name, ctx.sms,
-           t.source);
-  s += line;
+  s += std::string("# pospopcnt tune table: ") + prop.name + ", " + std::to_string(ctx.sms) +
+       " SMs (" + t.source + ")\n";
   s += "# stream <class> <bs> <minb> <depth> <hint> <ctas_per_sm> <min_rows>\n";
   for (int c = 0; c < kClasses; c++) {
     const Variant &v = stream_variant(t.stream[c].variant);
@@ -402,14 +401,12 @@ static bool device_addressable(const void *p, int device, const void **devptr) {
 cudaError_t launch_kernel(const void *fn, dim3 grid, dim3 block, void **args, cudaStream_t stream,
                           bool pdl, size_t smem) {
   if (!pdl) return cudaLaunchKernel(fn, grid, block, args, smem, stream);
-  cudaLaunchConfig_t cfg;
-  memset(&cfg, 0, sizeof cfg);
+  cudaLaunchConfig_t cfg = {};
   cfg.gridDim = grid;
   cfg.blockDim = block;
   cfg.dynamicSmemBytes = smem;
   cfg.stream = stream;
-  cudaLaunchAttribute at[1];
-  memset(at, 0, sizeof at);
+  cudaLaunchAttribute at[1] = {};
   at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
   at[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = at;

@@ -120,7 +120,7 @@ struct Variant {
   int minb;     // __launch_bounds__ min blocks per SM
   int depth;    // 16 or 32 vectors per flush
   int hint;     // load variant
-  int smem;     // dynamic shared memory bytes per block
+  int smem = 0; // dynamic shared memory bytes per block
 };
 
 constexpr int kPlanThreads = 1024;
