@@ -183,3 +183,25 @@ def test_small_requests_overtake_large_ones(gpu, pool):
     small_lat = small_done - recs["t_submit_ns"][nb:].astype(np.int64)
     assert small_done.max() < big_done
     assert np.median(small_lat) < 0.25 * (big_done - t0)
+
+
+def test_every_width_in_one_mix(gpu, orc, pool):
+    """Requests of widths 1, 2, 4, 8, 16, 32 and 64 in the same batches."""
+    n = 700
+    widths = np.array([1, 2, 4, 8, 16, 32, 64], dtype=np.int32)
+    w = widths[np.arange(n) % len(widths)]
+    rng = np.random.default_rng(17)
+    nbytes = synth.log_uniform_sizes(n, 1, 2 * MIB, seed=18).astype(np.uint64)
+    offs = rng.integers(0, 64 * MIB, n).astype(np.uint64)
+    srv = pp.pospop_server_create(1 << 30, 256, 2)
+    try:
+        results = np.zeros((n, 64), dtype=np.uint64)
+        recs = pp.pospop_server_run_trace(srv, (np.arange(n) * 3000).astype(np.int64), w,
+                                          pool.data_ptr() + offs, nbytes, results)
+    finally:
+        pp.pospop_server_destroy(srv)
+    assert (recs["status"] == 0).all()
+    host = pool.cpu().numpy()
+    for k in range(n):
+        seg = host[int(offs[k]):int(offs[k]) + int(nbytes[k])]
+        assert np.array_equal(results[k, :w[k]], orc.bytes(int(w[k]), seg)), (k, int(w[k]))
