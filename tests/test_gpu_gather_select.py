@@ -58,7 +58,7 @@ def test_gather_matches_oracle(gpu, orc):
     for m, hi, seed in ((1, 1000, 1), (37, 5000, 2), (3000, 1 << 20, 3)):
         starts, lens = _regions(m, seed, span, hi)
         regions = [host[s:s + n] for s, n in zip(starts, lens)]
-        for w in (1, 8, 16, 32, 64, 128, 256):
+        for w in (1, 2, 4, 8, 16, 32, 64, 128, 256):
             assert np.array_equal(_gather_gpu(w, buf, starts, lens), orc.gather(w, regions)), (m, w)
 
 

@@ -169,6 +169,14 @@ def test_host_memory_paths(gpu, orc):
         got2 = np.zeros(w, dtype=np.uint64)
         pp.pospopcnt_host(w, got2, pinned)               # pinned: read in place
         assert np.array_equal(got2, exp), ("pinned", w)
+    # the other widths through both host paths
+    pinned = torch.from_numpy(host).pin_memory()
+    for w in (1, 2, 4, 128, 256):
+        exp = orc.bytes_mt(w, host, 8)
+        for src in (host, pinned):
+            got = np.zeros(w, dtype=np.uint64)
+            pp.pospopcnt_host(w, got, src)
+            assert np.array_equal(got, exp), w
     # Fig. 2 entry points on plain host arrays
     words = host[:2 * 1000003].view("<u2")
     got = np.zeros(16, dtype=np.uint64)
