@@ -225,9 +225,11 @@ def test_masked_staged_form(gpu, orc, tune_override, w):
     W = w // 8
     base_tune = pp.pospopcnt_tune_describe()
     keep = "\n".join(l for l in base_tune.splitlines() if not l.startswith("staged"))
+    # 48 MiB of words: at least two 16-row chunks per warp for every ring
+    # shape (the 16-warp ring needs 38 MiB)
     for extra, seed, pad in ((0, 1, 0), (3, 2, 0), ((1 << 20) // W + 1, 3, 0),
                              (5, 4, W), (0, 5, 16 - W)):
-        n = (24 << 20) // W + extra
+        n = (48 << 20) // W + extra
         words_h = synth.random_bytes(n * W, seed=seed * 10 + w)
         sel_h = synth.random_bytes(4 * ((n + 31) // 32), seed=seed * 10 + w + 1)
         words = _dev_bytes(words_h, gpu, pad)   # pad > 0: the start is inside a granule
