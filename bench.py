@@ -10,8 +10,8 @@ also carries:
 * roofline: the counting kernel's achieved GB/s per launch against the
   measured HBM peak, plus the DRAM traffic per launch from the committed
   ncu summary (null when the kernel source changed since it was taken);
-* read_roofline: the roofline read kernel (Section 5's "dummy" kernel) on the
-  same array;
+* read_roofline: the roofline read kernels (Section 5's "dummy" kernel,
+  direct loads and cp.async.bulk staging) on the same array;
 * e2e: the same metric through the host-memory entry point (pinned host
   input, every step's input crosses the CPU-GPU link, counts read back);
 * batched: the ragged one-hot batch (200000 uint8 arrays, log-uniform
@@ -20,6 +20,10 @@ also carries:
   the oracle's time;
 * short: microseconds per call for short unaligned arrays, one launch each,
   plain and graph-replayed;
+* serving: the continuous-batching server on Poisson request streams at
+  0.3 / 0.6 / 0.9 of the large-array rate, GB/s and p50/p99 latency;
+* masked: the WHERE-selected count on the 8 GiB array as 32-bit words;
+* gather: 100000 separate regions of the array into one counter array;
 * cpu_baseline: the CPU oracle on the host cores on a bounded sample;
 * sweep: every w at 1 GiB and 8 GiB over Bernoulli(0.01/0.5/0.99) and
   all-ones bits, each cell's counts checked;
