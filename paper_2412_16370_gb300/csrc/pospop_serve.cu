@@ -74,6 +74,8 @@ struct Batch {
 constexpr int kServeClasses = 4;
 constexpr size_t kClassBound[kServeClasses - 1] = {size_t(1) << 20, size_t(16) << 20,
                                                    size_t(128) << 20};
+constexpr uint32_t kFineItemRows = 8;             // rows of 512 B
+constexpr size_t kFineBelowBytes = 512ull << 20;  // in-flight bytes
 constexpr size_t kBatchCap = 1024;      // requests per batch (4 launches of kServeMax)
 constexpr uint64_t kMaxServeGrid = uint64_t(1) << 20;
 
@@ -124,12 +126,18 @@ void free_batch(Batch &b) {
 // Enqueue one batch of the requests in b.reqs on b.s (loop thread only):
 // one launch per kServeMax requests, then the batch event.  Requests are
 // ordered smallest first, so that small requests' work items come first.
-int launch_batch(pospop_server &srv, Batch &b, const BatchTune &bt) {
+int launch_batch(pospop_server &srv, Batch &b, const BatchTune &bt, size_t load_bytes) {
   std::stable_sort(b.reqs.begin(), b.reqs.end(),
                    [](const Request *x, const Request *y) { return x->nbytes < y->nbytes; });
   const int n = (int)b.reqs.size();
   b.seq = b.seq + 1 == 0 ? 1 : b.seq + 1;
-  const uint32_t ir = bt.item_rows;
+  // While the server is lightly loaded, the smallest class's work items
+  // shrink to kFineItemRows, so that a small request is spread over several
+  // warps instead of one (its latency is then one short item); under load
+  // the tuned item size stays, since the extra blocks would only delay the
+  // large requests behind them.
+  const uint32_t ir = (b.level == 0 && load_bytes < kFineBelowBytes)
+                          ? std::min(bt.item_rows, kFineItemRows) : bt.item_rows;
   const Variant &v = serve_variant(bt.variant);
   const uint64_t wpb = (uint64_t)v.bs / 32;
   static thread_local ServeParams P;   // about 8 KiB: not on the loop thread's stack
@@ -252,6 +260,7 @@ void serve_loop(pospop_server *srv) {
     }
     to_launch.clear();
     bool stop_now = false;
+    size_t load_bytes = 0;   // device bytes in flight, as the launches saw them
     {
       std::unique_lock<std::mutex> lk(srv->mu);
       const int64_t tnow = now_ns();
@@ -298,6 +307,7 @@ void serve_loop(pospop_server *srv) {
           progress = true;
         }
       }
+      load_bytes = srv->inflight_bytes;
       const bool busy = std::any_of(srv->batches.begin(), srv->batches.end(),
                                     [](const Batch &b) { return b.busy; });
       if (srv->stop && !busy && srv->admitted.empty() && srv->pending.empty()) stop_now = true;
@@ -318,7 +328,7 @@ void serve_loop(pospop_server *srv) {
       b.reqs = std::move(bl.second);
       const int64_t tl = now_ns();
       for (Request *r : b.reqs) r->rec.t_launch_ns = tl;
-      const int rc = launch_batch(*srv, b, bt);
+      const int rc = launch_batch(*srv, b, bt, load_bytes);
       if (rc != POSPOP_OK) {
         // nothing of this batch reached the device in a usable state:
         // fail its requests (wait for what was enqueued before reusing it)
