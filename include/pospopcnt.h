@@ -201,9 +201,12 @@ int pospopcnt_plan(int w, size_t nbytes, uint32_t plan[8]);
  * Tune table.  A device starts with the table in the file named by the
  * environment variable POSPOP_TUNE_FILE, else pospopcnt_tune.txt next to
  * the library, else built-in defaults.  pospopcnt_autotune times every launch
- * candidate for each size class on the current device (allocating a scratch
- * buffer of up to max_bytes), installs the fastest, and, if path is not
- * NULL, writes the table there.  pospopcnt_tune_load installs a table
+ * candidate (block shape, CSA flush depth, load variant, blocks per SM, rows
+ * per warp; for the batched call work-item rows and grab size) for each width
+ * group (w <= 8, 16, 32, >= 64) and, for the single-array count, each size
+ * class on the current device (allocating a scratch buffer of up to
+ * max_bytes), installs the fastest, and, if path is not NULL, writes the
+ * table there.  pospopcnt_tune_load installs a table
  * written earlier; pospopcnt_tune_describe writes the current table, in the
  * same text format, into buf.
  */

@@ -80,8 +80,10 @@ TuneTable default_tune() {
   TuneTable t;
   const int sv = find_variant(false, 512, 1, 16, 1);
   const uint32_t minrows[kClasses] = {2, 4, 8, 16, 16};
-  for (int c = 0; c < kClasses; c++) t.stream[c] = StreamTune{sv, 1, minrows[c]};
-  t.batch = BatchTune{find_variant(true, 256, 2, 16, 1), 2, 511, 1};
+  for (int g = 0; g < kWidthGroups; g++) {
+    for (int c = 0; c < kClasses; c++) t.stream[g][c] = StreamTune{sv, 1, minrows[c]};
+    t.batch[g] = BatchTune{find_variant(true, 256, 2, 16, 1), 2, 511, 1};
+  }
   t.roof = RoofTune{find_roof_variant(512, 1), 4};
   t.max_rows_per_warp = kMaxRowsPerWarp;
   t.regroup = 0;
@@ -92,8 +94,11 @@ TuneTable default_tune() {
 }
 
 // Text format, one entry per line ('#' starts a comment):
-//   stream <class> <bs> <minb> <depth> <hint> <ctas_per_sm> <min_rows>
-//   batch <bs> <minb> <depth> <hint> <ctas_per_sm> <item_rows> <grab>
+//   stream [<w>] <class> <bs> <minb> <depth> <hint> <ctas_per_sm> <min_rows>
+//   batch [<w>] <bs> <minb> <depth> <hint> <ctas_per_sm> <item_rows> <grab>
+//                                 (<w> in {8, 16, 32, 64} sets the entry of that
+//                                  width group: 8 stands for w <= 8, 64 for
+//                                  w >= 64; without it the entry is every group's)
 //   roofline <bs> <hint> <ctas_per_sm>
 //   split <max_rows_per_warp>     (1 .. 2^26; a single-array count is split into
 //                                  several launches so that no warp takes more)
@@ -105,6 +110,41 @@ TuneTable default_tune() {
 //                                  stage their input in shared memory by bulk copies,
 //                                  ring shape k: 1 = 8 warps x 3 stages, 2 = 12 x 2,
 //                                  3 = 16 x 1; 0 = loads into registers)
+// The integers after the line's keyword, at most max of them: their number,
+// or -1 for a token that is not an integer or one too many.
+static int read_ints(const std::string &line, long long *v, int max) {
+  const char *q = line.c_str();
+  while (*q == ' ' || *q == '\t') q++;
+  while (*q && *q != ' ' && *q != '\t') q++;   // the keyword
+  int n = 0;
+  while (true) {
+    while (*q == ' ' || *q == '\t' || *q == '\r') q++;
+    if (!*q) return n;
+    if (n == max) return -1;
+    char *end = nullptr;
+    v[n] = strtoll(q, &end, 10);
+    if (end == q) return -1;
+    n++;
+    q = end;
+  }
+}
+
+// Width groups named by an optional leading <w>: [first, last) of the groups.
+static bool tune_groups(long long w, bool given, int *first, int *last) {
+  if (!given) {
+    *first = 0;
+    *last = kWidthGroups;
+    return true;
+  }
+  for (int g = 0; g < kWidthGroups; g++)
+    if (w == kGroupWidth[g]) {
+      *first = g;
+      *last = g + 1;
+      return true;
+    }
+  return false;
+}
+
 int parse_tune(const char *text, TuneTable *out) {
   TuneTable t = default_tune();
   std::string s(text);
@@ -120,24 +160,25 @@ int parse_tune(const char *text, TuneTable *out) {
     if (hash != std::string::npos) line.resize(hash);
     char kind[16] = {0};
     if (sscanf(line.c_str(), "%15s", kind) != 1) continue;
-    if (strcmp(kind, "stream") == 0) {
-      int c, bs, minb, d, h, cps;
-      unsigned mr;
-      if (sscanf(line.c_str(), "%*s %d %d %d %d %d %d %u", &c, &bs, &minb, &d, &h, &cps, &mr) != 7)
-        return POSPOP_EINVAL;
-      const int v = find_variant(false, bs, minb, d, h);
-      if (c < 0 || c >= kClasses || v < 0 || cps < 1 || mr < 1) return POSPOP_EINVAL;
-      t.stream[c] = StreamTune{v, cps, mr};
-    } else if (strcmp(kind, "batch") == 0) {
-      int bs, minb, d, h, cps;
-      unsigned ir, grab;
-      if (sscanf(line.c_str(), "%*s %d %d %d %d %d %u %u", &bs, &minb, &d, &h, &cps, &ir, &grab) !=
-          7)
-        return POSPOP_EINVAL;
-      const int v = find_variant(true, bs, minb, d, h);
-      if (v < 0 || cps < 1 || ir < 1 || ir > (1u << 20) || grab < 1 || grab > 64)
-        return POSPOP_EINVAL;
-      t.batch = BatchTune{v, cps, ir, grab};
+    if (strcmp(kind, "stream") == 0 || strcmp(kind, "batch") == 0) {
+      long long a[8];
+      const int n = read_ints(line, a, 8);
+      int g0 = 0, g1 = 0;
+      if ((n != 7 && n != 8) || !tune_groups(a[0], n == 8, &g0, &g1)) return POSPOP_EINVAL;
+      const long long *f = a + (n - 7);   // the seven fields after the optional <w>
+      for (int i = 0; i < 7; i++)
+        if (f[i] < 0 || f[i] > (1ll << 30)) return POSPOP_EINVAL;
+      if (kind[0] == 's') {
+        const int c = (int)f[0], v = find_variant(false, (int)f[1], (int)f[2], (int)f[3], (int)f[4]);
+        if (c >= kClasses || v < 0 || f[5] < 1 || f[6] < 1) return POSPOP_EINVAL;
+        for (int g = g0; g < g1; g++) t.stream[g][c] = StreamTune{v, (int)f[5], (uint32_t)f[6]};
+      } else {
+        const int v = find_variant(true, (int)f[0], (int)f[1], (int)f[2], (int)f[3]);
+        if (v < 0 || f[4] < 1 || f[5] < 1 || f[5] > (1 << 20) || f[6] < 1 || f[6] > 64)
+          return POSPOP_EINVAL;
+        for (int g = g0; g < g1; g++)
+          t.batch[g] = BatchTune{v, (int)f[4], (uint32_t)f[5], (uint32_t)f[6]};
+      }
     } else if (strcmp(kind, "short") == 0) {
       unsigned rg;
       if (sscanf(line.c_str(), "%*s %u", &rg) != 1 || rg > 1) return POSPOP_EINVAL;
@@ -180,19 +221,43 @@ std::string format_tune(const DevCtx &ctx, const TuneTable &t) {
   }
   s += std::string("# pospopcnt tune table: ") + prop.name + ", " + std::to_string(ctx.sms) +
        " SMs (" + t.source + ")\n";
-  s += "# stream <class> <bs> <minb> <depth> <hint> <ctas_per_sm> <min_rows>\n";
+  // an entry that is the same for every width group is written once,
+  // without <w>
+  s += "# stream [<w>] <class> <bs> <minb> <depth> <hint> <ctas_per_sm> <min_rows>\n";
   for (int c = 0; c < kClasses; c++) {
-    const Variant &v = stream_variant(t.stream[c].variant);
-    snprintf(line, sizeof line, "stream %d %d %d %d %d %d %u\n", c, v.bs, v.minb, v.depth, v.hint,
-             t.stream[c].ctas_per_sm, t.stream[c].min_rows);
-    s += line;
+    bool same = true;
+    for (int g = 1; g < kWidthGroups; g++) {
+      const StreamTune &a = t.stream[0][c], &b = t.stream[g][c];
+      same = same && a.variant == b.variant && a.ctas_per_sm == b.ctas_per_sm &&
+             a.min_rows == b.min_rows;
+    }
+    for (int g = 0; g < (same ? 1 : kWidthGroups); g++) {
+      const StreamTune &e = t.stream[g][c];
+      const Variant &v = stream_variant(e.variant);
+      char wfield[16] = "";
+      if (!same) snprintf(wfield, sizeof wfield, "%d ", kGroupWidth[g]);
+      snprintf(line, sizeof line, "stream %s%d %d %d %d %d %d %u\n", wfield, c, v.bs, v.minb,
+               v.depth, v.hint, e.ctas_per_sm, e.min_rows);
+      s += line;
+    }
   }
   {
-    const Variant &v = batch_variant(t.batch.variant);
-    s += "# batch <bs> <minb> <depth> <hint> <ctas_per_sm> <item_rows> <grab>\n";
-    snprintf(line, sizeof line, "batch %d %d %d %d %d %u %u\n", v.bs, v.minb, v.depth, v.hint,
-             t.batch.ctas_per_sm, t.batch.item_rows, t.batch.grab);
-    s += line;
+    s += "# batch [<w>] <bs> <minb> <depth> <hint> <ctas_per_sm> <item_rows> <grab>\n";
+    bool same = true;
+    for (int g = 1; g < kWidthGroups; g++) {
+      const BatchTune &a = t.batch[0], &b = t.batch[g];
+      same = same && a.variant == b.variant && a.ctas_per_sm == b.ctas_per_sm &&
+             a.item_rows == b.item_rows && a.grab == b.grab;
+    }
+    for (int g = 0; g < (same ? 1 : kWidthGroups); g++) {
+      const BatchTune &e = t.batch[g];
+      const Variant &v = batch_variant(e.variant);
+      char wfield[16] = "";
+      if (!same) snprintf(wfield, sizeof wfield, "%d ", kGroupWidth[g]);
+      snprintf(line, sizeof line, "batch %s%d %d %d %d %d %u %u\n", wfield, v.bs, v.minb, v.depth,
+               v.hint, e.ctas_per_sm, e.item_rows, e.grab);
+      s += line;
+    }
   }
   snprintf(line, sizeof line, "# short <0 transpose | 1 per-lane regroup> (w = 8, <= 3 rows)\nshort %u\n",
            t.regroup);
@@ -417,10 +482,10 @@ cudaError_t launch_kernel(const void *fn, dim3 grid, dim3 block, void **args, cu
 // ---------------------------------------------------------------------------
 // Single-array launches.
 // ---------------------------------------------------------------------------
-StreamPlan plan_stream(const DevCtx &ctx, const TuneTable &t, uint64_t rows) {
+StreamPlan plan_stream(const DevCtx &ctx, const TuneTable &t, int w, uint64_t rows) {
   StreamPlan p;
   p.cls = size_class(rows);
-  const StreamTune &st = t.stream[p.cls];
+  const StreamTune &st = t.stream[width_group(w)][p.cls];
   p.variant = st.variant;
   const Variant &v = stream_variant(st.variant);
   // ctas_per_sm above the occupancy limit is allowed: the grid then runs in
@@ -458,7 +523,7 @@ int launch_stream_with(const DevCtx &ctx, const TuneTable &t, int w, unsigned lo
   P.rot = (8u * P.s.head) & (uint32_t)(w - 1);
   P.regroup = t.regroup;
   const uint64_t R = (P.s.G + 31) >> 5;
-  const StreamPlan pl = plan_stream(ctx, t, R);
+  const StreamPlan pl = plan_stream(ctx, t, w, R);
   const Variant *vp = &stream_variant(pl.variant);
   if (w == 256) {   // the two-parity kernel with the planned block shape
     const int pick = pick_shape(stream256_variant_count(), stream256_variant, 1, *vp);
@@ -609,6 +674,7 @@ int launch_batch_with(DevCtx &ctx, const TuneTable &t, int w, unsigned long long
     cudaGetLastError();
     return POSPOP_ECUDA;
   }
+  const BatchTune &bt = t.batch[width_group(w)];
   PlanParams pp;
   pp.gptrs = nullptr;
   pp.glens = nullptr;
@@ -619,7 +685,7 @@ int launch_batch_with(DevCtx &ctx, const TuneTable &t, int w, unsigned long long
   pp.block_sum = ws->block_sum;
   pp.next = ws->next;
   pp.status = ws->status;
-  pp.item_rows = t.batch.item_rows;
+  pp.item_rows = bt.item_rows;
   pp.nblocks = (uint32_t)((m + kPlanChunk - 1) / kPlanChunk);
   int rc = launch_plan(plan_items_fn(), pp, stream, t.pdl != 0);
   if (rc != POSPOP_OK) return rc;
@@ -635,18 +701,18 @@ int launch_batch_with(DevCtx &ctx, const TuneTable &t, int w, unsigned long long
   bp.item_start = ws->item_start;
   bp.next = ws->next;
   bp.status = ws->status;
-  bp.item_rows = t.batch.item_rows;
-  bp.grab = t.batch.grab;
+  bp.item_rows = bt.item_rows;
+  bp.grab = bt.grab;
   bp.regroup = t.regroup;
-  const Variant *vp = &batch_variant(t.batch.variant);
+  const Variant *vp = &batch_variant(bt.variant);
   if (w == 256) {   // the two-parity kernel with the tuned block shape
     const int pick = pick_shape(batch256_variant_count(), batch256_variant, 1, *vp);
     if (pick < 0) return POSPOP_EINVAL;
     vp = &batch256_variant(pick);
   }
   const Variant &v = *vp;
-  int cps = t.batch.ctas_per_sm < ctx.occ_batch[t.batch.variant] ? t.batch.ctas_per_sm
-                                                                 : ctx.occ_batch[t.batch.variant];
+  int cps = bt.ctas_per_sm < ctx.occ_batch[bt.variant] ? bt.ctas_per_sm
+                                                                 : ctx.occ_batch[bt.variant];
   if (cps < 1) cps = 1;
   void *args[] = {&bp};
   if (launch_kernel(v.fn, dim3((unsigned)(ctx.sms * cps)), dim3(v.bs), args, stream,
@@ -674,6 +740,7 @@ static int launch_gather_with(DevCtx &ctx, const TuneTable &t, int w, unsigned l
     cudaGetLastError();
     return POSPOP_ECUDA;
   }
+  const BatchTune &bt = t.batch[width_group(w)];
   PlanParams pp;
   memset(&pp, 0, sizeof pp);
   pp.gptrs = ptrs;
@@ -683,7 +750,7 @@ static int launch_gather_with(DevCtx &ctx, const TuneTable &t, int w, unsigned l
   pp.block_sum = ws->block_sum;
   pp.next = ws->next;
   pp.status = ws->status;
-  pp.item_rows = t.batch.item_rows;
+  pp.item_rows = bt.item_rows;
   pp.nblocks = (uint32_t)((n + kPlanChunk - 1) / kPlanChunk);
   const int prc = launch_plan(plan_items_gather_fn(), pp, stream, t.pdl != 0);
   if (prc != POSPOP_OK) return prc;
@@ -697,17 +764,17 @@ static int launch_gather_with(DevCtx &ctx, const TuneTable &t, int w, unsigned l
   bp.item_start = ws->item_start;
   bp.next = ws->next;
   bp.status = ws->status;
-  bp.item_rows = t.batch.item_rows;
-  bp.grab = t.batch.grab;
+  bp.item_rows = bt.item_rows;
+  bp.grab = bt.grab;
   bp.regroup = t.regroup;
-  const Variant *vp = &gather_variant(t.batch.variant);
+  const Variant *vp = &gather_variant(bt.variant);
   if (w == 256) {   // the two-parity kernel with the tuned block shape
     const int pick = pick_shape(gather256_variant_count(), gather256_variant, 1, *vp);
     if (pick < 0) return POSPOP_EINVAL;
     vp = &gather256_variant(pick);
   }
   const Variant &v = *vp;
-  int cps = std::min(t.batch.ctas_per_sm, ctx.occ_batch[t.batch.variant]);
+  int cps = std::min(bt.ctas_per_sm, ctx.occ_batch[bt.variant]);
   if (cps < 1) cps = 1;
   void *bargs[] = {&bp};
   if (launch_kernel(v.fn, dim3((unsigned)(ctx.sms * cps)), dim3(v.bs), bargs, stream,
@@ -805,9 +872,9 @@ static int launch_select_with(DevCtx &ctx, const TuneTable &t, int w,
   // the selection kernel is ALU-heavier than the plain count and runs best
   // in a single wave (measured on GB300): cap the blocks per SM at occupancy
   TuneTable ts = t;
-  StreamTune &st = ts.stream[size_class(R)];
+  StreamTune &st = ts.stream[width_group(w)][size_class(R)];
   if (st.ctas_per_sm > ctx.occ_stream[st.variant]) st.ctas_per_sm = ctx.occ_stream[st.variant];
-  const StreamPlan pl = plan_stream(ctx, ts, R);
+  const StreamPlan pl = plan_stream(ctx, ts, w, R);
   // the selection kernels come in the tune table's block shapes (flush depth
   // 16), four word sizes each; take the planned block shape
   const int shape = pick_shape(select_variant_count(), select_variant, 4, stream_variant(pl.variant));
@@ -1161,7 +1228,7 @@ int pospopcnt_plan(int w, size_t nbytes, uint32_t plan[8]) {
   }
   const uint64_t G = (nbytes + 15) / 16;
   const uint64_t R = (G + 31) / 32;
-  const StreamPlan p = plan_stream(*c, t, R);
+  const StreamPlan p = plan_stream(*c, t, w, R);
   const Variant &v = stream_variant(p.variant);
   plan[0] = p.grid;
   plan[1] = p.block;

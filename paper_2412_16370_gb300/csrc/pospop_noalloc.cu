@@ -98,7 +98,7 @@ extern "C" int pospopcnt_batch_noalloc(int w, uint64_t *counts, const void *base
   uint32_t regroup;
   {
     std::lock_guard<std::mutex> g(c->mu);
-    bt = c->tune.batch;
+    bt = c->tune.batch[width_group(w)];
     regroup = c->tune.regroup;
   }
   cudaStream_t s = static_cast<cudaStream_t>(stream);

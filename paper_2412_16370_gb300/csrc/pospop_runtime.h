@@ -18,6 +18,7 @@ namespace pospop {
 
 constexpr int kMaxDevices = 64;
 constexpr int kClasses = 5;          // single-array size classes (by rows of 512 B)
+constexpr int kWidthGroups = 4;      // tune-table width groups: w <= 8, 16, 32, >= 64
 constexpr int kStageBufs = 2;
 constexpr size_t kStageChunk = size_t(64) << 20;   // host-path staging chunk (64 MiB)
 constexpr uint64_t kMaxRowsPerWarp = uint64_t(1) << 26;  // u32 counters: 32 * 2^26 < 2^32
@@ -37,9 +38,15 @@ struct RoofTune {
   int variant;
   int ctas_per_sm;
 };
+// Width group of w (1..256, a power of two): the tune table keeps one
+// single-array entry per (width group, size class) and one batch entry per
+// width group.
+constexpr int width_group(int w) { return w <= 8 ? 0 : w == 16 ? 1 : w == 32 ? 2 : 3; }
+constexpr int kGroupWidth[kWidthGroups] = {8, 16, 32, 64};   // the width each group is tuned at
+
 struct TuneTable {
-  StreamTune stream[kClasses];
-  BatchTune batch;
+  StreamTune stream[kWidthGroups][kClasses];
+  BatchTune batch[kWidthGroups];
   RoofTune roof;
   uint64_t max_rows_per_warp;   // single-array launch split (<= kMaxRowsPerWarp)
   uint32_t regroup;             // w = 8 short sequences: 1 = per-lane bit regroup, 0 = transpose
@@ -106,7 +113,7 @@ struct StreamPlan {
   int cls;
   int cps;
 };
-StreamPlan plan_stream(const DevCtx &ctx, const TuneTable &t, uint64_t rows);
+StreamPlan plan_stream(const DevCtx &ctx, const TuneTable &t, int w, uint64_t rows);
 
 // Enqueue the single-array count of [bytes, bytes + nbytes) (device
 // addressable) into counts (device, w entries) on `stream`.

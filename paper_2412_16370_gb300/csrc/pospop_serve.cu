@@ -74,6 +74,8 @@ struct Batch {
 constexpr int kServeClasses = 4;
 constexpr size_t kClassBound[kServeClasses - 1] = {size_t(1) << 20, size_t(16) << 20,
                                                    size_t(128) << 20};
+// batches mix widths 8..64: they take the w = 32 batch entry of the tune table
+constexpr int kServeWidthGroup = width_group(32);
 constexpr uint32_t kFineItemRows = 8;             // rows of 512 B
 constexpr size_t kFineBelowBytes = 512ull << 20;  // in-flight bytes
 constexpr size_t kBatchCap = 1024;      // requests per batch (4 launches of kServeMax)
@@ -321,7 +323,7 @@ void serve_loop(pospop_server *srv) {
     BatchTune bt{};
     if (!to_launch.empty()) {
       std::lock_guard<std::mutex> g(srv->ctx->mu);
-      bt = srv->ctx->tune.batch;
+      bt = srv->ctx->tune.batch[kServeWidthGroup];
     }
     for (auto &bl : to_launch) {
       Batch &b = *bl.first;

@@ -1,6 +1,7 @@
 // pospop_tune.cu -- the autotuner behind pospopcnt_autotune: times every
-// launch candidate of the single-array kernel per size class, of the
-// batched kernel on a ragged batch, and of the roofline read kernel, and
+// launch candidate of the single-array kernel per width group and size
+// class, of the batched kernel on a ragged batch per width group, and of the
+// roofline read kernel, and
 // installs the fastest of each (a candidate must beat the current entry by
 // 1%, so measurement noise does not flip near-equal choices).  Timing is with CUDA events on the tuning
 // stream; counting kernels do not depend on the data values, so the scratch
@@ -101,43 +102,48 @@ extern "C" int pospopcnt_autotune(size_t max_bytes, const char *path) {
   }
   TuneTable cand = best;
 
-  // --- single-array kernel, per size class -----------------------------------
+  // --- single-array kernel, per width group and size class ------------------
   const size_t rep_bytes[kClasses] = {size_t(16) << 10, size_t(512) << 10, size_t(16) << 20,
                                       size_t(512) << 20, max_bytes};
   const uint32_t minrows_set[] = {1, 2, 4, 8, 16, 32, 64, 128};
-  for (int cls = 0; cls < kClasses; cls++) {
-    const size_t nbytes = std::min(rep_bytes[cls], max_bytes);
-    const uint64_t rows = (nbytes / 16 + 31) / 32;
-    if (size_class(rows) != cls) {   // scratch too small for this class: inherit
-      if (cls > 0) best.stream[cls] = best.stream[cls - 1];
-      continue;
-    }
-    // the incumbent is timed first; a candidate must beat it by 1% (ties and
-    // noise keep the current entry)
-    double best_ms = tm.time([&] { return launch_stream_with(*c, best, 16, counts, buf, nbytes, tm.s); });
-    if (best_ms <= 0) best_ms = 1e30;
-    for (int v = 0; v < stream_variant_count(); v++) {
-      for (int cps = 1; cps <= std::max(4, c->occ_stream[v]); cps++) {
-        unsigned last_grid = 0;
-        for (uint32_t mr : minrows_set) {
-          cand = best;
-          cand.stream[cls] = StreamTune{v, cps, mr};
-          const StreamPlan pl = plan_stream(*c, cand, rows);
-          if (pl.grid == last_grid) continue;   // same launch as the previous min_rows
-          last_grid = pl.grid;
-          const double ms = tm.time([&] {
-            return launch_stream_with(*c, cand, 16, counts, buf, nbytes, tm.s);
-          });
-          if (ms > 0 && ms < 0.99 * best_ms) {
-            best_ms = ms;
-            best.stream[cls] = cand.stream[cls];
+  for (int g = 0; g < kWidthGroups; g++) {
+    const int w = kGroupWidth[g];
+    for (int cls = 0; cls < kClasses; cls++) {
+      const size_t nbytes = std::min(rep_bytes[cls], max_bytes);
+      const uint64_t rows = (nbytes / 16 + 31) / 32;
+      if (size_class(rows) != cls) {   // scratch too small for this class: inherit
+        if (cls > 0) best.stream[g][cls] = best.stream[g][cls - 1];
+        continue;
+      }
+      // the incumbent is timed first; a candidate must beat it by 1% (ties
+      // and noise keep the current entry)
+      double best_ms =
+          tm.time([&] { return launch_stream_with(*c, best, w, counts, buf, nbytes, tm.s); });
+      if (best_ms <= 0) best_ms = 1e30;
+      for (int v = 0; v < stream_variant_count(); v++) {
+        for (int cps = 1; cps <= std::max(4, c->occ_stream[v]); cps++) {
+          unsigned last_grid = 0;
+          for (uint32_t mr : minrows_set) {
+            cand = best;
+            cand.stream[g][cls] = StreamTune{v, cps, mr};
+            const StreamPlan pl = plan_stream(*c, cand, w, rows);
+            if (pl.grid == last_grid) continue;   // same launch as the previous min_rows
+            last_grid = pl.grid;
+            const double ms = tm.time([&] {
+              return launch_stream_with(*c, cand, w, counts, buf, nbytes, tm.s);
+            });
+            if (ms > 0 && ms < 0.99 * best_ms) {
+              best_ms = ms;
+              best.stream[g][cls] = cand.stream[g][cls];
+            }
           }
         }
       }
     }
   }
 
-  // --- batched kernel on a ragged batch (log-uniform sizes, 1 B .. 4 MiB) ----
+  // --- batched kernel on a ragged batch (log-uniform sizes, 1 B .. 4 MiB),
+  //     per width group --------------------------------------------------------
   {
     Rng rng{0x9E3779B97F4A7C15ull};
     std::vector<uint64_t> off(1, 0);
@@ -151,25 +157,28 @@ extern "C" int pospopcnt_autotune(size_t max_bytes, const char *path) {
     if (m > 0 && cudaMalloc(&doff, off.size() * sizeof(uint64_t)) == cudaSuccess &&
         cudaMemcpy(doff, off.data(), off.size() * sizeof(uint64_t), cudaMemcpyHostToDevice) ==
             cudaSuccess) {
-      double best_ms =
-          tm.time([&] { return launch_batch_with(*c, best, 8, counts, buf + 3, doff, m, tm.s); });
-      if (best_ms <= 0) best_ms = 1e30;
       const uint32_t item_rows_set[] = {63, 127, 255, 511, 1023, 2047};
       const uint32_t grab_set[] = {1, 2, 4};
-      for (int v = 0; v < batch_variant_count(); v++)
-        for (int cps = 1; cps <= std::min(c->occ_batch[v], 4); cps++)
-          for (uint32_t ir : item_rows_set)
-            for (uint32_t gr : grab_set) {
-              cand = best;
-              cand.batch = BatchTune{v, cps, ir, gr};
-              const double ms = tm.time([&] {
-                return launch_batch_with(*c, cand, 8, counts, buf + 3, doff, m, tm.s);
-              });
-              if (ms > 0 && ms < 0.99 * best_ms) {
-                best_ms = ms;
-                best.batch = cand.batch;
+      for (int g = 0; g < kWidthGroups; g++) {
+        const int w = kGroupWidth[g];
+        double best_ms = tm.time(
+            [&] { return launch_batch_with(*c, best, w, counts, buf + 3, doff, m, tm.s); });
+        if (best_ms <= 0) best_ms = 1e30;
+        for (int v = 0; v < batch_variant_count(); v++)
+          for (int cps = 1; cps <= std::min(c->occ_batch[v], 4); cps++)
+            for (uint32_t ir : item_rows_set)
+              for (uint32_t gr : grab_set) {
+                cand = best;
+                cand.batch[g] = BatchTune{v, cps, ir, gr};
+                const double ms = tm.time([&] {
+                  return launch_batch_with(*c, cand, w, counts, buf + 3, doff, m, tm.s);
+                });
+                if (ms > 0 && ms < 0.99 * best_ms) {
+                  best_ms = ms;
+                  best.batch[g] = cand.batch[g];
+                }
               }
-            }
+      }
     }
     cudaGetLastError();
   }
