@@ -215,6 +215,15 @@ int pospopcnt_tune_load(const char *path);
 int pospopcnt_tune_describe(char *buf, size_t len);
 
 /*
+ * Check a tune file without a GPU: parse `path` as pospopcnt_tune_load
+ * would (same format and limits) and install nothing.  Needs no device and
+ * makes no CUDA call.  Returns POSPOP_OK, or POSPOP_EINVAL with *bad_line
+ * (if not NULL) set to the 1-based number of the first line that does not
+ * parse, 0 when the file cannot be read.
+ */
+int pospopcnt_tune_check(const char *path, int *bad_line);
+
+/*
  * CUDA graph of one batched call (planning + counting), captured on
  * `stream` and replayed with pospopcnt_graph_launch.  The graph keeps the
  * pointers and m it was made with.  *graph receives an opaque handle.

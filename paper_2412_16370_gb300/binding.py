@@ -60,6 +60,7 @@ _SIGNATURES = {
     "pospopcnt_autotune": ([_sz, ctypes.c_char_p], _int),
     "pospopcnt_tune_load": ([ctypes.c_char_p], _int),
     "pospopcnt_tune_describe": ([ctypes.c_char_p, _sz], _int),
+    "pospopcnt_tune_check": ([ctypes.c_char_p, ctypes.POINTER(_int)], _int),
     "pospopcnt_batch_graph_create": ([_int, _vp, _vp, _vp, _sz, _vp, ctypes.POINTER(_vp)], _int),
     "pospopcnt_graph_launch": ([_vp, _vp], _int),
     "pospopcnt_graph_destroy": ([_vp], _int),
@@ -250,6 +251,16 @@ def pospopcnt_autotune(max_bytes: int = 0, path: str | None = None):
 
 def pospopcnt_tune_load(path: str):
     return _check(lib().pospopcnt_tune_load(path.encode()))
+
+
+def pospopcnt_tune_check(path: str) -> int:
+    """0 if the tune file parses, else the 1-based number of its first bad
+    line (no GPU needed); raises if the file cannot be read."""
+    line = _int(0)
+    rc = lib().pospopcnt_tune_check(path.encode(), ctypes.byref(line))
+    if rc != POSPOP_OK and line.value == 0:
+        raise PospopError(rc, f"cannot read {path}")
+    return line.value
 
 
 def pospopcnt_tune_describe() -> str:

@@ -145,7 +145,7 @@ static bool tune_groups(long long w, bool given, int *first, int *last) {
   return false;
 }
 
-int parse_tune(const char *text, TuneTable *out) {
+int parse_tune(const char *text, TuneTable *out, int *bad_line) {
   TuneTable t = default_tune();
   std::string s(text);
   size_t pos = 0;
@@ -156,6 +156,7 @@ int parse_tune(const char *text, TuneTable *out) {
     std::string line = s.substr(pos, nl - pos);
     pos = nl + 1;
     lineno++;
+    if (bad_line) *bad_line = lineno;   // the line being read, if it fails
     const size_t hash = line.find('#');
     if (hash != std::string::npos) line.resize(hash);
     char kind[16] = {0};
@@ -207,6 +208,7 @@ int parse_tune(const char *text, TuneTable *out) {
       return POSPOP_EINVAL;
     }
   }
+  if (bad_line) *bad_line = 0;
   *out = t;
   return POSPOP_OK;
 }
@@ -1239,6 +1241,18 @@ int pospopcnt_plan(int w, size_t nbytes, uint32_t plan[8]) {
   plan[6] = (uint32_t)p.launches;
   plan[7] = (uint32_t)p.cps;
   return POSPOP_OK;
+}
+
+int pospopcnt_tune_check(const char *path, int *bad_line) {
+  if (bad_line) *bad_line = 0;
+  if (!path) return POSPOP_EINVAL;
+  std::string text;
+  if (!read_file(path, &text)) return POSPOP_EINVAL;
+  TuneTable t;
+  int line = 0;
+  const int rc = parse_tune(text.c_str(), &t, &line);
+  if (bad_line) *bad_line = rc == POSPOP_OK ? 0 : line;
+  return rc;
 }
 
 int pospopcnt_tune_load(const char *path) {

@@ -99,7 +99,9 @@ DevCtx *ctx_for_device(int device, int *rc);
 int size_class(uint64_t rows);
 TuneTable default_tune();
 int find_variant(bool batch, int bs, int minb, int depth, int hint);
-int parse_tune(const char *text, TuneTable *out);
+// Parses a tune table (text format in pospop_api.cu); on failure returns
+// POSPOP_EINVAL and, if bad_line is not null, the 1-based failing line.
+int parse_tune(const char *text, TuneTable *out, int *bad_line = nullptr);
 std::string format_tune(const DevCtx &ctx, const TuneTable &t);
 
 // Launch plan of one single-array count.

@@ -1,0 +1,74 @@
+"""The tune-file parser, checked on the host (no GPU): the shipped table,
+per-width entries, and the line numbers of malformed lines."""
+import os
+import shutil
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SHIPPED = os.path.join(ROOT, "paper_2412_16370_gb300", "pospopcnt_tune.txt")
+
+
+@pytest.fixture(scope="module")
+def pp():
+    if shutil.which("nvcc") is None and not os.path.exists("/usr/local/cuda/bin/nvcc"):
+        pytest.skip("nvcc not available")
+    from paper_2412_16370_gb300 import build, binding
+    build.build()
+    return binding
+
+
+def _check(pp, tmp_path, text):
+    f = tmp_path / "t.txt"
+    f.write_text(text)
+    return pp.pospopcnt_tune_check(str(f))
+
+
+def test_shipped_table_parses(pp):
+    assert pp.pospopcnt_tune_check(SHIPPED) == 0
+
+
+def test_empty_and_comment_only_files_parse(pp, tmp_path):
+    assert _check(pp, tmp_path, "") == 0
+    assert _check(pp, tmp_path, "# nothing here\n\n   \n") == 0
+
+
+def test_per_width_and_every_width_entries(pp, tmp_path):
+    lines = ["stream 0 256 2 16 1 1 2"]                 # every width
+    for w in (8, 16, 32, 64):
+        lines.append(f"stream {w} 1 128 4 32 0 3 1")    # one width group
+        lines.append(f"batch {w} 512 1 16 1 1 127 1")
+    lines += ["batch 256 2 16 0 2 63 4", "pdl 0", "staged 0", "short 1", "split 1024",
+              "roofline 256 1 18", "stream 4 512 1 16 0 3 1   # trailing comment"]
+    assert _check(pp, tmp_path, "\n".join(lines) + "\n") == 0
+    assert _check(pp, tmp_path, "\r\n".join(lines) + "\r\n") == 0   # CRLF line ends
+
+
+@pytest.mark.parametrize("bad", [
+    "stream 24 2 512 1 16 1 1 8",        # 24 is not a width group
+    "stream 128 2 512 1 16 1 1 8",       # groups are named by 8, 16, 32, 64
+    "stream 5 512 1 16 1 1 8",           # size class out of range
+    "stream 8 2 512 1 16 1 1",           # seven fields: class 8 out of range
+    "stream 0 512 1 16 1 1",             # too few fields
+    "stream 8 2 512 1 16 1 1 8 9",       # too many
+    "stream 0 500 1 16 1 1 8",           # no such block shape
+    "stream 0 512 1 24 1 1 8",           # no such flush depth
+    "stream 0 512 1 16 1 0 8",           # ctas per SM below 1
+    "stream 0 512 1 16 1 1 0",           # rows per warp below 1
+    "stream 0 512 1 16 1 1 x",           # not an integer
+    "stream 0 512 1 16 1 -1 8",          # negative
+    "batch 512 1 16 1 1 0 1",            # item rows below 1
+    "batch 512 1 16 1 1 2097152 1",      # item rows above 2^20
+    "batch 512 1 16 1 1 127 65",         # grab above 64
+    "batch 64 512 1 16 1 1 127 1 1",     # too many fields
+    "pdl 2", "short 2", "split 0", "split 67108865", "staged 99",
+    "roofline 300 1 4", "roofline 256 1", "bogus 1",
+])
+def test_malformed_line_is_reported_with_its_number(pp, tmp_path, bad):
+    text = "# header\nstream 0 256 2 16 1 1 2\n\n" + bad + "\npdl 1\n"
+    assert _check(pp, tmp_path, text) == 4
+
+
+def test_unreadable_file_raises(pp, tmp_path):
+    with pytest.raises(pp.PospopError):
+        pp.pospopcnt_tune_check(str(tmp_path / "missing.txt"))
