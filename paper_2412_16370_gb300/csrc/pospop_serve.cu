@@ -76,7 +76,7 @@ constexpr size_t kClassBound[kServeClasses - 1] = {size_t(1) << 20, size_t(16) <
                                                    size_t(128) << 20};
 // batches mix widths 8..64: they take the w = 32 batch entry of the tune table
 constexpr int kServeWidthGroup = width_group(32);
-constexpr uint32_t kFineItemRows = 8;             // rows of 512 B
+constexpr uint32_t kFineItemRows[2] = {8, 32};    // rows of 512 B, classes 0 and 1
 constexpr size_t kFineBelowBytes = 512ull << 20;  // in-flight bytes
 constexpr size_t kBatchCap = 1024;      // requests per batch (4 launches of kServeMax)
 constexpr uint64_t kMaxServeGrid = uint64_t(1) << 20;
@@ -133,13 +133,13 @@ int launch_batch(pospop_server &srv, Batch &b, const BatchTune &bt, size_t load_
                    [](const Request *x, const Request *y) { return x->nbytes < y->nbytes; });
   const int n = (int)b.reqs.size();
   b.seq = b.seq + 1 == 0 ? 1 : b.seq + 1;
-  // While the server is lightly loaded, the smallest class's work items
-  // shrink to kFineItemRows, so that a small request is spread over several
-  // warps instead of one (its latency is then one short item); under load
-  // the tuned item size stays, since the extra blocks would only delay the
-  // large requests behind them.
-  const uint32_t ir = (b.level == 0 && load_bytes < kFineBelowBytes)
-                          ? std::min(bt.item_rows, kFineItemRows) : bt.item_rows;
+  // While the server is lightly loaded, the two smallest classes' work
+  // items shrink to kFineItemRows, so that a small request is spread over
+  // many warps instead of a few (its latency is then one short item); under
+  // load the tuned item size stays, since the extra blocks would only delay
+  // the large requests behind them.
+  const uint32_t ir = (b.level < 2 && load_bytes < kFineBelowBytes)
+                          ? std::min(bt.item_rows, kFineItemRows[b.level]) : bt.item_rows;
   const Variant &v = serve_variant(bt.variant);
   const uint64_t wpb = (uint64_t)v.bs / 32;
   static thread_local ServeParams P;   // about 8 KiB: not on the loop thread's stack
