@@ -161,15 +161,18 @@ int parse_tune(const char *text, TuneTable *out, int *bad_line) {
     if (hash != std::string::npos) line.resize(hash);
     char kind[16] = {0};
     if (sscanf(line.c_str(), "%15s", kind) != 1) continue;
-    if (strcmp(kind, "stream") == 0 || strcmp(kind, "batch") == 0) {
-      long long a[8];
-      const int n = read_ints(line, a, 8);
+    // every field is a decimal integer; a line with a stray token or the
+    // wrong number of fields is refused
+    long long a[8];
+    const int n = read_ints(line, a, 8);
+    const bool is_stream = strcmp(kind, "stream") == 0;
+    if (is_stream || strcmp(kind, "batch") == 0) {
       int g0 = 0, g1 = 0;
       if ((n != 7 && n != 8) || !tune_groups(a[0], n == 8, &g0, &g1)) return POSPOP_EINVAL;
       const long long *f = a + (n - 7);   // the seven fields after the optional <w>
       for (int i = 0; i < 7; i++)
         if (f[i] < 0 || f[i] > (1ll << 30)) return POSPOP_EINVAL;
-      if (kind[0] == 's') {
+      if (is_stream) {
         const int c = (int)f[0], v = find_variant(false, (int)f[1], (int)f[2], (int)f[3], (int)f[4]);
         if (c >= kClasses || v < 0 || f[5] < 1 || f[6] < 1) return POSPOP_EINVAL;
         for (int g = g0; g < g1; g++) t.stream[g][c] = StreamTune{v, (int)f[5], (uint32_t)f[6]};
@@ -181,29 +184,24 @@ int parse_tune(const char *text, TuneTable *out, int *bad_line) {
           t.batch[g] = BatchTune{v, (int)f[4], (uint32_t)f[5], (uint32_t)f[6]};
       }
     } else if (strcmp(kind, "short") == 0) {
-      unsigned rg;
-      if (sscanf(line.c_str(), "%*s %u", &rg) != 1 || rg > 1) return POSPOP_EINVAL;
-      t.regroup = rg;
+      if (n != 1 || a[0] < 0 || a[0] > 1) return POSPOP_EINVAL;
+      t.regroup = (uint32_t)a[0];
     } else if (strcmp(kind, "pdl") == 0) {
-      unsigned v;
-      if (sscanf(line.c_str(), "%*s %u", &v) != 1 || v > 1) return POSPOP_EINVAL;
-      t.pdl = v;
+      if (n != 1 || a[0] < 0 || a[0] > 1) return POSPOP_EINVAL;
+      t.pdl = (uint32_t)a[0];
     } else if (strcmp(kind, "staged") == 0) {
-      unsigned v;
-      if (sscanf(line.c_str(), "%*s %u", &v) != 1 || (int)v > select_staged_variant_count() / 4)
-        return POSPOP_EINVAL;
-      t.staged = v;
+      if (n != 1 || a[0] < 0 || a[0] > select_staged_variant_count() / 4) return POSPOP_EINVAL;
+      t.staged = (uint32_t)a[0];
     } else if (strcmp(kind, "split") == 0) {
-      unsigned long long mr;
-      if (sscanf(line.c_str(), "%*s %llu", &mr) != 1 || mr < 1 || mr > kMaxRowsPerWarp)
-        return POSPOP_EINVAL;
-      t.max_rows_per_warp = mr;
+      if (n != 1 || a[0] < 1 || (unsigned long long)a[0] > kMaxRowsPerWarp) return POSPOP_EINVAL;
+      t.max_rows_per_warp = (uint64_t)a[0];
     } else if (strcmp(kind, "roofline") == 0) {
-      int bs, h, cps;
-      if (sscanf(line.c_str(), "%*s %d %d %d", &bs, &h, &cps) != 3) return POSPOP_EINVAL;
-      const int v = find_roof_variant(bs, h);
-      if (v < 0 || cps < 1) return POSPOP_EINVAL;
-      t.roof = RoofTune{v, cps};
+      if (n != 3 || a[0] < 1 || a[0] > 1024 || a[1] < 0 || a[1] > 16 || a[2] < 1 ||
+          a[2] > 1024)
+        return POSPOP_EINVAL;
+      const int v = find_roof_variant((int)a[0], (int)a[1]);
+      if (v < 0) return POSPOP_EINVAL;
+      t.roof = RoofTune{v, (int)a[2]};
     } else {
       return POSPOP_EINVAL;
     }

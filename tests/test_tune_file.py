@@ -61,8 +61,9 @@ def test_per_width_and_every_width_entries(pp, tmp_path):
     "batch 512 1 16 1 1 2097152 1",      # item rows above 2^20
     "batch 512 1 16 1 1 127 65",         # grab above 64
     "batch 64 512 1 16 1 1 127 1 1",     # too many fields
-    "pdl 2", "short 2", "split 0", "split 67108865", "staged 99",
-    "roofline 300 1 4", "roofline 256 1", "bogus 1",
+    "pdl 2", "pdl 1 1", "pdl", "pdl -1", "short 2", "short 1 x", "split 0", "split 67108865",
+    "split 4 x", "staged 99", "staged", "roofline 300 1 4", "roofline 256 1",
+    "roofline 256 1 18 5", "roofline 256 1 0", "bogus 1",
 ])
 def test_malformed_line_is_reported_with_its_number(pp, tmp_path, bad):
     text = "# header\nstream 0 256 2 16 1 1 2\n\n" + bad + "\npdl 1\n"
