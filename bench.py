@@ -24,13 +24,19 @@ also carries:
   0.3 / 0.6 / 0.9 of the large-array rate, GB/s and p50/p99 latency;
 * masked: the WHERE-selected count on the 8 GiB array as 32-bit words;
 * gather: 100000 separate regions of the array into one counter array;
+* counts_ok: the timed counts of every w checked against the CPU oracle's
+  count of the whole 8 GiB array (host copy, all host cores), outside the
+  timed region;
 * cpu_baseline: the CPU oracle on the host cores on a bounded sample;
 * sweep: every w at 1 GiB and 8 GiB over Bernoulli(0.01/0.5/0.99) and
   all-ones bits, each cell's counts checked;
 * clocks: SM clocks and throttle reasons sampled during the timed region.
 
 ``--impl reference`` times the CPU oracle on the same workload instead.
-Under torchrun each rank runs an independent replica (weak scaling).
+Under torchrun each rank runs an independent replica (weak scaling);
+``--shard`` instead splits the one 8 GiB array into per-rank shards (64-byte
+boundaries), each rank counts its shard and one all-reduce of the counters
+per step completes the count (strong scaling).
 """
 from __future__ import annotations
 
@@ -162,6 +168,40 @@ def _profile_traffic(nbytes: int):
                                                  "to this launch's input bytes")
 
 
+def _oracle_counts(data_dev, widths, chunk: int = GIB):
+    """The CPU oracle's counts of a device buffer (copied back in 1 GiB
+    chunks, which start on word boundaries; all host cores), one array per w."""
+    import torch
+    import oracle
+    orc = oracle.load()
+    cores = os.cpu_count() or 1
+    n = data_dev.numel()
+    out = {w: np.zeros(w, dtype=np.uint64) for w in widths}
+    host = torch.empty(min(chunk, n), dtype=torch.uint8, pin_memory=True)
+    for c0 in range(0, n, chunk):
+        h = host[:min(chunk, n - c0)]
+        h.copy_(data_dev[c0:c0 + h.numel()])
+        a = h.numpy()
+        for w in widths:
+            orc.bytes_mt(w, a, cores, counts=out[w])
+    return out
+
+
+def _verify_counts(counts, data, launches):
+    """The timed counters hold `launches` counts of the array for each w:
+    compare them with the oracle's count of the array."""
+    t0 = time.perf_counter()
+    exp = _oracle_counts(data, WIDTHS)
+    got = counts.cpu().numpy().view(np.uint64)
+    per_w = {str(w): bool(np.array_equal(got[k, :w], exp[w] * np.uint64(launches)))
+             for k, w in enumerate(WIDTHS)}
+    return {"all": all(per_w.values()), "per_w": per_w,
+            "how": f"timed counters (each the sum of {launches} launches) == {launches} x the CPU "
+                   "oracle's count of the whole array (Fig. 2 loop on the host copy, all cores), "
+                   "checked after the timed region",
+            "oracle_s": round(time.perf_counter() - t0, 1)}
+
+
 def _cpu_baseline(data_dev, budget_s: float = 12.0, runs: int = 5):
     """The oracle as it stands on a bounded sample of the array: all host
     cores and one thread, each the median of `runs` timed passes (every pass
@@ -242,20 +282,34 @@ def run_ours(args):
     peaks, peak_kind = _measured_peaks()
     hbm_peak = float(peaks["hbm_gbs"])
 
-    nbytes = args.gib * GIB
-    data = torch.empty(nbytes, dtype=torch.uint8, device=dev)
-    synth_device.bernoulli_(data, 0.5, seed=0 + rank)
+    total_bytes = args.gib * GIB
+    if args.shard:
+        # one array (seed 0) split across the ranks; each makes only its shard
+        from paper_2412_16370_gb300 import shard
+        lo, hi = shard.shard_range(total_bytes, rank, world)
+        nbytes = hi - lo
+        data = torch.empty(max(1, nbytes), dtype=torch.uint8, device=dev)[:nbytes]
+        synth_device.bernoulli_(data, 0.5, seed=0, start=lo, nbytes=nbytes)
+    else:
+        # independent replicas: rank r counts its own array (seed r)
+        nbytes = total_bytes
+        data = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+        synth_device.bernoulli_(data, 0.5, seed=0 + rank)
     counts = torch.zeros((len(WIDTHS), 64), dtype=torch.int64, device=dev)
     stream = torch.cuda.current_stream()
     torch.cuda.synchronize()
 
     def step(ev=None):
+        if args.shard:
+            counts.zero_()
         for k, w in enumerate(WIDTHS):
             if ev is not None:
                 ev[k][0].record(stream)
             pp.pospopcnt_async(w, counts[k], data, nbytes, stream)
             if ev is not None:
                 ev[k][1].record(stream)
+        if args.shard and world > 1:
+            dist.all_reduce(counts, op=dist.ReduceOp.SUM)   # w x 8 bytes per width
 
     for _ in range(args.warmup):
         step()
@@ -293,7 +347,8 @@ def run_ours(args):
         total_ms = float(t.item())
     ms_step = total_ms / args.steps
     bytes_step = nbytes * len(WIDTHS)
-    value = world * bytes_step * args.steps / (total_ms / 1e3) / 1e9
+    job_bytes_step = (total_bytes if args.shard else world * nbytes) * len(WIDTHS)
+    value = job_bytes_step * args.steps / (total_ms / 1e3) / 1e9
 
     per_w = {}
     launch_ms_all = []
@@ -307,10 +362,26 @@ def run_ours(args):
     achieved = nbytes / (avg_launch_ms / 1e3) / 1e9
     traffic, traffic_note = _profile_traffic(nbytes)
 
-    # correctness spot check of the timed counts: every w's counts add up to the
-    # same total (the array's popcount), times the number of launches
+    # correctness of the timed counts: every w's counts add up to the same
+    # total (the array's popcount), and each equals the oracle's count
     tot = counts.sum(dim=1).cpu().numpy()
     consistent = bool(np.all(tot == tot[0]))
+    counts_ok = None
+    if args.shard:
+        # the all-reduced counters of the last step against the sum over the
+        # ranks of the oracle's counts of each shard (additivity)
+        exp = _oracle_counts(data, WIDTHS) if nbytes else {w: np.zeros(w, np.uint64)
+                                                           for w in WIDTHS}
+        e = torch.zeros((len(WIDTHS), 64), dtype=torch.int64, device=dev)
+        for k, w in enumerate(WIDTHS):
+            e[k, :w] = torch.from_numpy(exp[w].view(np.int64))
+        if world > 1:
+            dist.all_reduce(e, op=dist.ReduceOp.SUM)
+        counts_ok = {"all": bool(torch.equal(e, counts)),
+                     "how": "all-reduced counters of the last step == the sum over ranks of "
+                            "the CPU oracle's count of each rank's shard"}
+    elif rank == 0 and not args.no_verify:
+        counts_ok = _verify_counts(counts, data, args.warmup + args.steps)
 
     # roofline read kernel on the same array
     rsum = torch.zeros(1, dtype=torch.int64, device=dev)
@@ -344,7 +415,7 @@ def run_ours(args):
     extra = {}
     sections = set(args.sections.split(",")) if args.sections else None
     want = (lambda k: sections is None or k in sections)
-    if not args.quick:
+    if not args.quick and not args.shard:
         if want("e2e"):
             extra["e2e"] = _e2e(args, pp, data, nbytes, world, dist)
         if rank == 0:
@@ -380,14 +451,16 @@ def run_ours(args):
         "warmup": args.warmup,
         "ms_per_step": round(ms_step, 4),
         "higher_is_better": True,
-        "scaling": "weak",
+        "scaling": "strong" if args.shard else "weak",
         "vs_baseline": None,
         "dtype": "u32",
         "data": "synthetic (seeded SplitMix64 Bernoulli(0.5) bits, generated on the device)",
         "config": {"workload": WORKLOAD, "bytes_per_step_per_gpu": bytes_step,
-                   "array_bytes": nbytes, "widths": list(WIDTHS),
+                   "array_bytes": total_bytes, "widths": list(WIDTHS),
                    "l2": "inputs (8 GiB) far larger than L2 (126 MB): no flush between steps",
-                   "parallelism": f"replicas x{world}",
+                   "parallelism": (f"shard x{world} (one array split at 64-byte boundaries, "
+                                   "all-reduce of the counters per step)") if args.shard
+                                  else f"replicas x{world}",
                    "tune": tune_line},
         "per_w": per_w,
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak,
@@ -402,6 +475,7 @@ def run_ours(args):
                                          "shared memory, 3 x 8 KiB stages per warp)"},
         "gpu_launches": int(launches),
         "counts_consistent_across_w": consistent,
+        "counts_ok": counts_ok,
         "clocks": clocks,
     }
     line.update(extra)
@@ -738,6 +812,41 @@ def _serving(pp, synth, pool, pool_bytes, large_gbs, dev, loads=(0.3, 0.6, 0.9),
             "p99_us_below_1MiB": _pct(lat_us[r["nbytes"] < (1 << 20)], 99),
             "p99_us_from_128MiB": _pct(lat_us[r["nbytes"] >= (128 << 20)], 99),
             "status_ok": bool((recs["status"] == 0).all()), "results_match_solo": bool(same)})
+    out["lone_request"] = _serving_lone(pp, pool, dev)
+    return out
+
+
+def _serving_lone(pp, pool, dev, sizes=(64 << 10, 1 << 20, 16 << 20, 128 << 20, 256 << 20),
+                  reps=20):
+    """One request at a time (an idle server, light load): submit-to-done
+    latency per size and the request's bytes over that latency."""
+    import torch
+    srv = pp.pospop_server_create(32 << 30, 4096, 8)
+    out = []
+    try:
+        res = np.zeros(64, dtype=np.uint64)
+        for nb in sizes:
+            lat = []
+            for r in range(reps + 3):          # 3 warm-up requests
+                p0 = pool.data_ptr() + 16 * 1000 * r + 5
+                pp.pospop_server_submit(srv, 16, p0, nb, res)
+                rec = []
+                while not rec:
+                    rec = pp.pospop_server_poll(srv, 1, 1000)
+                if r >= 3:
+                    lat.append((rec[0].t_done_ns - rec[0].t_submit_ns) / 1e3)
+            # the last request's result against its single-array count
+            solo = torch.zeros(16, dtype=torch.int64, device=dev)
+            pp.pospopcnt_async(16, solo, p0, nb)
+            torch.cuda.synchronize()
+            med = float(np.median(lat))
+            out.append({"bytes": nb, "p50_us": round(med, 1),
+                        "p99_us": round(float(np.percentile(lat, 99)), 1),
+                        "GBps_at_p50": round(nb / (med * 1e-6) / 1e9, 1),
+                        "result_matches_solo": bool(np.array_equal(
+                            res[:16], solo.cpu().numpy().view(np.uint64)))})
+    finally:
+        pp.pospop_server_destroy(srv)
     return out
 
 
@@ -921,6 +1030,11 @@ def main():
     ap.add_argument("--batched-m", type=int, default=200000,
                     help="arrays in the batched section (200000 = the workload)")
     ap.add_argument("--ref-sample-mib", type=int, default=16)
+    ap.add_argument("--shard", action="store_true",
+                    help="split one array across the ranks (strong scaling) instead of "
+                         "independent replicas")
+    ap.add_argument("--no-verify", action="store_true",
+                    help="skip the oracle check of the timed counts (about 10 s of host work)")
     ap.add_argument("--quick", action="store_true",
                     help="skip every section after the headline (e2e, batched, plain, "
                          "short, serving, masked, gather, cpu_baseline, sweep)")

@@ -144,9 +144,10 @@ int pospopcnt_masked(int w, uint64_t *counts, const void *words, size_t n, const
  * lives in a fixed array of the library's own device image (about 513 KiB,
  * held by every GPU that loads the library until the process exits) instead
  * of a cudaMalloc'ed workspace: no call allocates or frees anything.  Limit:
- * m <= 65535 arrays, else POSPOP_ERANGE.  The first call on a device looks
- * up the array's address with that device current; make it before capturing
- * any stream.  Every call shares the array, so calls that overlap on the GPU
+ * m <= 65535 arrays, else POSPOP_ERANGE.  The library looks the array's
+ * address up when it sets a device up (pospopcnt_init, or the first call of
+ * any entry point on that device), with that device current; make that
+ * first call before capturing any stream.  Every call shares the array, so calls that overlap on the GPU
  * (two streams at once, unordered host threads) race and give wrong counts:
  * order them.  Decreasing offsets leave the counters untouched (no status is
  * reported; use pospopcnt_batch to get one).
@@ -155,15 +156,22 @@ int pospopcnt_batch_noalloc(int w, uint64_t *counts, const void *base, const uin
                             size_t m, void *stream);
 
 /* Synchronise `stream` and return (then clear) the device-side status word of
- * `stream`, set by the batched, gathered and roofline calls on it since it
- * was last read: POSPOP_OK, POSPOP_EINVAL (decreasing offsets) or
- * POSPOP_ETIMEDOUT (a staging wait of the bulk-copy roofline kernel
- * expired). */
+ * `stream`, set by the batched, gathered, selected and roofline calls on it
+ * since it was last read: POSPOP_OK, POSPOP_EINVAL (decreasing offsets) or
+ * POSPOP_ETIMEDOUT (a staging wait of the bulk-copy roofline kernel or of
+ * the staged selected count expired; see the tune entry `wait`). */
 int pospopcnt_batch_status(void *stream);
 
 /* Grow the workspace of `stream` so that batch calls with up to m_max
  * arrays need no allocation (required before capturing such calls into a
- * CUDA graph; a capture that needs more returns POSPOP_ENOMEM). */
+ * CUDA graph of the caller's; a capture that needs more returns
+ * POSPOP_ENOMEM).  A workspace that was used while its stream was being
+ * captured is never freed while the library is set up: when a later call
+ * needs a larger one, the old buffer is kept (the caller's graph still
+ * replays into it) until pospopcnt_shutdown, so destroy such graphs before
+ * shutting down.  A caller's graph reports its status through
+ * pospopcnt_batch_status of the capture stream only while that stream's
+ * workspace has not been replaced. */
 int pospopcnt_reserve(size_t m_max, void *stream);
 
 /*
@@ -206,7 +214,10 @@ int pospopcnt_plan(int w, size_t nbytes, uint32_t plan[8]);
  * group (w <= 8, 16, 32, >= 64) and, for the single-array count, each size
  * class on the current device (allocating a scratch buffer of up to
  * max_bytes), installs the fastest, and, if path is not NULL, writes the
- * table there.  pospopcnt_tune_load installs a table
+ * table there.  The table's `wait <cycles>` entry (0 .. 2^31, default 2^31,
+ * about a second) bounds how long a staged kernel waits for one bulk copy
+ * before it reports POSPOP_ETIMEDOUT and leaves; 0 makes every such wait
+ * give up at once (a way to exercise that exit on healthy copies).  pospopcnt_tune_load installs a table
  * written earlier; pospopcnt_tune_describe writes the current table, in the
  * same text format, into buf.
  */
@@ -225,13 +236,27 @@ int pospopcnt_tune_check(const char *path, int *bad_line);
 
 /*
  * CUDA graph of one batched call (planning + counting), captured on
- * `stream` and replayed with pospopcnt_graph_launch.  The graph keeps the
- * pointers and m it was made with.  *graph receives an opaque handle.
+ * `stream` (not the legacy stream, and not a stream already being captured)
+ * and replayed with pospopcnt_graph_launch on any stream of the same
+ * device.  The graph keeps the pointers, w and m it was made with, and owns
+ * its scratch memory: a workspace for m arrays allocated when the graph is
+ * made and freed by pospopcnt_graph_destroy (which first waits for the last
+ * replay to finish).  No other call of the library frees or reuses it, not
+ * even pospopcnt_shutdown, so a graph stays valid until it is destroyed.
+ * Replays of one graph must not overlap on the GPU (they share its
+ * scratch).  *graph receives an opaque handle.
  */
 int pospopcnt_batch_graph_create(int w, uint64_t *counts, const void *base,
                                  const uint64_t *offsets, size_t m, void *stream,
                                  void **graph);
 int pospopcnt_graph_launch(void *graph, void *stream);
+/* Wait for the graph's last replay and return (then clear) its device-side
+ * status word: POSPOP_OK, or POSPOP_EINVAL if a replay found decreasing
+ * offsets (that replay changed no counter). */
+int pospopcnt_graph_status(void *graph);
+/* The graph's own scratch memory: device address and size in bytes (either
+ * pointer may be NULL).  Fixed for the graph's lifetime. */
+int pospopcnt_graph_workspace(void *graph, void **addr, size_t *bytes);
 int pospopcnt_graph_destroy(void *graph);
 
 /*
@@ -246,11 +271,16 @@ int pospopcnt_graph_destroy(void *graph);
  * 128 MiB, and above; as many classes as the device has stream priority
  * levels, at most four), and each class has `max_batches` streams with a
  * priority that falls as the class grows.  A class's admitted requests are
- * gathered into one batch (at most 1024 requests) as soon as one of its
- * streams is free, so requests arriving while others run are counted in the
- * next batch while earlier batches are still on the device, and blocks of a
- * smaller class run before waiting blocks of a larger one.  Each result is
- * the same as the request's single-array count.  Waits are bounded by the
+ * gathered into one batch as soon as one of its streams is free, so requests
+ * arriving while others run are counted in the next batch while earlier
+ * batches are still on the device, and blocks of a smaller class run before
+ * waiting blocks of a larger one.  The tune table's `serve` entry of each
+ * class sets its work-item rows (while the server is lightly loaded, and
+ * otherwise), how many of its batches may run at once (at most
+ * `max_batches`) and how many requests a batch takes (at most 1024);
+ * `serve_light` sets the in-flight bytes below which the server counts as
+ * lightly loaded.  The server reads them as it goes.  Each result is the
+ * same as the request's single-array count.  Waits are bounded by the
  * caller's timeouts.
  * ---------------------------------------------------------------------------
  */

@@ -63,6 +63,8 @@ _SIGNATURES = {
     "pospopcnt_tune_check": ([ctypes.c_char_p, ctypes.POINTER(_int)], _int),
     "pospopcnt_batch_graph_create": ([_int, _vp, _vp, _vp, _sz, _vp, ctypes.POINTER(_vp)], _int),
     "pospopcnt_graph_launch": ([_vp, _vp], _int),
+    "pospopcnt_graph_status": ([_vp], _int),
+    "pospopcnt_graph_workspace": ([_vp, ctypes.POINTER(_vp), ctypes.POINTER(_sz)], _int),
     "pospopcnt_graph_destroy": ([_vp], _int),
     "pospopcnt_launch_count": ([], ctypes.c_uint64),
     "pospop_server_create": ([_sz, _int, _int, ctypes.POINTER(_vp)], _int),
@@ -280,6 +282,18 @@ def pospopcnt_batch_graph_create(w: int, counts, base, offsets, m=None, stream=N
 
 def pospopcnt_graph_launch(graph: int, stream=None):
     return _check(lib().pospopcnt_graph_launch(graph, _stream(stream)))
+
+
+def pospopcnt_graph_status(graph: int) -> int:
+    """Status of the graph's last replay (0 or a negative code; does not raise)."""
+    return lib().pospopcnt_graph_status(graph)
+
+
+def pospopcnt_graph_workspace(graph: int) -> tuple[int, int]:
+    """(device address, bytes) of the graph's own scratch memory."""
+    addr, size = _vp(), _sz()
+    _check(lib().pospopcnt_graph_workspace(graph, ctypes.byref(addr), ctypes.byref(size)))
+    return addr.value or 0, size.value
 
 
 def pospopcnt_graph_destroy(graph: int):

@@ -89,6 +89,13 @@ TuneTable default_tune() {
   t.regroup = 0;
   t.pdl = 1;
   t.staged = 3;   // 16 warps x 1 stage: measured fastest on GB300
+  t.wait_cycles = kBulkWaitCycles;
+  // serving: small classes split into short items while lightly loaded
+  t.serve[0] = ServeTune{8, 127, 64, 1024};
+  t.serve[1] = ServeTune{32, 127, 64, 1024};
+  t.serve[2] = ServeTune{0, 127, 64, 1024};
+  t.serve[3] = ServeTune{0, 127, 64, 1024};
+  t.serve_light = uint64_t(512) << 20;
   t.set_source("built-in defaults");
   return t;
 }
@@ -110,6 +117,19 @@ TuneTable default_tune() {
 //                                  stage their input in shared memory by bulk copies,
 //                                  ring shape k: 1 = 8 warps x 3 stages, 2 = 12 x 2,
 //                                  3 = 16 x 1; 0 = loads into registers)
+//   serve <class> <light_rows> <rows> <streams> <cap>
+//                                 (serving size class 0..3 = below 1 MiB, 16 MiB,
+//                                  128 MiB, above: work-item rows while lightly loaded
+//                                  (0 = spread the batch over every SM) and otherwise
+//                                  (1 .. 2^20), batch streams of the class running at
+//                                  once (1 .. 64), requests per batch (1 .. 1024))
+//   serve_light <bytes>           (in-flight input bytes below which the server counts
+//                                  as lightly loaded)
+//   wait <cycles>                 (0 .. 2^31: how long a staged kernel waits for a
+//                                  stage's bulk copy, in SM clock cycles, before it
+//                                  reports POSPOP_ETIMEDOUT and leaves; default 2^31,
+//                                  about a second; 0 gives up at once, which tests
+//                                  the time-out exit on healthy copies)
 // The integers after the line's keyword, at most max of them: their number,
 // or -1 for a token that is not an integer or one too many.
 static int read_ints(const std::string &line, long long *v, int max) {
@@ -192,6 +212,17 @@ int parse_tune(const char *text, TuneTable *out, int *bad_line) {
     } else if (strcmp(kind, "staged") == 0) {
       if (n != 1 || a[0] < 0 || a[0] > select_staged_variant_count() / 4) return POSPOP_EINVAL;
       t.staged = (uint32_t)a[0];
+    } else if (strcmp(kind, "serve") == 0) {
+      if (n != 5 || a[0] < 0 || a[0] >= kServeClasses || a[1] < 0 || a[1] > (1 << 20) ||
+          a[2] < 1 || a[2] > (1 << 20) || a[3] < 1 || a[3] > 64 || a[4] < 1 || a[4] > 1024)
+        return POSPOP_EINVAL;
+      t.serve[a[0]] = ServeTune{(uint32_t)a[1], (uint32_t)a[2], (uint32_t)a[3], (uint32_t)a[4]};
+    } else if (strcmp(kind, "serve_light") == 0) {
+      if (n != 1 || a[0] < 0) return POSPOP_EINVAL;
+      t.serve_light = (uint64_t)a[0];
+    } else if (strcmp(kind, "wait") == 0) {
+      if (n != 1 || a[0] < 0 || a[0] > kBulkWaitCycles) return POSPOP_EINVAL;
+      t.wait_cycles = a[0];
     } else if (strcmp(kind, "split") == 0) {
       if (n != 1 || a[0] < 1 || (unsigned long long)a[0] > kMaxRowsPerWarp) return POSPOP_EINVAL;
       t.max_rows_per_warp = (uint64_t)a[0];
@@ -272,6 +303,19 @@ std::string format_tune(const DevCtx &ctx, const TuneTable &t) {
     snprintf(line, sizeof line, "split %llu\n", (unsigned long long)t.max_rows_per_warp);
     s += line;
   }
+  s += "# serve <class> <light_rows> <rows> <streams> <cap>\n";
+  for (int k = 0; k < kServeClasses; k++) {
+    const ServeTune &e = t.serve[k];
+    snprintf(line, sizeof line, "serve %d %u %u %u %u\n", k, e.light_rows, e.rows, e.streams,
+             e.cap);
+    s += line;
+  }
+  snprintf(line, sizeof line, "serve_light %llu\n", (unsigned long long)t.serve_light);
+  s += line;
+  if (t.wait_cycles != kBulkWaitCycles) {
+    snprintf(line, sizeof line, "wait %lld\n", t.wait_cycles);
+    s += line;
+  }
   {
     const Variant &v = roofline_variant(t.roof.variant);
     s += "# roofline <bs> <hint> <ctas_per_sm>\n";
@@ -345,6 +389,15 @@ static int init_ctx(DevCtx &c, int device) {
     }
     c.occ_batch[i] = n > 0 ? n : 1;
   }
+  for (int i = 0; i < serve_variant_count(); i++) {
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, serve_variant(i).fn,
+                                                      serve_variant(i).bs, 0) != cudaSuccess) {
+      cudaGetLastError();
+      return POSPOP_ECUDA;
+    }
+    c.occ_serve[i] = n > 0 ? n : 1;
+  }
   for (int i = 0; i < roofline_variant_count(); i++) {
     const Variant &v = roofline_variant(i);
     int n = 0;
@@ -369,6 +422,9 @@ static int init_ctx(DevCtx &c, int device) {
     }
     c.occ_select_staged[i] = n;
   }
+  // the no-allocation batch's scratch array: its device address, looked up
+  // once per device with that device current
+  if (noalloc_lookup(&c.noalloc_scratch) != POSPOP_OK) return POSPOP_ECUDA;
   c.device = device;
   c.sms = sms;
   c.tune = initial_tune();
@@ -421,6 +477,8 @@ static void free_ctx(DevCtx &c) {
   for (auto &kv : c.ws)
     if (kv.second.buf) cudaFree(kv.second.buf);
   c.ws.clear();
+  for (void *b : c.retired) cudaFree(b);
+  c.retired.clear();
   free_staging(c.st);
   c.ready = false;
   cudaGetLastError();
@@ -455,7 +513,7 @@ static PtrKind classify(const void *p, int device, const void **devptr) {
   }
 }
 
-static bool device_addressable(const void *p, int device, const void **devptr) {
+bool device_addressable(const void *p, int device, const void **devptr) {
   const PtrKind k = classify(p, device, devptr);
   return k == kDev || k == kPinned;
 }
@@ -556,7 +614,8 @@ int launch_stream(DevCtx &ctx, int w, unsigned long long *counts, const void *by
 }
 
 int launch_roofline_with(const DevCtx &ctx, const RoofTune &rt, const void *bytes, size_t nbytes,
-                         unsigned long long *sum, int *status, cudaStream_t stream, bool pdl) {
+                         unsigned long long *sum, int *status, long long wait_cycles,
+                         cudaStream_t stream, bool pdl) {
   const uint64_t p0 = (uint64_t)bytes;
   const uint64_t A = (p0 + 15u) & ~15ull, E = (p0 + nbytes) & ~15ull;
   if (E <= A) return POSPOP_OK;
@@ -565,6 +624,7 @@ int launch_roofline_with(const DevCtx &ctx, const RoofTune &rt, const void *byte
   P.G = (E - A) >> 4;
   P.sum = sum;
   P.status = status;
+  P.wait_cycles = wait_cycles;
   const Variant &v = roofline_variant(rt.variant);
   if (v.smem > 0 && !status) return POSPOP_EINVAL;
   int cps = rt.ctas_per_sm;   // above the occupancy limit: waves, as for the count
@@ -589,9 +649,15 @@ int launch_roofline_with(const DevCtx &ctx, const RoofTune &rt, const void *byte
 // ---------------------------------------------------------------------------
 // Batched launches and their workspace.
 // ---------------------------------------------------------------------------
-static size_t ws_bytes(size_t m_cap) {
+Scratch scratch_layout(void *buf, size_t m_cap) {
   const size_t nb = (m_cap + kPlanChunk - 1) / kPlanChunk + 1;
-  return 8 * (m_cap + 1) + 8 * nb + 16;
+  uint8_t *b = static_cast<uint8_t *>(buf);
+  Scratch r;
+  r.item_start = reinterpret_cast<uint64_t *>(b);
+  r.block_sum = reinterpret_cast<uint64_t *>(b + 8 * (m_cap + 1));
+  r.next = reinterpret_cast<unsigned long long *>(b + 8 * (m_cap + 1) + 8 * nb);
+  r.status = reinterpret_cast<int *>(b + 8 * (m_cap + 1) + 8 * nb + 8);
+  return r;
 }
 
 static int is_capturing(cudaStream_t s, bool *cap) {
@@ -605,38 +671,43 @@ static int is_capturing(cudaStream_t s, bool *cap) {
 }
 
 // Workspace of `stream` with room for m arrays (grown if needed).  Caller
-// holds ctx.mu.
+// holds ctx.mu.  A call made while the stream is being captured into a
+// caller's CUDA graph marks the workspace as captured: the graph keeps its
+// addresses, so once the workspace has to grow the old buffer is retired
+// (kept until pospopcnt_shutdown) instead of freed.  Graphs made by
+// pospopcnt_batch_graph_create have a workspace of their own.
 static int get_ws(DevCtx &ctx, cudaStream_t stream, size_t m, Workspace **out) {
   Workspace &w = ctx.ws[stream];
-  if (w.buf && w.m_cap >= m) {
-    *out = &w;
-    return POSPOP_OK;
-  }
   bool cap = false;
   int rc = is_capturing(stream, &cap);
   if (rc != POSPOP_OK) return rc;
+  if (w.buf && w.m_cap >= m) {
+    w.captured = w.captured || cap;
+    *out = &w;
+    return POSPOP_OK;
+  }
   if (cap) return POSPOP_ENOMEM;   // no allocation inside a capture: call pospopcnt_reserve first
   size_t cap_m = w.m_cap ? w.m_cap : 65536;
   while (cap_m < m) cap_m *= 2;
   void *buf = nullptr;
-  if (cudaMalloc(&buf, ws_bytes(cap_m)) != cudaSuccess) {
+  if (cudaMalloc(&buf, scratch_bytes(cap_m)) != cudaSuccess) {
     cudaGetLastError();
     return POSPOP_ENOMEM;
   }
   if (w.buf) {
-    // the old buffer may still be in use by work queued on this stream
-    if (cudaStreamSynchronize(stream) != cudaSuccess) { cudaGetLastError(); }
-    cudaFree(w.buf);
+    if (w.captured) {
+      ctx.retired.push_back(w.buf);   // a caller's graph may replay into it
+    } else {
+      // the old buffer may still be in use by work queued on this stream
+      if (cudaStreamSynchronize(stream) != cudaSuccess) { cudaGetLastError(); }
+      cudaFree(w.buf);
+    }
   }
-  const size_t nb = (cap_m + kPlanChunk - 1) / kPlanChunk + 1;
-  uint8_t *b = static_cast<uint8_t *>(buf);
   w.buf = buf;
   w.m_cap = cap_m;
-  w.item_start = reinterpret_cast<uint64_t *>(b);
-  w.block_sum = reinterpret_cast<uint64_t *>(b + 8 * (cap_m + 1));
-  w.next = reinterpret_cast<unsigned long long *>(b + 8 * (cap_m + 1) + 8 * nb);
-  w.status = reinterpret_cast<int *>(b + 8 * (cap_m + 1) + 8 * nb + 8);
-  if (cudaMemsetAsync(w.status, 0, sizeof(int), stream) != cudaSuccess) {
+  w.scr = scratch_layout(buf, cap_m);
+  w.captured = false;
+  if (cudaMemsetAsync(w.scr.status, 0, sizeof(int), stream) != cudaSuccess) {
     cudaGetLastError();
     return POSPOP_ECUDA;
   }
@@ -664,13 +735,21 @@ static int launch_plan(const void *items_fn, const PlanParams &pp, cudaStream_t 
 
 int launch_batch_with(DevCtx &ctx, const TuneTable &t, int w, unsigned long long *counts,
                       const void *base, const uint64_t *offsets, size_t m, cudaStream_t stream) {
-  Workspace *ws = nullptr;
+  Scratch scr;
   {
     std::lock_guard<std::mutex> g(ctx.mu);
+    Workspace *ws = nullptr;
     const int rc = get_ws(ctx, stream, m, &ws);
     if (rc != POSPOP_OK) return rc;
+    scr = ws->scr;
   }
-  if (cudaMemsetAsync(ws->status, 0, sizeof(int), stream) != cudaSuccess) {
+  return launch_batch_scratch(ctx, t, w, counts, base, offsets, m, scr, stream);
+}
+
+int launch_batch_scratch(const DevCtx &ctx, const TuneTable &t, int w, unsigned long long *counts,
+                         const void *base, const uint64_t *offsets, size_t m,
+                         const Scratch &scr, cudaStream_t stream) {
+  if (cudaMemsetAsync(scr.status, 0, sizeof(int), stream) != cudaSuccess) {
     cudaGetLastError();
     return POSPOP_ECUDA;
   }
@@ -681,10 +760,10 @@ int launch_batch_with(DevCtx &ctx, const TuneTable &t, int w, unsigned long long
   pp.offsets = offsets;
   pp.m = m;
   pp.base_addr = (uint64_t)base;
-  pp.item_start = ws->item_start;
-  pp.block_sum = ws->block_sum;
-  pp.next = ws->next;
-  pp.status = ws->status;
+  pp.item_start = scr.item_start;
+  pp.block_sum = scr.block_sum;
+  pp.next = scr.next;
+  pp.status = scr.status;
   pp.item_rows = bt.item_rows;
   pp.nblocks = (uint32_t)((m + kPlanChunk - 1) / kPlanChunk);
   int rc = launch_plan(plan_items_fn(), pp, stream, t.pdl != 0);
@@ -698,9 +777,9 @@ int launch_batch_with(DevCtx &ctx, const TuneTable &t, int w, unsigned long long
   bp.m = m;
   bp.counts = counts;
   bp.w = w;
-  bp.item_start = ws->item_start;
-  bp.next = ws->next;
-  bp.status = ws->status;
+  bp.item_start = scr.item_start;
+  bp.next = scr.next;
+  bp.status = scr.status;
   bp.item_rows = bt.item_rows;
   bp.grab = bt.grab;
   bp.regroup = t.regroup;
@@ -730,13 +809,15 @@ int launch_batch_with(DevCtx &ctx, const TuneTable &t, int w, unsigned long long
 static int launch_gather_with(DevCtx &ctx, const TuneTable &t, int w, unsigned long long *counts,
                               const uint64_t *ptrs, const uint64_t *lens, size_t n,
                               cudaStream_t stream) {
-  Workspace *ws = nullptr;
+  Scratch scr;
   {
     std::lock_guard<std::mutex> g(ctx.mu);
+    Workspace *ws = nullptr;
     const int rc = get_ws(ctx, stream, n, &ws);
     if (rc != POSPOP_OK) return rc;
+    scr = ws->scr;
   }
-  if (cudaMemsetAsync(ws->status, 0, sizeof(int), stream) != cudaSuccess) {
+  if (cudaMemsetAsync(scr.status, 0, sizeof(int), stream) != cudaSuccess) {
     cudaGetLastError();
     return POSPOP_ECUDA;
   }
@@ -746,10 +827,10 @@ static int launch_gather_with(DevCtx &ctx, const TuneTable &t, int w, unsigned l
   pp.gptrs = ptrs;
   pp.glens = lens;
   pp.m = n;
-  pp.item_start = ws->item_start;
-  pp.block_sum = ws->block_sum;
-  pp.next = ws->next;
-  pp.status = ws->status;
+  pp.item_start = scr.item_start;
+  pp.block_sum = scr.block_sum;
+  pp.next = scr.next;
+  pp.status = scr.status;
   pp.item_rows = bt.item_rows;
   pp.nblocks = (uint32_t)((n + kPlanChunk - 1) / kPlanChunk);
   const int prc = launch_plan(plan_items_gather_fn(), pp, stream, t.pdl != 0);
@@ -761,9 +842,9 @@ static int launch_gather_with(DevCtx &ctx, const TuneTable &t, int w, unsigned l
   bp.m = n;
   bp.counts = counts;
   bp.w = w;
-  bp.item_start = ws->item_start;
-  bp.next = ws->next;
-  bp.status = ws->status;
+  bp.item_start = scr.item_start;
+  bp.next = scr.next;
+  bp.status = scr.status;
   bp.item_rows = bt.item_rows;
   bp.grab = bt.grab;
   bp.regroup = t.regroup;
@@ -813,6 +894,7 @@ static int launch_select_with(DevCtx &ctx, const TuneTable &t, int w,
   Q.sel_base = nullptr;
   Q.sel_bit0 = 0;
   Q.status = nullptr;
+  Q.wait_cycles = t.wait_cycles;
   const uint64_t R = (P.s.G + 31) >> 5;
   // Staged form: enough chunks wholly inside the span (16 rows; not chunk 0
   // when the span or the bitmap starts inside a 16-byte block, not the
@@ -845,7 +927,7 @@ static int launch_select_with(DevCtx &ctx, const TuneTable &t, int w,
         Workspace *ws = nullptr;
         const int rc = get_ws(ctx, stream, 0, &ws);
         if (rc != POSPOP_OK) return rc;
-        status = ws->status;
+        status = ws->scr.status;
       }
       if (cudaMemsetAsync(status, 0, sizeof(int), stream) != cudaSuccess) {
         cudaGetLastError();
@@ -857,6 +939,7 @@ static int launch_select_with(DevCtx &ctx, const TuneTable &t, int w,
       Q.sel_base = static_cast<const uint8_t *>(select) - mb;
       Q.sel_bit0 = bit0;
       Q.status = status;
+      Q.wait_cycles = t.wait_cycles;
       P.row_begin = 0;
       P.row_end = R;
       void *args[] = {&Q};
@@ -1154,7 +1237,7 @@ int pospopcnt_batch_status(void *stream) {
     std::lock_guard<std::mutex> g(c->mu);
     auto it = c->ws.find(s);
     if (it == c->ws.end() || !it->second.buf) return POSPOP_OK;
-    status = it->second.status;
+    status = it->second.scr.status;
   }
   int h = 0;
   if (cudaMemcpy(&h, status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess ||
@@ -1196,16 +1279,18 @@ int pospopcnt_roofline_read(const void *bytes, size_t nbytes, uint64_t *sum, voi
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   RoofTune rt;
   bool pdl;
+  long long wait_cycles;
   int *status = nullptr;
   {
     std::lock_guard<std::mutex> g(c->mu);
     rt = c->tune.roof;
     pdl = c->tune.pdl != 0;
+    wait_cycles = c->tune.wait_cycles;
     if (roofline_variant(rt.variant).smem > 0) {   // bulk-copy form: the stream's status word
       Workspace *ws = nullptr;
       rc = get_ws(*c, s, 0, &ws);
       if (rc != POSPOP_OK) return rc;
-      status = ws->status;
+      status = ws->scr.status;
     }
   }
   if (status && cudaMemsetAsync(status, 0, sizeof(int), s) != cudaSuccess) {
@@ -1213,7 +1298,7 @@ int pospopcnt_roofline_read(const void *bytes, size_t nbytes, uint64_t *sum, voi
     return POSPOP_ECUDA;
   }
   return launch_roofline_with(*c, rt, db, nbytes, (unsigned long long *)const_cast<void *>(ds),
-                              status, s, pdl);
+                              status, wait_cycles, s, pdl);
 }
 
 int pospopcnt_plan(int w, size_t nbytes, uint32_t plan[8]) {
@@ -1283,38 +1368,85 @@ int pospopcnt_tune_describe(char *buf, size_t len) {
   return s.size() < len ? POSPOP_OK : POSPOP_ERANGE;
 }
 
+// A graph made by pospopcnt_batch_graph_create owns the scratch it was
+// captured with (allocated before the capture, freed by
+// pospopcnt_graph_destroy), so no later call of the library (a larger batch
+// on the same stream, pospopcnt_shutdown) can free memory the graph replays
+// into.  `done` is recorded after every replay: destroy waits for it before
+// freeing the scratch, and the status query waits for it before reading.
 struct pospop_graph {
-  cudaGraph_t graph;
-  cudaGraphExec_t exec;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaEvent_t done = nullptr;
+  void *ws = nullptr;
+  size_t ws_bytes = 0;
+  Scratch scr;
+  int device = -1;
 };
+
+static void free_graph(pospop_graph *h) {
+  if (h->done) cudaEventSynchronize(h->done);   // the last replay has finished
+  if (h->exec) cudaGraphExecDestroy(h->exec);
+  if (h->graph) cudaGraphDestroy(h->graph);
+  if (h->done) cudaEventDestroy(h->done);
+  if (h->ws) cudaFree(h->ws);
+  cudaGetLastError();
+  delete h;
+}
 
 int pospopcnt_batch_graph_create(int w, uint64_t *counts, const void *base,
                                  const uint64_t *offsets, size_t m, void *stream, void **graph) {
   if (!graph || !stream) return POSPOP_EINVAL;   // the legacy stream cannot be captured
   *graph = nullptr;
-  int rc = pospopcnt_reserve(m, stream);
-  if (rc != POSPOP_OK) return rc;
+  if (!valid_w_multi(w) || m == 0 || !counts || !base || !offsets) return POSPOP_EINVAL;
+  if (m > (SIZE_MAX / 8) / 256 - 1) return POSPOP_ERANGE;
+  int rc = POSPOP_OK;
+  DevCtx *c = current_ctx(&rc);
+  if (!c) return rc;
+  const void *dc = nullptr, *db = nullptr, *doff = nullptr;
+  if (!device_addressable(counts, c->device, &dc) || !device_addressable(base, c->device, &db) ||
+      !device_addressable(offsets, c->device, &doff))
+    return POSPOP_EPTR;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  bool cap = false;
+  rc = is_capturing(s, &cap);
+  if (rc != POSPOP_OK) return rc;
+  if (cap) return POSPOP_EINVAL;   // the graph is captured on `stream` itself
+  TuneTable t;
+  {
+    std::lock_guard<std::mutex> g(c->mu);
+    t = c->tune;
+  }
+  pospop_graph *h = new pospop_graph();
+  h->device = c->device;
+  h->ws_bytes = scratch_bytes(m);
+  if (cudaMalloc(&h->ws, h->ws_bytes) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->done, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    free_graph(h);
+    return POSPOP_ENOMEM;
+  }
+  h->scr = scratch_layout(h->ws, m);
   if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
     cudaGetLastError();
+    free_graph(h);
     return POSPOP_ECUDA;
   }
-  rc = pospopcnt_batch(w, counts, base, offsets, m, stream);
-  cudaGraph_t g = nullptr;
-  const cudaError_t e = cudaStreamEndCapture(s, &g);
+  rc = launch_batch_scratch(*c, t, w, (unsigned long long *)const_cast<void *>(dc), db,
+                            static_cast<const uint64_t *>(doff), m, h->scr, s);
+  const cudaError_t e = cudaStreamEndCapture(s, &h->graph);
   if (rc == POSPOP_OK && e != cudaSuccess) rc = POSPOP_ECUDA;
+  if (rc == POSPOP_OK && cudaGraphInstantiate(&h->exec, h->graph, 0) != cudaSuccess)
+    rc = POSPOP_ECUDA;
+  // the status word starts clear (the graph clears it again on every replay)
+  if (rc == POSPOP_OK && (cudaMemset(h->scr.status, 0, sizeof(int)) != cudaSuccess ||
+                          cudaEventRecord(h->done, s) != cudaSuccess))
+    rc = POSPOP_ECUDA;
   if (rc != POSPOP_OK) {
     cudaGetLastError();
-    if (g) cudaGraphDestroy(g);
+    free_graph(h);
     return rc;
   }
-  cudaGraphExec_t x = nullptr;
-  if (cudaGraphInstantiate(&x, g, 0) != cudaSuccess) {
-    cudaGetLastError();
-    cudaGraphDestroy(g);
-    return POSPOP_ECUDA;
-  }
-  pospop_graph *h = new pospop_graph{g, x};
   *graph = h;
   return POSPOP_OK;
 }
@@ -1322,7 +1454,8 @@ int pospopcnt_batch_graph_create(int w, uint64_t *counts, const void *base,
 int pospopcnt_graph_launch(void *graph, void *stream) {
   if (!graph) return POSPOP_EINVAL;
   pospop_graph *h = static_cast<pospop_graph *>(graph);
-  if (cudaGraphLaunch(h->exec, static_cast<cudaStream_t>(stream)) != cudaSuccess) {
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (cudaGraphLaunch(h->exec, s) != cudaSuccess || cudaEventRecord(h->done, s) != cudaSuccess) {
     cudaGetLastError();
     return POSPOP_ECUDA;
   }
@@ -1330,12 +1463,41 @@ int pospopcnt_graph_launch(void *graph, void *stream) {
   return POSPOP_OK;
 }
 
+int pospopcnt_graph_status(void *graph) {
+  if (!graph) return POSPOP_EINVAL;
+  pospop_graph *h = static_cast<pospop_graph *>(graph);
+  int prev = -1;
+  cudaGetDevice(&prev);
+  int host = 0;
+  const bool ok = cudaSetDevice(h->device) == cudaSuccess &&
+                  cudaEventSynchronize(h->done) == cudaSuccess &&
+                  cudaMemcpy(&host, h->scr.status, sizeof(int), cudaMemcpyDeviceToHost) ==
+                      cudaSuccess &&
+                  cudaMemset(h->scr.status, 0, sizeof(int)) == cudaSuccess;
+  if (prev >= 0) cudaSetDevice(prev);
+  if (!ok) {
+    cudaGetLastError();
+    return POSPOP_ECUDA;
+  }
+  return host == 0 ? POSPOP_OK : POSPOP_EINVAL;
+}
+
+int pospopcnt_graph_workspace(void *graph, void **addr, size_t *bytes) {
+  if (!graph) return POSPOP_EINVAL;
+  const pospop_graph *h = static_cast<const pospop_graph *>(graph);
+  if (addr) *addr = h->ws;
+  if (bytes) *bytes = h->ws_bytes;
+  return POSPOP_OK;
+}
+
 int pospopcnt_graph_destroy(void *graph) {
   if (!graph) return POSPOP_EINVAL;
   pospop_graph *h = static_cast<pospop_graph *>(graph);
-  cudaGraphExecDestroy(h->exec);
-  cudaGraphDestroy(h->graph);
-  delete h;
+  int prev = -1;
+  cudaGetDevice(&prev);
+  cudaSetDevice(h->device);
+  free_graph(h);
+  if (prev >= 0) cudaSetDevice(prev);
   return POSPOP_OK;
 }
 

@@ -6,10 +6,11 @@
 
 #include <cstdint>
 
+#include "pospop_internal.h"
+
 namespace pospop {
 
 constexpr uint32_t kBulkChunk = 8192;                  // bytes per chunk = 512 granules
-constexpr long long kBulkWaitCycles = 1ll << 31;       // about a second at 2 GHz
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -56,12 +57,16 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
 }
 
 // Wait for the barrier phase with the given parity to complete; false if it
-// has not after kBulkWaitCycles.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+// has not within `limit` SM clock cycles.  The clock is checked before each
+// try, so a limit of 0 gives up without waiting at all (the kernels take
+// their time-out exit on a healthy copy: that is how the exit is tested).
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity,
+                                          long long limit = kBulkWaitCycles) {
   const long long t0 = clock64();
-  while (!mbar_try(bar, parity))
-    if (clock64() - t0 > kBulkWaitCycles) return false;
-  return true;
+  for (;;) {
+    if (clock64() - t0 >= limit) return false;
+    if (mbar_try(bar, parity)) return true;
+  }
 }
 
 }  // namespace pospop

@@ -8,6 +8,12 @@
 
 namespace pospop {
 
+// Longest wait of a staged kernel for one bulk copy, in SM clock cycles
+// (about a second at 2 GHz): the default limit of the first wait on a
+// stage, and the fixed limit of the waits that drain a warp's copies still
+// in flight before it leaves.
+constexpr long long kBulkWaitCycles = 1ll << 31;
+
 // One array (or a piece of one) in 16-byte granule coordinates; see
 // pospop_device.cuh for the layout.
 struct SpanH {
@@ -103,6 +109,7 @@ struct SelectParams {
   const uint8_t *sel_base;      // staged form: the bitmap rounded down to 16 bytes
   int64_t sel_bit0;             // staged form: bit of sel_base where chunk 0's bits start
   int *status;                  // staged form: set to POSPOP_ETIMEDOUT if a wait expires
+  long long wait_cycles;        // staged form: limit of a wait for a stage (SM clock cycles)
 };
 
 struct RooflineParams {
@@ -110,6 +117,7 @@ struct RooflineParams {
   uint64_t G;                   // whole granules
   unsigned long long *sum;
   int *status;                  // bulk-copy form: set to POSPOP_ETIMEDOUT if a wait expires
+  long long wait_cycles;        // bulk-copy form: limit of a wait for a stage (SM clock cycles)
 };
 
 // Kernel variant descriptor.  `fn` is the __global__ function to launch

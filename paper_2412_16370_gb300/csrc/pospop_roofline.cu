@@ -90,7 +90,8 @@ __global__ void __launch_bounds__(NW * 32, 1) roofline_bulk_kernel(RooflineParam
   for (uint64_t c = gw; c < nch; c += TW, it++) {
     const int k = (int)(it % S);
     // warp-uniform: every lane leaves together if any lane's wait expired
-    if (!__all_sync(kFull, mbar_wait(smem_addr(bars + k), (uint32_t)((it / S) & 1u)))) {
+    if (!__all_sync(kFull,
+                    mbar_wait(smem_addr(bars + k), (uint32_t)((it / S) & 1u), P.wait_cycles))) {
       timed_out = true;
       break;
     }
@@ -110,8 +111,9 @@ __global__ void __launch_bounds__(NW * 32, 1) roofline_bulk_kernel(RooflineParam
     }
   }
   if (timed_out) {
-    // report, then wait (bounded again) for this warp's copies still in
-    // flight so that none lands after the block has left
+    // report, then wait (bounded by the fixed kBulkWaitCycles, whatever
+    // P.wait_cycles is) for this warp's copies still in flight so that none
+    // lands after the block has left
     if (lane == 0 && P.status) atomicExch(P.status, POSPOP_ETIMEDOUT);
     for (uint64_t j = 0, c = gw + it * TW; j < (uint64_t)S && c < nch; j++, c += TW)
       (void)mbar_wait(smem_addr(bars + (int)((it + j) % S)), (uint32_t)(((it + j) / S) & 1u));

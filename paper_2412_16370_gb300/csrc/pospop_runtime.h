@@ -11,6 +11,7 @@
 #include <mutex>
 #include <string>
 #include <unordered_map>
+#include <vector>
 
 #include "pospop_internal.h"
 
@@ -38,6 +39,17 @@ struct RoofTune {
   int variant;
   int ctas_per_sm;
 };
+// Serving: one entry per request size class of the server (below 1 MiB,
+// 16 MiB, 128 MiB, and above).
+constexpr int kServeClasses = 4;
+struct ServeTune {
+  uint32_t light_rows;      // work-item rows while the server is lightly loaded (0 = spread the
+                            // batch over every SM: the fewest rows that give each resident warp
+                            // of the GPU two items, at most `rows`)
+  uint32_t rows;            // work-item rows otherwise
+  uint32_t streams;         // batch streams of the class that may run at once
+  uint32_t cap;             // requests per batch
+};
 // Width group of w (1..256, a power of two): the tune table keeps one
 // single-array entry per (width group, size class) and one batch entry per
 // width group.
@@ -53,17 +65,37 @@ struct TuneTable {
   uint32_t pdl;                 // 1 = launch with programmatic stream serialization
   uint32_t staged;              // selected counts of aligned spans: 0 = registers, k > 0 =
                                 // bulk-copy staging with ring shape k - 1
+  ServeTune serve[kServeClasses];
+  uint64_t serve_light;         // in-flight input bytes below which the server counts as light
+  long long wait_cycles;        // limit of a staged kernel's wait for a bulk copy (SM clock
+                                // cycles, 0 .. kBulkWaitCycles; 0 = give up at once)
   char source[240];             // where the table came from (copied with the table: no heap)
   void set_source(const char *s);
 };
 
-struct Workspace {
-  void *buf = nullptr;
-  size_t m_cap = 0;
+// Scratch memory of one batched or gathered count: per-array prefix sums of
+// work items (m + 1), the planning blocks' sums, the work counter and the
+// device-side status word.
+struct Scratch {
   uint64_t *item_start = nullptr;
   uint64_t *block_sum = nullptr;
   unsigned long long *next = nullptr;
   int *status = nullptr;
+};
+
+// Bytes of scratch for up to m_cap arrays, and its layout in a buffer of
+// that size (256-byte aligned): item_start[m_cap + 1], one block sum per
+// planning block (plus one), the work counter, the status word.
+constexpr size_t scratch_bytes(size_t m_cap) {
+  return 8 * (m_cap + 1) + 8 * ((m_cap + kPlanChunk - 1) / kPlanChunk + 1) + 16;
+}
+Scratch scratch_layout(void *buf, size_t m_cap);
+
+struct Workspace {
+  void *buf = nullptr;
+  size_t m_cap = 0;
+  Scratch scr;
+  bool captured = false;   // used while the stream was being captured into a graph
 };
 
 struct Staging {
@@ -83,12 +115,15 @@ struct DevCtx {
   std::mutex mu;        // workspace map, tune table
   std::mutex host_mu;   // staging area
   std::unordered_map<cudaStream_t, Workspace> ws;
+  std::vector<void *> retired;   // outgrown workspaces that a caller's graph may still use
+  unsigned char *noalloc_scratch = nullptr;   // device address of the no-allocation array
   Staging st;
   TuneTable tune;
   int occ_stream[64] = {0};
   int occ_batch[64] = {0};
   int occ_roof[16] = {0};
   int occ_select_staged[16] = {0};
+  int occ_serve[64] = {0};
 };
 
 // Returns the context of the current device, setting it up if needed, or
@@ -125,10 +160,30 @@ int launch_stream(DevCtx &ctx, int w, unsigned long long *counts, const void *by
                   size_t nbytes, cudaStream_t stream);
 int launch_batch_with(DevCtx &ctx, const TuneTable &t, int w, unsigned long long *counts,
                       const void *base, const uint64_t *offsets, size_t m, cudaStream_t stream);
+// The batched count over CSR offsets with the given scratch (room for m
+// arrays): clears the status word, then enqueues the three planning kernels
+// and the persistent counting kernel on `stream`.  Every batched form (the
+// per-stream workspace, a graph's own workspace, the no-allocation array)
+// launches through this one routine.
+int launch_batch_scratch(const DevCtx &ctx, const TuneTable &t, int w, unsigned long long *counts,
+                         const void *base, const uint64_t *offsets, size_t m,
+                         const Scratch &scr, cudaStream_t stream);
 // status: a device int the bulk-copy form sets to POSPOP_ETIMEDOUT when a
-// staging wait expires (required for that form, ignored by the others).
+// staging wait expires (required for that form, ignored by the others);
+// wait_cycles: that wait's limit.
 int launch_roofline_with(const DevCtx &ctx, const RoofTune &rt, const void *bytes, size_t nbytes,
-                         unsigned long long *sum, int *status, cudaStream_t stream, bool pdl);
+                         unsigned long long *sum, int *status, long long wait_cycles,
+                         cudaStream_t stream, bool pdl);
+
+// A pointer the device can read or write (device memory of ctx's device,
+// managed memory, or pinned host memory mapped into the device's address
+// space); *devptr receives the address to give a kernel.
+bool device_addressable(const void *p, int device, const void **devptr);
+
+// Device address of the no-allocation batch's scratch array on the current
+// device (pospop_noalloc.cu); called once per device when its context is
+// set up, with that device current.
+int noalloc_lookup(unsigned char **out);
 
 void note_launches(uint64_t n);
 

@@ -126,7 +126,8 @@ __global__ void __launch_bounds__(NW * 32, 1) select_staged_kernel(SelectParams 
   bool timed_out = false;
   for (uint64_t c = c0; c < nch; c += TW, it++) {
     const int k = (int)(it % S);
-    if (!__all_sync(kFull, mbar_wait(smem_addr(bars + k), (uint32_t)((it / S) & 1u)))) {
+    if (!__all_sync(kFull,
+                    mbar_wait(smem_addr(bars + k), (uint32_t)((it / S) & 1u), Q.wait_cycles))) {
       timed_out = true;
       break;
     }
@@ -154,9 +155,10 @@ __global__ void __launch_bounds__(NW * 32, 1) select_staged_kernel(SelectParams 
     flush_plane<4>(cnt, csa16(p, v), xk);
   }
   if (timed_out) {
-    // report, then wait (bounded again) for this warp's copies still in
-    // flight so that none lands after the block has left; the block still
-    // meets at the barrier below
+    // report, then wait (bounded by the fixed kBulkWaitCycles, whatever
+    // Q.wait_cycles is) for this warp's copies still in flight so that none
+    // lands after the block has left; the block still meets at the barrier
+    // below
     if (lane == 0 && Q.status) atomicExch(Q.status, POSPOP_ETIMEDOUT);
     for (uint64_t j = 0, c = c0 + it * TW; j < (uint64_t)S && c < nch; j++, c += TW)
       (void)mbar_wait(smem_addr(bars + (int)((it + j) % S)), (uint32_t)(((it + j) / S) & 1u));

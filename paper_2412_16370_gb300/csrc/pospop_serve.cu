@@ -70,16 +70,24 @@ struct Batch {
 };
 
 // Size classes: request bytes below kClassBound[k] (and not below the bound
-// before) go to class k; the last class takes the rest.
-constexpr int kServeClasses = 4;
+// before) go to class k; the last class takes the rest.  Each class has a
+// `serve` entry in the tune table (work-item rows at light load and
+// otherwise, batch streams running at once, requests per batch).
 constexpr size_t kClassBound[kServeClasses - 1] = {size_t(1) << 20, size_t(16) << 20,
                                                    size_t(128) << 20};
 // batches mix widths 8..64: they take the w = 32 batch entry of the tune table
+// (block shape, flush depth, load variant)
 constexpr int kServeWidthGroup = width_group(32);
-constexpr uint32_t kFineItemRows[2] = {8, 32};    // rows of 512 B, classes 0 and 1
-constexpr size_t kFineBelowBytes = 512ull << 20;  // in-flight bytes
-constexpr size_t kBatchCap = 1024;      // requests per batch (4 launches of kServeMax)
+constexpr size_t kBatchCap = 1024;      // requests per batch, at most (4 launches of kServeMax)
 constexpr uint64_t kMaxServeGrid = uint64_t(1) << 20;
+constexpr uint32_t kMinItemRows = 8;    // the shortest work item of a spread batch
+
+// The tune-table entries the loop works with (copied once per loop pass).
+struct LoopTune {
+  BatchTune bt;
+  ServeTune cls[kServeClasses];
+  uint64_t light;
+};
 
 int request_class(size_t nbytes, int levels) {
   int k = 0;
@@ -125,21 +133,43 @@ void free_batch(Batch &b) {
   cudaGetLastError();
 }
 
+uint64_t request_rows(const Request *r) {
+  if (r->nbytes == 0) return 0;
+  const uint64_t s0 = (uint64_t)r->dptr, e0 = s0 + r->nbytes;
+  const uint64_t G = (((e0 + 15u) & ~15ull) - (s0 & ~15ull)) >> 4;
+  return (G + 31u) >> 5;
+}
+
+// Work-item rows of a batch of `rows` rows of class `level`.  While the
+// server is lightly loaded, items are shorter, so that a request is spread
+// over many warps instead of a few (its latency is then a few short items):
+// the class's light_rows, or with light_rows 0 the fewest rows that still
+// give every resident warp of the GPU two items.  Under load the class's
+// `rows` stay, since the extra blocks would only delay the requests behind.
+uint32_t batch_item_rows(const pospop_server &srv, const LoopTune &lt, int level, uint64_t rows,
+                         size_t load_bytes) {
+  const ServeTune &st = lt.cls[level];
+  if (load_bytes >= lt.light) return st.rows;
+  if (st.light_rows > 0) return std::min(st.light_rows, st.rows);
+  const Variant &v = serve_variant(lt.bt.variant);
+  const uint64_t warps = (uint64_t)srv.ctx->sms * (uint64_t)srv.ctx->occ_serve[lt.bt.variant] *
+                         (uint64_t)(v.bs / 32);
+  const uint64_t want = (rows + 2 * warps - 1) / (2 * warps);
+  return (uint32_t)std::min<uint64_t>(st.rows, std::max<uint64_t>(kMinItemRows, want));
+}
+
 // Enqueue one batch of the requests in b.reqs on b.s (loop thread only):
 // one launch per kServeMax requests, then the batch event.  Requests are
 // ordered smallest first, so that small requests' work items come first.
-int launch_batch(pospop_server &srv, Batch &b, const BatchTune &bt, size_t load_bytes) {
+int launch_batch(pospop_server &srv, Batch &b, const LoopTune &lt, size_t load_bytes) {
   std::stable_sort(b.reqs.begin(), b.reqs.end(),
                    [](const Request *x, const Request *y) { return x->nbytes < y->nbytes; });
   const int n = (int)b.reqs.size();
   b.seq = b.seq + 1 == 0 ? 1 : b.seq + 1;
-  // While the server is lightly loaded, the two smallest classes' work
-  // items shrink to kFineItemRows, so that a small request is spread over
-  // many warps instead of a few (its latency is then one short item); under
-  // load the tuned item size stays, since the extra blocks would only delay
-  // the large requests behind them.
-  const uint32_t ir = (b.level < 2 && load_bytes < kFineBelowBytes)
-                          ? std::min(bt.item_rows, kFineItemRows[b.level]) : bt.item_rows;
+  uint64_t rows = 0;
+  for (const Request *r : b.reqs) rows += request_rows(r);
+  const uint32_t ir = batch_item_rows(srv, lt, b.level, rows, load_bytes);
+  const BatchTune &bt = lt.bt;
   const Variant &v = serve_variant(bt.variant);
   const uint64_t wpb = (uint64_t)v.bs / 32;
   static thread_local ServeParams P;   // about 8 KiB: not on the loop thread's stack
@@ -156,13 +186,7 @@ int launch_batch(pospop_server &srv, Batch &b, const BatchTune &bt, size_t load_
     uint64_t items = 0;
     for (int k = 0; k < cnt; k++) {
       const Request *r = b.reqs[k0 + k];
-      uint64_t it = 0;
-      if (r->nbytes > 0) {
-        const uint64_t s0 = (uint64_t)r->dptr, e0 = s0 + r->nbytes;
-        const uint64_t G = (((e0 + 15u) & ~15ull) - (s0 & ~15ull)) >> 4;
-        const uint64_t R = (G + 31u) >> 5;
-        it = (R + ir - 1) / ir;
-      }
+      const uint64_t it = (request_rows(r) + ir - 1) / ir;
       P.item_start[k] = items;
       P.req[k] = ServeReq{r->dptr, (uint64_t)r->nbytes, r->w, (uint32_t)it};
       items += it;
@@ -214,8 +238,15 @@ void serve_loop(pospop_server *srv) {
   uint32_t iter = 0;
   int64_t last_activity = now_ns();
   std::vector<std::pair<Batch *, std::vector<Request *>>> to_launch;
+  LoopTune lt{};
   while (true) {
     bool progress = false;
+    {
+      std::lock_guard<std::mutex> g(srv->ctx->mu);
+      lt.bt = srv->ctx->tune.batch[kServeWidthGroup];
+      for (int k = 0; k < kServeClasses; k++) lt.cls[k] = srv->ctx->tune.serve[k];
+      lt.light = srv->ctx->tune.serve_light;
+    }
     // 1. completions, without the lock: requests whose flag the device has
     //    raised, and whole batches whose event has fired (which frees the
     //    batch's stream and request slots; a request still unflagged then
@@ -287,16 +318,25 @@ void serve_loop(pospop_server *srv) {
         progress = true;
       }
       // 3. admitted requests go, by size class and in admission order, into
-      //    the next free batch of their class
+      //    the next free batch of their class (while fewer than the class's
+      //    `streams` batches are running; at most `cap` requests a batch)
       if (!srv->admitted.empty()) {
         Batch *free_b[kServeClasses] = {nullptr, nullptr, nullptr, nullptr};
-        for (Batch &b : srv->batches)
-          if (!b.busy && !free_b[b.level]) free_b[b.level] = &b;
+        uint32_t running[kServeClasses] = {0, 0, 0, 0};
+        for (Batch &b : srv->batches) {
+          if (b.busy)
+            running[b.level]++;
+          else if (!free_b[b.level])
+            free_b[b.level] = &b;
+        }
+        for (int k = 0; k < kServeClasses; k++)
+          if (running[k] >= lt.cls[k].streams) free_b[k] = nullptr;
         std::vector<Request *> take[kServeClasses];
         std::deque<Request *> keep;
         for (Request *r : srv->admitted) {
           const int k = request_class(r->nbytes, srv->levels);
-          if (free_b[k] && take[k].size() < kBatchCap)
+          const size_t cap = std::min<size_t>(kBatchCap, lt.cls[k].cap);
+          if (free_b[k] && take[k].size() < cap)
             take[k].push_back(r);
           else
             keep.push_back(r);
@@ -320,17 +360,12 @@ void serve_loop(pospop_server *srv) {
         srv->cv_loop.wait_for(lk, std::chrono::milliseconds(50));
     }
     // launches, without the lock
-    BatchTune bt{};
-    if (!to_launch.empty()) {
-      std::lock_guard<std::mutex> g(srv->ctx->mu);
-      bt = srv->ctx->tune.batch[kServeWidthGroup];
-    }
     for (auto &bl : to_launch) {
       Batch &b = *bl.first;
       b.reqs = std::move(bl.second);
       const int64_t tl = now_ns();
       for (Request *r : b.reqs) r->rec.t_launch_ns = tl;
-      const int rc = launch_batch(*srv, b, bt, load_bytes);
+      const int rc = launch_batch(*srv, b, lt, load_bytes);
       if (rc != POSPOP_OK) {
         // nothing of this batch reached the device in a usable state:
         // fail its requests (wait for what was enqueued before reusing it)

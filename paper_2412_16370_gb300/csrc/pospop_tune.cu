@@ -194,15 +194,16 @@ extern "C" int pospopcnt_autotune(size_t max_bytes, const char *path) {
       return cudaMemcpy(&h, dstatus, sizeof(int), cudaMemcpyDeviceToHost) == cudaSuccess && h == 0;
     };
     double best_ms = tm.time([&] {
-      return launch_roofline_with(*c, best.roof, buf, max_bytes, counts, dstatus, tm.s,
-                                  best.pdl != 0);
+      return launch_roofline_with(*c, best.roof, buf, max_bytes, counts, dstatus,
+                                  best.wait_cycles, tm.s, best.pdl != 0);
     });
     if (best_ms <= 0 || !status_ok()) best_ms = 1e30;
     for (int v = 0; v < roofline_variant_count(); v++)
       for (int cps = 1; cps <= 4 * c->occ_roof[v]; cps++) {
         const RoofTune rt{v, cps};
         const double ms = tm.time([&] {
-          return launch_roofline_with(*c, rt, buf, max_bytes, counts, dstatus, tm.s, best.pdl != 0);
+          return launch_roofline_with(*c, rt, buf, max_bytes, counts, dstatus, best.wait_cycles,
+                                      tm.s, best.pdl != 0);
         });
         if (!status_ok()) break;
         if (ms > 0 && ms < 0.99 * best_ms) {

@@ -63,3 +63,30 @@ def oracle_batch_parallel(orc, w: int, base: np.ndarray, offsets: np.ndarray, th
     with ThreadPoolExecutor(threads) as ex:
         list(ex.map(run, range(threads)))
     return out
+
+
+def oracle_batch_device(orc, widths, base: torch.Tensor, offsets: np.ndarray,
+                        chunk: int = 1 << 30, threads: int = 0):
+    """Oracle counts of every array of a batch resident on the device: the
+    arrays are copied back in runs of whole arrays of at most ``chunk`` bytes
+    (an array larger than ``chunk`` is a run of its own) and each run is
+    counted with oracle.batch on all host cores.  Returns {w: (m, w) uint64}."""
+    import os
+    threads = threads or max(1, os.cpu_count() or 1)
+    m = offsets.size - 1
+    out = {w: np.zeros((m, w), dtype=np.uint64) for w in widths}
+    span = int(max(chunk, int(np.diff(offsets).max()) if m else 0))
+    host = torch.empty(max(1, span), dtype=torch.uint8, pin_memory=True)
+    a0 = 0
+    while a0 < m:
+        # the longest run of arrays a0 .. a1-1 within `span` bytes (at least one)
+        a1 = int(np.searchsorted(offsets, offsets[a0] + span, side="right")) - 1
+        a1 = min(max(a1, a0 + 1), m)
+        lo, hi = int(offsets[a0]), int(offsets[a1])
+        h = host[:hi - lo]
+        h.copy_(base[lo:hi])
+        sub = (offsets[a0:a1 + 1] - offsets[a0]).astype(np.uint64)
+        for w in widths:
+            out[w][a0:a1] = oracle_batch_parallel(orc, w, h.numpy(), sub, threads)
+        a0 = a1
+    return out

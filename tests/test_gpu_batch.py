@@ -2,12 +2,11 @@
 
 The ragged one-hot workload: uint8 arrays, each byte with exactly one of 8
 bits set (Zipf(1.1) categories), sizes log-uniform on 1 B .. 4 MiB,
-concatenated back to back (so starts are unaligned).  A 20000-array subset is
-checked exactly against the oracle for every array; the full 200000-array
-batch (about 55 GB) is checked on every array through the one-hot property
-(counts of an array add up to its length) and exactly against the oracle on
-sampled arrays.  Also: every kernel variant and work-item size, zero-length
-arrays, decreasing offsets, and CUDA-graph replay.
+concatenated back to back (so starts are unaligned).  A 20000-array subset
+(every w) and the full 200000-array batch (about 55 GB; w = 8 and 16) are
+checked against the oracle on every array.  Also: every kernel variant and
+work-item size, zero-length arrays, decreasing offsets, and CUDA-graph
+replay, including a graph's own workspace outliving later calls.
 """
 import numpy as np
 import pytest
@@ -16,7 +15,7 @@ import torch
 from paper_2412_16370_gb300 import binding as pp
 from paper_2412_16370_gb300 import synth, synth_device
 
-from _gpu import WORD_W, counts_np, oracle_batch_parallel
+from _gpu import WORD_W, counts_np, oracle_batch_device, oracle_batch_parallel
 
 pytestmark = pytest.mark.gpu
 
@@ -67,31 +66,29 @@ def test_subset_every_array_exact(gpu, orc):
             assert np.array_equal(got.sum(axis=1), sizes.astype(np.uint64))
 
 
-def test_full_batch_one_hot_and_sampled(gpu, orc):
+def test_full_batch_every_array_exact(gpu, orc):
+    """The stated workload at full size: all 200000 arrays (about 55 GB),
+    every array compared with the oracle at w = 8 and w = 16."""
     m = 200000
     sizes, offs, base, offs_d = _one_hot_batch(gpu, m)
-    counts = torch.zeros((m, 8), dtype=torch.int64, device=gpu)
-    pp.pospopcnt_batch(8, counts, base, offs_d, m)
-    assert pp.pospopcnt_batch_status() == pp.POSPOP_OK
-    got = counts_np(counts)
-    # every byte has exactly one bit set: an array's counts add up to its length
-    assert np.array_equal(got.sum(axis=1), sizes.astype(np.uint64))
-    rng = np.random.default_rng(0)
-    sample = set(rng.choice(m, 1500, replace=False).tolist())
-    sample.update(np.argsort(sizes)[-40:].tolist())
-    sample.update([0, 1, m - 2, m - 1])
-    for a in sorted(sample):
-        lo, hi = int(offs[a]), int(offs[a + 1])
-        seg = base[lo:hi].cpu().numpy()
-        assert np.array_equal(got[a], orc.bytes(8, seg)), a
-    # w = 16 over the same batch: folding pairs of bytes
-    c16 = torch.zeros((m, 16), dtype=torch.int64, device=gpu)
-    pp.pospopcnt_batch(16, c16, base, offs_d, m)
-    g16 = counts_np(c16)
-    assert np.array_equal(g16.sum(axis=1), sizes.astype(np.uint64))
-    for a in sorted(sample)[:300]:
-        seg = base[int(offs[a]):int(offs[a + 1])].cpu().numpy()
-        assert np.array_equal(g16[a], orc.bytes(16, seg)), a
+    got = {}
+    for w in (8, 16):
+        counts = torch.zeros((m, w), dtype=torch.int64, device=gpu)
+        pp.pospopcnt_batch(w, counts, base, offs_d, m)
+        assert pp.pospopcnt_batch_status() == pp.POSPOP_OK
+        got[w] = counts_np(counts)
+        del counts
+    exp = oracle_batch_device(orc, (8, 16), base, offs)
+    for w in (8, 16):
+        bad = np.nonzero((got[w] != exp[w]).any(axis=1))[0]
+        assert bad.size == 0, (w, bad.size, bad[:5].tolist())
+        # every byte has exactly one bit set: an array's counts add up to its length
+        assert np.array_equal(got[w].sum(axis=1), sizes.astype(np.uint64)), w
+    # the device generator made the recipe's bytes (sampled windows)
+    total = int(offs[-1])
+    for s0 in (0, total // 2 + 7, total - 4096):
+        win = base[s0:s0 + 4096].cpu().numpy()
+        assert np.array_equal(win, synth.one_hot_bytes(4096, ONE_HOT_SEED, start=s0))
 
 
 def test_every_variant_and_item_size(gpu, orc, tune_override):
@@ -174,6 +171,75 @@ def test_graph_replay_matches_direct(gpu, orc):
             pp.pospopcnt_graph_launch(g, s)
         s.synchronize()
         assert np.array_equal(counts_np(c), 3 * exp)
+    finally:
+        pp.pospopcnt_graph_destroy(g)
+
+
+def test_graph_owns_its_workspace(gpu, orc):
+    """A graph made by pospopcnt_batch_graph_create keeps its own scratch:
+    a later, larger batch on the capture stream (which replaces that
+    stream's workspace) and a shutdown of the library leave it valid."""
+    m = 2000
+    sizes = synth.log_uniform_sizes(m, 1, 1 << 18, seed=14)
+    sizes[::97] = 0
+    offs = synth.csr_offsets(sizes)
+    host = synth.random_bytes(int(offs[-1]) + 7, seed=15)
+    dbuf = torch.from_numpy(host).to(gpu)
+    base = dbuf[7:]
+    offs_d = torch.from_numpy(offs.view(np.int64)).to(gpu)
+    exp = orc.batch(16, host[7:], offs)
+    s = torch.cuda.Stream()
+    c = torch.zeros((m, 16), dtype=torch.int64, device=gpu)
+    pp.pospopcnt_batch(16, c, base, offs_d, m, s)   # the stream's own workspace exists
+    s.synchronize()
+    g = pp.pospopcnt_batch_graph_create(16, c, base, offs_d, stream=s)
+    try:
+        addr0, size0 = pp.pospopcnt_graph_workspace(g)
+        assert addr0 != 0 and size0 >= 8 * (m + 1)
+        s.synchronize()
+        c.zero_()
+        torch.cuda.synchronize()
+        # a batch with many more arrays on the same stream grows (replaces)
+        # the stream's workspace
+        big_m = 300000
+        bsz = synth.log_uniform_sizes(big_m, 1, 64, seed=16)
+        boffs = synth.csr_offsets(bsz)
+        bbase = torch.zeros(int(boffs[-1]) + 16, dtype=torch.uint8, device=gpu)
+        bc = torch.zeros((big_m, 8), dtype=torch.int64, device=gpu)
+        pp.pospopcnt_batch(8, bc, bbase, torch.from_numpy(boffs.view(np.int64)).to(gpu), big_m, s)
+        assert pp.pospopcnt_batch_status(s) == pp.POSPOP_OK
+        pp.pospopcnt_graph_launch(g, s)
+        s.synchronize()   # replays of one graph must not overlap
+        pp.pospopcnt_graph_launch(g, torch.cuda.current_stream())   # any stream
+        assert pp.pospopcnt_graph_status(g) == pp.POSPOP_OK
+        # and a shutdown of the library (which frees every stream workspace)
+        pp.shutdown()
+        pp.init(0)
+        pp.pospopcnt_graph_launch(g, s)
+        assert pp.pospopcnt_graph_status(g) == pp.POSPOP_OK
+        torch.cuda.synchronize()
+        assert np.array_equal(counts_np(c), 3 * exp)
+        assert pp.pospopcnt_graph_workspace(g) == (addr0, size0)
+    finally:
+        pp.pospopcnt_graph_destroy(g)
+
+
+def test_graph_reports_decreasing_offsets(gpu):
+    offs = torch.tensor([0, 10, 30, 20, 40], dtype=torch.int64, device=gpu)
+    base = torch.ones(64, dtype=torch.uint8, device=gpu)
+    c = torch.full((4, 8), 7, dtype=torch.int64, device=gpu)
+    s = torch.cuda.Stream()
+    g = pp.pospopcnt_batch_graph_create(8, c, base, offs, 4, s)
+    try:
+        pp.pospopcnt_graph_launch(g, s)
+        assert pp.pospopcnt_graph_status(g) == pp.POSPOP_EINVAL
+        assert (c == 7).all()
+        assert pp.pospopcnt_graph_status(g) == pp.POSPOP_OK   # cleared once read
+        offs[3] = 30
+        pp.pospopcnt_graph_launch(g, s)
+        assert pp.pospopcnt_graph_status(g) == pp.POSPOP_OK
+        torch.cuda.synchronize()
+        assert c.sum().item() == 4 * 8 * 7 + 40
     finally:
         pp.pospopcnt_graph_destroy(g)
 

@@ -39,7 +39,10 @@ def test_per_width_and_every_width_entries(pp, tmp_path):
         lines.append(f"stream {w} 1 128 4 32 0 3 1")    # one width group
         lines.append(f"batch {w} 512 1 16 1 1 127 1")
     lines += ["batch 256 2 16 0 2 63 4", "pdl 0", "staged 0", "short 1", "split 1024",
-              "roofline 256 1 18", "stream 4 512 1 16 0 3 1   # trailing comment"]
+              "roofline 256 1 18", "wait 0", "wait 2147483648",
+              "serve 0 8 127 64 1024", "serve 3 0 127 1 1", "serve_light 0",
+              "serve_light 536870912",
+              "stream 4 512 1 16 0 3 1   # trailing comment"]
     assert _check(pp, tmp_path, "\n".join(lines) + "\n") == 0
     assert _check(pp, tmp_path, "\r\n".join(lines) + "\r\n") == 0   # CRLF line ends
 
@@ -64,6 +67,13 @@ def test_per_width_and_every_width_entries(pp, tmp_path):
     "pdl 2", "pdl 1 1", "pdl", "pdl -1", "short 2", "short 1 x", "split 0", "split 67108865",
     "split 4 x", "staged 99", "staged", "roofline 300 1 4", "roofline 256 1",
     "roofline 256 1 18 5", "roofline 256 1 0", "bogus 1",
+    "wait -1", "wait 2147483649", "wait", "wait 5 5", "wait x",
+    "serve 4 8 127 8 1024",              # no such serving class
+    "serve 0 8 0 8 1024",                # rows below 1
+    "serve 0 8 127 0 1024",              # streams below 1
+    "serve 0 8 127 65 1024",             # streams above 64
+    "serve 0 8 127 8 1025",              # batch cap above 1024
+    "serve 0 8 127 8", "serve_light", "serve_light -5",
 ])
 def test_malformed_line_is_reported_with_its_number(pp, tmp_path, bad):
     text = "# header\nstream 0 256 2 16 1 1 2\n\n" + bad + "\npdl 1\n"
