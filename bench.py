@@ -20,6 +20,9 @@ also carries:
   the oracle's time;
 * short: microseconds per call for short unaligned arrays, one launch each,
   plain and graph-replayed;
+* multi: several counts in one launch (pospopcnt_multi): the plain
+  configuration queued 16 counts a launch, and four 1 GiB arrays in one
+  launch against four single launches;
 * serving: the continuous-batching server on Poisson request streams at
   0.3 / 0.6 / 0.9 of the large-array rate, GB/s and p50/p99 latency;
 * masked: the WHERE-selected count on the 8 GiB array as 32-bit words;
@@ -423,6 +426,8 @@ def run_ours(args):
                                                          achieved, hbm_peak, m=args.batched_m)),
                             ("plain", lambda: _plain(pp, synth_device, dev, stream)),
                             ("short", lambda: _short(pp, synth, synth_device, dev, stream)),
+                            ("multi", lambda: _multi(pp, synth_device, data, nbytes, dev, stream,
+                                                     hbm_peak)),
                             ("serving", lambda: _serving(pp, synth, data, nbytes, achieved, dev)),
                             ("masked", lambda: _masked(pp, synth_device, data, nbytes, dev,
                                                        stream, achieved, hbm_peak)),
@@ -766,6 +771,68 @@ def _short(pp, synth, synth_device, dev, stream, n=2000):
                     "through the C entry point with prepared arguments"}
 
 
+def _multi(pp, synth_device, data, nbytes, dev, stream, hbm_peak, group=16):
+    """pospopcnt_multi through the C entry point with prepared arguments:
+    (1) the plain configuration (524288 uint16 words, 1 MiB, seed 0, w = 16)
+    counted `group` times per launch, each into its own counters, device
+    microseconds per count (L2-resident, like the plain section); (2) four
+    1 GiB arrays (the first 4 GiB of the resident array, w = 8, 16, 32, 64)
+    in one launch, against the same four counts as four single launches."""
+    import ctypes
+    import torch
+    import oracle
+    L = pp.lib()
+    n = 524288
+    words = torch.empty(2 * n, dtype=torch.uint8, device=dev)
+    synth_device.random_(words, 0)
+    c = torch.zeros((group, 16), dtype=torch.int64, device=dev)
+    W = (ctypes.c_int * group)(*([16] * group))
+    C = (ctypes.c_uint64 * group)(*[c[i].data_ptr() for i in range(group)])
+    P = (ctypes.c_uint64 * group)(*([words.data_ptr()] * group))
+    N = (ctypes.c_size_t * group)(*([2 * n] * group))
+    sp = stream.cuda_stream
+    calls = []
+    ms = _time_ms(lambda: L.pospopcnt_multi(group, W, C, P, N, sp), stream, reps=200, calls=calls)
+    orc = oracle.load()
+    exp = orc.typed(16, words.cpu().numpy().view(np.uint16))
+    got = c.cpu().numpy().view(np.uint64)
+    ok_plain = bool(all(np.array_equal(got[i], exp * np.uint64(calls[0])) for i in range(group)))
+    out = {"plain_group": {
+        "workload": f"{group} counts of the plain configuration (1 MiB of uint16 words, w=16) "
+                    "per launch, each into its own counters",
+        "device_us_per_launch": round(ms * 1e3, 2), "device_us_per_count": round(ms * 1e3 / group, 3),
+        "GBps": round(group * 2 * n / (ms / 1e3) / 1e9, 1), "counts_ok": ok_plain}}
+    if nbytes >= 4 * GIB:
+        ws = (8, 16, 32, 64)
+        c4 = torch.zeros((4, 64), dtype=torch.int64, device=dev)
+        W4 = (ctypes.c_int * 4)(*ws)
+        C4 = (ctypes.c_uint64 * 4)(*[c4[i].data_ptr() for i in range(4)])
+        P4 = (ctypes.c_uint64 * 4)(*[data.data_ptr() + i * GIB for i in range(4)])
+        N4 = (ctypes.c_size_t * 4)(*([GIB] * 4))
+        ms_multi = _time_ms(lambda: L.pospopcnt_multi(4, W4, C4, P4, N4, sp), stream, reps=10)
+
+        def singles():
+            for i, w in enumerate(ws):
+                L.pospopcnt_async(w, c4[i].data_ptr(), data.data_ptr() + i * GIB, GIB, sp)
+
+        ms_single = _time_ms(singles, stream, reps=10)
+        # the two ways agree count for count (the same calls, so the same totals)
+        c4.zero_()
+        L.pospopcnt_multi(4, W4, C4, P4, N4, sp)
+        a = c4.clone()
+        c4.zero_()
+        singles()
+        torch.cuda.synchronize()
+        gm = 4 * GIB / (ms_multi / 1e3) / 1e9
+        gs = 4 * GIB / (ms_single / 1e3) / 1e9
+        out["four_1GiB"] = {"workload": "the first 4 GiB of the resident array as four 1 GiB "
+                                        "counts (w = 8, 16, 32, 64)",
+                            "multi_GBps": round(gm, 1), "single_launches_GBps": round(gs, 1),
+                            "multi_frac_of_hbm_peak": round(gm / hbm_peak, 4),
+                            "same_counts": bool(torch.equal(a, c4))}
+    return out
+
+
 def _serving(pp, synth, pool, pool_bytes, large_gbs, dev, loads=(0.3, 0.6, 0.9),
              duration_s=0.3, budget=32 << 30):
     """Poisson request streams at fractions of the large-array rate, served by
@@ -1039,8 +1106,8 @@ def main():
                     help="skip every section after the headline (e2e, batched, plain, "
                          "short, serving, masked, gather, cpu_baseline, sweep)")
     ap.add_argument("--sections", default="",
-                    help="comma list of extra sections to run "
-                         "(e2e,batched,plain,short,serving,masked,gather,cpu_baseline,sweep)")
+                    help="comma list of extra sections to run (e2e,batched,plain,short,multi,"
+                         "serving,masked,gather,cpu_baseline,sweep)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")

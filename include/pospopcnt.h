@@ -107,6 +107,22 @@ int pospopcnt_batch(int w, uint64_t *counts, const void *base, const uint64_t *o
                     size_t m, void *stream);
 
 /*
+ * Several independent counts in one launch (each Fig. 2 / Section 1's
+ * byte-length count): for i < n, counts[i][0..w[i]-1] += the width-w[i]
+ * count of the nbytes[i] bytes at ptrs[i] (any alignment; a trailing partial
+ * word zero-padded).  w, counts, ptrs and nbytes are HOST arrays of n
+ * entries; counts[i] and ptrs[i] are device-addressable pointers (counts may
+ * alias: counts into one counter array add up).  Widths 1 .. 64.  The work
+ * is planned on the host and passed in the kernel's parameter block (no
+ * upload, no planning kernels), up to 256 counts per launch (more are split
+ * into several launches), so a group of small counts costs about one launch
+ * instead of one each.  Every entry is checked before anything is enqueued;
+ * on an error nothing is counted.  Asynchronous on `stream`.
+ */
+int pospopcnt_multi(size_t n, const int *w, uint64_t *const *counts, const void *const *ptrs,
+                    const size_t *nbytes, void *stream);
+
+/*
  * Gathered regions (Section 4, step 1 and its footnote: leaving the
  * counters uncleared lets non-contiguous memory regions be counted into one
  * counter array): counts[0..w-1] += the counts of the n regions
@@ -302,6 +318,34 @@ typedef struct pospop_completion {
  * 1 <= max_inflight <= 2^20, 1 <= max_batches <= 64. */
 int pospop_server_create(size_t mem_budget, int max_inflight, int max_batches,
                          pospop_server **out);
+
+/* A server as pospop_server_create, that also owns a device staging pool of
+ * mem_budget bytes, allocated here once and freed by pospop_server_destroy,
+ * for requests whose input is in host memory (pospop_server_submit_host).
+ * Such a request is admitted only when a contiguous range of the pool (first
+ * fit, in 256-byte granules) is free for it, as well as the budget and slot
+ * conditions above, so the budget bounds device memory that is really
+ * allocated.  Once admitted, the server's uploader thread copies the input
+ * into its range (cudaMemcpyAsync on the server's copy stream), the request's
+ * batch waits for that copy, and the range is released when the request
+ * completes.  POSPOP_ENOMEM if the pool cannot be allocated. */
+int pospop_server_create_pooled(size_t mem_budget, int max_inflight, int max_batches,
+                                pospop_server **out);
+
+/* Queue one request whose nbytes of input are in HOST memory at `bytes`
+ * (pinned or pageable; it must stay valid and unchanged until the request
+ * completes): staged into the server's pool, then counted as by
+ * pospop_server_submit.  Only for a server made by
+ * pospop_server_create_pooled (else POSPOP_EINVAL); nbytes > mem_budget
+ * returns POSPOP_ERANGE; a device or managed pointer returns POSPOP_EPTR.
+ * Never blocks. */
+int pospop_server_submit_host(pospop_server *s, int w, const void *bytes, size_t nbytes,
+                              uint64_t *result, uint64_t *id);
+
+/* Staging pool of a pooled server: stats[0] its bytes, stats[1] bytes held
+ * by admitted, unfinished host requests now, stats[2] the most ever held at
+ * once (never more than stats[0]).  All zero for a server without a pool. */
+int pospop_server_pool_stats(pospop_server *s, uint64_t stats[3]);
 
 /* Queue one request: count the nbytes device-addressable bytes at `bytes`
  * with width w (1, 2, 4, 8, 16, 32, 64).  When it completes, result[0..w-1]

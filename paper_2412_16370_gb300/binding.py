@@ -51,6 +51,7 @@ _SIGNATURES = {
     "pospopcnt_batch": ([_int, _vp, _vp, _vp, _sz, _vp], _int),
     "pospopcnt_batch_noalloc": ([_int, _vp, _vp, _vp, _sz, _vp], _int),
     "pospopcnt_gather": ([_int, _vp, _vp, _vp, _sz, _vp], _int),
+    "pospopcnt_multi": ([_sz, _vp, _vp, _vp, _vp, _vp], _int),
     "pospopcnt_masked": ([_int, _vp, _vp, _sz, _vp, _vp], _int),
     "pospopcnt_batch_status": ([_vp], _int),
     "pospopcnt_reserve": ([_sz, _vp], _int),
@@ -69,6 +70,10 @@ _SIGNATURES = {
     "pospopcnt_launch_count": ([], ctypes.c_uint64),
     "pospop_server_create": ([_sz, _int, _int, ctypes.POINTER(_vp)], _int),
     "pospop_server_submit": ([_vp, _int, _vp, _sz, _vp, ctypes.POINTER(ctypes.c_uint64)], _int),
+    "pospop_server_create_pooled": ([_sz, _int, _int, ctypes.POINTER(_vp)], _int),
+    "pospop_server_submit_host": ([_vp, _int, _vp, _sz, _vp, ctypes.POINTER(ctypes.c_uint64)],
+                                  _int),
+    "pospop_server_pool_stats": ([_vp, ctypes.POINTER(ctypes.c_uint64)], _int),
     "pospop_server_poll": ([_vp, _vp, _int, _int], _int),
     "pospop_server_drain": ([_vp, _int], _int),
     "pospop_server_stats": ([_vp, ctypes.POINTER(ctypes.c_uint64)], _int),
@@ -202,6 +207,22 @@ def pospopcnt_batch_noalloc(w: int, counts, base, offsets, m=None, stream=None):
                                                 _stream(stream)))
 
 
+def pospopcnt_multi(widths, counts, ptrs, nbytes, stream=None):
+    """Several independent counts in one launch: widths[i], counter address
+    counts[i], input address ptrs[i] and length nbytes[i] (sequences of
+    ints, or tensors / arrays for the addresses)."""
+    import numpy as np
+    n = len(widths)
+    w = np.ascontiguousarray(widths, dtype=np.int32)
+    c = np.ascontiguousarray([_ptr(x) for x in counts], dtype=np.uint64)
+    p = np.ascontiguousarray([_ptr(x) for x in ptrs], dtype=np.uint64)
+    nb = np.ascontiguousarray(nbytes, dtype=np.uint64)
+    if not (len(c) == len(p) == len(nb) == n):
+        raise ValueError("widths, counts, ptrs and nbytes differ in length")
+    return _check(lib().pospopcnt_multi(n, w.ctypes.data, c.ctypes.data, p.ctypes.data,
+                                        nb.ctypes.data, _stream(stream)))
+
+
 def pospopcnt_gather(w: int, counts, ptrs, lens, n=None, stream=None):
     """Count n device regions (device arrays of start addresses and lengths) into one counter array."""
     if n is None:
@@ -309,6 +330,32 @@ def pospop_server_create(mem_budget: int, max_inflight: int = 4096, max_batches:
     h = _vp()
     _check(lib().pospop_server_create(mem_budget, max_inflight, max_batches, ctypes.byref(h)))
     return h.value
+
+
+def pospop_server_create_pooled(mem_budget: int, max_inflight: int = 4096,
+                                max_batches: int = 4) -> int:
+    """A server with a device staging pool of mem_budget bytes for host input."""
+    h = _vp()
+    _check(lib().pospop_server_create_pooled(mem_budget, max_inflight, max_batches,
+                                             ctypes.byref(h)))
+    return h.value
+
+
+def pospop_server_submit_host(server: int, w: int, data, nbytes=None, result=None) -> int:
+    """Queue a request whose input is host memory (numpy array, CPU tensor or address)."""
+    if nbytes is None:
+        nbytes = _nbytes(data)
+    rid = ctypes.c_uint64()
+    _check(lib().pospop_server_submit_host(server, w, _ptr(data), nbytes, _ptr(result),
+                                           ctypes.byref(rid)))
+    return rid.value
+
+
+def pospop_server_pool_stats(server: int) -> tuple[int, int, int]:
+    """(pool bytes, bytes held now, most bytes ever held at once)."""
+    out = (ctypes.c_uint64 * 3)()
+    _check(lib().pospop_server_pool_stats(server, out))
+    return tuple(int(x) for x in out)
 
 
 def pospop_server_submit(server: int, w: int, data, nbytes=None, result=None) -> int:

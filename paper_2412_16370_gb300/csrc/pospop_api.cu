@@ -8,6 +8,7 @@
 #include <dlfcn.h>
 
 #include <algorithm>
+#include <cstddef>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -82,7 +83,7 @@ TuneTable default_tune() {
   const uint32_t minrows[kClasses] = {2, 4, 8, 16, 16};
   for (int g = 0; g < kWidthGroups; g++) {
     for (int c = 0; c < kClasses; c++) t.stream[g][c] = StreamTune{sv, 1, minrows[c]};
-    t.batch[g] = BatchTune{find_variant(true, 256, 2, 16, 1), 2, 511, 1};
+    t.batch[g] = BatchTune{find_variant(true, 256, 2, 16, 1), 2, {511, 511, 511, 511}, 1};
   }
   t.roof = RoofTune{find_roof_variant(512, 1), 4};
   t.max_rows_per_warp = kMaxRowsPerWarp;
@@ -90,11 +91,13 @@ TuneTable default_tune() {
   t.pdl = 1;
   t.staged = 3;   // 16 warps x 1 stage: measured fastest on GB300
   t.wait_cycles = kBulkWaitCycles;
-  // serving: small classes split into short items while lightly loaded
+  // serving (measured on GB300, Poisson traces at 0.3 / 0.6 / 0.9 of the
+  // large-array rate): longer items for the larger classes under load, short
+  // wave-aligned items while lightly loaded
   t.serve[0] = ServeTune{8, 127, 64, 1024};
-  t.serve[1] = ServeTune{32, 127, 64, 1024};
-  t.serve[2] = ServeTune{0, 127, 64, 1024};
-  t.serve[3] = ServeTune{0, 127, 64, 1024};
+  t.serve[1] = ServeTune{32, 255, 64, 1024};
+  t.serve[2] = ServeTune{127, 511, 64, 1024};
+  t.serve[3] = ServeTune{127, 511, 64, 1024};
   t.serve_light = uint64_t(512) << 20;
   t.set_source("built-in defaults");
   return t;
@@ -105,7 +108,12 @@ TuneTable default_tune() {
 //   batch [<w>] <bs> <minb> <depth> <hint> <ctas_per_sm> <item_rows> <grab>
 //                                 (<w> in {8, 16, 32, 64} sets the entry of that
 //                                  width group: 8 stands for w <= 8, 64 for
-//                                  w >= 64; without it the entry is every group's)
+//                                  w >= 64; without it the entry is every group's;
+//                                  item_rows is every array size class's)
+//   batch_rows [<w>] <r0> <r1> <r2> <r3>
+//                                 (work-item rows of arrays of at most 2 KiB, 32 KiB,
+//                                  1 MiB, and above, 1 .. 2^20; after the batch line
+//                                  of the same width groups)
 //   roofline <bs> <hint> <ctas_per_sm>
 //   split <max_rows_per_warp>     (1 .. 2^26; a single-array count is split into
 //                                  several launches so that no warp takes more)
@@ -119,10 +127,11 @@ TuneTable default_tune() {
 //                                  3 = 16 x 1; 0 = loads into registers)
 //   serve <class> <light_rows> <rows> <streams> <cap>
 //                                 (serving size class 0..3 = below 1 MiB, 16 MiB,
-//                                  128 MiB, above: work-item rows while lightly loaded
-//                                  (0 = spread the batch over every SM) and otherwise
-//                                  (1 .. 2^20), batch streams of the class running at
-//                                  once (1 .. 64), requests per batch (1 .. 1024))
+//                                  128 MiB, above: most work-item rows while lightly
+//                                  loaded (0 = rows; items are wave-aligned, at least
+//                                  half that) and rows otherwise (1 .. 2^20), batch
+//                                  streams of the class running at once (1 .. 64),
+//                                  requests per batch (1 .. 1024))
 //   serve_light <bytes>           (in-flight input bytes below which the server counts
 //                                  as lightly loaded)
 //   wait <cycles>                 (0 .. 2^31: how long a staged kernel waits for a
@@ -200,9 +209,20 @@ int parse_tune(const char *text, TuneTable *out, int *bad_line) {
         const int v = find_variant(true, (int)f[0], (int)f[1], (int)f[2], (int)f[3]);
         if (v < 0 || f[4] < 1 || f[5] < 1 || f[5] > (1 << 20) || f[6] < 1 || f[6] > 64)
           return POSPOP_EINVAL;
+        const uint32_t ir = (uint32_t)f[5];
         for (int g = g0; g < g1; g++)
-          t.batch[g] = BatchTune{v, (int)f[4], (uint32_t)f[5], (uint32_t)f[6]};
+          t.batch[g] = BatchTune{v, (int)f[4], {ir, ir, ir, ir}, (uint32_t)f[6]};
       }
+    } else if (strcmp(kind, "batch_rows") == 0) {
+      int g0 = 0, g1 = 0;
+      if ((n != kBatchClasses && n != kBatchClasses + 1) ||
+          !tune_groups(a[0], n == kBatchClasses + 1, &g0, &g1))
+        return POSPOP_EINVAL;
+      const long long *f = a + (n - kBatchClasses);
+      for (int c = 0; c < kBatchClasses; c++)
+        if (f[c] < 1 || f[c] > (1 << 20)) return POSPOP_EINVAL;
+      for (int g = g0; g < g1; g++)
+        for (int c = 0; c < kBatchClasses; c++) t.batch[g].item_rows[c] = (uint32_t)f[c];
     } else if (strcmp(kind, "short") == 0) {
       if (n != 1 || a[0] < 0 || a[0] > 1) return POSPOP_EINVAL;
       t.regroup = (uint32_t)a[0];
@@ -274,11 +294,13 @@ std::string format_tune(const DevCtx &ctx, const TuneTable &t) {
   }
   {
     s += "# batch [<w>] <bs> <minb> <depth> <hint> <ctas_per_sm> <item_rows> <grab>\n";
+    s += "# batch_rows [<w>] <rows: arrays <= 2 KiB> <<= 32 KiB> <<= 1 MiB> <above>>\n";
     bool same = true;
     for (int g = 1; g < kWidthGroups; g++) {
       const BatchTune &a = t.batch[0], &b = t.batch[g];
       same = same && a.variant == b.variant && a.ctas_per_sm == b.ctas_per_sm &&
-             a.item_rows == b.item_rows && a.grab == b.grab;
+             a.grab == b.grab;
+      for (int c = 0; c < kBatchClasses; c++) same = same && a.item_rows[c] == b.item_rows[c];
     }
     for (int g = 0; g < (same ? 1 : kWidthGroups); g++) {
       const BatchTune &e = t.batch[g];
@@ -286,8 +308,15 @@ std::string format_tune(const DevCtx &ctx, const TuneTable &t) {
       char wfield[16] = "";
       if (!same) snprintf(wfield, sizeof wfield, "%d ", kGroupWidth[g]);
       snprintf(line, sizeof line, "batch %s%d %d %d %d %d %u %u\n", wfield, v.bs, v.minb, v.depth,
-               v.hint, e.ctas_per_sm, e.item_rows, e.grab);
+               v.hint, e.ctas_per_sm, e.item_rows[kBatchClasses - 1], e.grab);
       s += line;
+      bool uniform = true;
+      for (int c = 0; c < kBatchClasses; c++) uniform = uniform && e.item_rows[c] == e.item_rows[0];
+      if (!uniform) {
+        snprintf(line, sizeof line, "batch_rows %s%u %u %u %u\n", wfield, e.item_rows[0],
+                 e.item_rows[1], e.item_rows[2], e.item_rows[3]);
+        s += line;
+      }
     }
   }
   snprintf(line, sizeof line, "# short <0 transpose | 1 per-lane regroup> (w = 8, <= 3 rows)\nshort %u\n",
@@ -764,7 +793,7 @@ int launch_batch_scratch(const DevCtx &ctx, const TuneTable &t, int w, unsigned 
   pp.block_sum = scr.block_sum;
   pp.next = scr.next;
   pp.status = scr.status;
-  pp.item_rows = bt.item_rows;
+  memcpy(pp.item_rows, bt.item_rows, sizeof pp.item_rows);
   pp.nblocks = (uint32_t)((m + kPlanChunk - 1) / kPlanChunk);
   int rc = launch_plan(plan_items_fn(), pp, stream, t.pdl != 0);
   if (rc != POSPOP_OK) return rc;
@@ -780,7 +809,7 @@ int launch_batch_scratch(const DevCtx &ctx, const TuneTable &t, int w, unsigned 
   bp.item_start = scr.item_start;
   bp.next = scr.next;
   bp.status = scr.status;
-  bp.item_rows = bt.item_rows;
+  memcpy(bp.item_rows, bt.item_rows, sizeof bp.item_rows);
   bp.grab = bt.grab;
   bp.regroup = t.regroup;
   const Variant *vp = &batch_variant(bt.variant);
@@ -831,7 +860,7 @@ static int launch_gather_with(DevCtx &ctx, const TuneTable &t, int w, unsigned l
   pp.block_sum = scr.block_sum;
   pp.next = scr.next;
   pp.status = scr.status;
-  pp.item_rows = bt.item_rows;
+  memcpy(pp.item_rows, bt.item_rows, sizeof pp.item_rows);
   pp.nblocks = (uint32_t)((n + kPlanChunk - 1) / kPlanChunk);
   const int prc = launch_plan(plan_items_gather_fn(), pp, stream, t.pdl != 0);
   if (prc != POSPOP_OK) return prc;
@@ -845,7 +874,7 @@ static int launch_gather_with(DevCtx &ctx, const TuneTable &t, int w, unsigned l
   bp.item_start = scr.item_start;
   bp.next = scr.next;
   bp.status = scr.status;
-  bp.item_rows = bt.item_rows;
+  memcpy(bp.item_rows, bt.item_rows, sizeof bp.item_rows);
   bp.grab = bt.grab;
   bp.regroup = t.regroup;
   const Variant *vp = &gather_variant(bt.variant);
@@ -1221,6 +1250,78 @@ int pospopcnt_masked(int w, uint64_t *counts, const void *words, size_t n, const
   }
   return launch_select_with(*c, t, w, (unsigned long long *)const_cast<void *>(dc), dw, n, ds,
                             static_cast<cudaStream_t>(stream));
+}
+
+int pospopcnt_multi(size_t n, const int *w, uint64_t *const *counts, const void *const *ptrs,
+                    const size_t *nbytes, void *stream) {
+  if (n == 0) return POSPOP_OK;
+  if (!w || !counts || !ptrs || !nbytes) return POSPOP_EINVAL;
+  int rc = POSPOP_OK;
+  DevCtx *c = current_ctx(&rc);
+  if (!c) return rc;
+  // every count is checked before anything is launched
+  std::vector<ServeReq> reqs;
+  reqs.reserve(n);
+  uint64_t rows = 0;
+  for (size_t i = 0; i < n; i++) {
+    if (!valid_w(w[i])) return POSPOP_EINVAL;
+    if (nbytes[i] == 0) continue;
+    if (!counts[i] || !ptrs[i]) return POSPOP_EINVAL;
+    const void *dc = nullptr, *dp = nullptr;
+    if (!device_addressable(counts[i], c->device, &dc) ||
+        !device_addressable(ptrs[i], c->device, &dp))
+      return POSPOP_EPTR;
+    ServeReq r;
+    r.ptr = dp;
+    r.nbytes = nbytes[i];
+    r.w = w[i];
+    r.items = 0;
+    r.out = (unsigned long long *)const_cast<void *>(dc);
+    reqs.push_back(r);
+    rows += serve_rows(dp, nbytes[i]);
+  }
+  if (reqs.empty()) return POSPOP_OK;
+  TuneTable t;
+  {
+    std::lock_guard<std::mutex> g(c->mu);
+    t = c->tune;
+  }
+  // the launch shape of the w = 32 batch entry (counts mix widths); work
+  // items of at most kMultiItemRows rows and at least 8, wave-aligned over
+  // the whole group, so that a group of small counts still spreads over the
+  // GPU and a group of large ones runs in whole waves
+  constexpr uint32_t kMultiItemRows = 127;
+  const int vi = t.batch[width_group(32)].variant;
+  const Variant &v = multi_variant(vi);
+  const uint32_t ir = serve_light_rows(*c, vi, rows, kMultiItemRows, 8);
+  static thread_local ServeParams P;   // about 10 KiB: not on the caller's stack
+  memset(&P, 0, offsetof(ServeParams, req));
+  P.item_rows = ir;
+  const uint64_t wpb = (uint64_t)v.bs / 32;
+  for (size_t k0 = 0; k0 < reqs.size(); k0 += kServeMax) {
+    const size_t cnt = std::min<size_t>(kServeMax, reqs.size() - k0);
+    uint64_t items = 0;
+    for (size_t k = 0; k < cnt; k++) {
+      ServeReq r = reqs[k0 + k];
+      r.items = (uint32_t)((serve_rows(r.ptr, r.nbytes) + ir - 1) / ir);
+      P.item_start[k] = items;
+      P.req[k] = r;
+      items += r.items;
+    }
+    P.item_start[cnt] = items;
+    P.n = (uint32_t)cnt;
+    P.total = items;
+    // one work item per warp (the kernel's grid-stride loop covers a cap)
+    const uint64_t grid = std::min<uint64_t>((items + wpb - 1) / wpb, uint64_t(1) << 20);
+    void *args[] = {&P};
+    if (launch_kernel(v.fn, dim3((unsigned)grid), dim3(v.bs), args,
+                      static_cast<cudaStream_t>(stream), t.pdl != 0) != cudaSuccess) {
+      cudaGetLastError();
+      return POSPOP_ECUDA;
+    }
+    note_launches(1);
+  }
+  return POSPOP_OK;
 }
 
 int pospopcnt_batch_status(void *stream) {

@@ -39,15 +39,17 @@ __device__ __forceinline__ ArrayRef array_ref(const BatchParams &P, uint64_t a) 
 
 // ---------------------------------------------------------------------------
 // Planning.  Array a spans granules [s/16, ceil(e/16)); its rows of 32
-// granules are cut into work items of item_rows rows.  item_start is the
-// exclusive prefix sum of the items per array.  Decreasing CSR offsets set
-// the status and give the array no items.
+// granules are cut into work items of item_rows[batch_class(rows)] rows.
+// item_start is the exclusive prefix sum of the items per array.  Decreasing
+// CSR offsets set the status and give the array no items.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ uint64_t span_items(uint64_t s, uint64_t e, uint32_t item_rows) {
+__device__ __forceinline__ uint64_t span_items(uint64_t s, uint64_t e,
+                                               const uint32_t (&item_rows)[kBatchClasses]) {
   if (e <= s) return 0;
   const uint64_t G = (((e + 15u) & ~15ull) - (s & ~15ull)) >> 4;
   const uint64_t R = (G + 31u) >> 5;
-  return (R + item_rows - 1) / item_rows;
+  const uint32_t ir = item_rows[batch_class(R)];
+  return (R + ir - 1) / ir;
 }
 
 // Inclusive block-wide scan of one value per thread (kPlanThreads threads).
@@ -232,8 +234,9 @@ __global__ void __launch_bounds__(BS, MINB) batch_kernel(BatchParams P) {
       s.tail = (uint32_t)(r.e - (A + 16u * (s.G - 1)));
       const uint32_t rot = (8u * s.head) & (uint32_t)(r.w - 1);
       const uint64_t R = span_rows(s);
-      const uint64_t r0 = k * P.item_rows;
-      const uint64_t r1 = (r0 + P.item_rows < R) ? r0 + P.item_rows : R;
+      const uint32_t ir = P.item_rows[batch_class(R)];
+      const uint64_t r0 = k * ir;
+      const uint64_t r1 = (r0 + ir < R) ? r0 + ir : R;
       unsigned long long *out = r.out;
       if (!PAR2 && P.regroup && r.w == 8 && r1 - r0 <= 3) {
         uint32_t lo = 0u, hi = 0u;

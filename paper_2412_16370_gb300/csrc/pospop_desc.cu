@@ -1,6 +1,6 @@
-// pospop_desc.cu -- the serving loop's counting kernel: one launch counts up
-// to kServeMax requests of mixed width and size, passed by value in the
-// kernel's parameter block (a __grid_constant__ struct of about 8 KiB, read
+// pospop_desc.cu -- the serving loop's counting kernel (and its add-into
+// form behind pospopcnt_multi): one launch counts up to kServeMax requests
+// of mixed width and size, passed by value in the kernel's parameter block (a __grid_constant__ struct of about 8 KiB, read
 // in place through the constant cache: no upload copy before the launch).
 //
 // Work items (item_rows rows of 512 B of one request, as in the batched
@@ -36,8 +36,13 @@ __device__ __forceinline__ uint32_t find_request(const uint64_t *item_start, uin
   return lo;
 }
 
-template <int BS, int MINB, int DEPTH, int HINT>
+// ADD: the add-into form of pospopcnt_multi: every work item's counts are
+// added straight into its count's own counters (req.out), with no request
+// slots and no completion tracking; it waits for the previous kernel on the
+// stream (programmatic dependent launch) like the other counting kernels.
+template <int BS, int MINB, int DEPTH, int HINT, bool ADD = false>
 __global__ void __launch_bounds__(BS, MINB) serve_kernel(const __grid_constant__ ServeParams P) {
+  if (ADD) pdl_enter();
   constexpr unsigned WPB = BS / 32;
   const unsigned lane = threadIdx.x & 31u;
   const uint64_t NW = (uint64_t)gridDim.x * WPB;
@@ -59,6 +64,13 @@ __global__ void __launch_bounds__(BS, MINB) serve_kernel(const __grid_constant__
     const uint64_t r1 = (r0 + P.item_rows < R) ? r0 + P.item_rows : R;
     uint32_t cnt[4] = {0u, 0u, 0u, 0u};
     count_rows<DEPTH, HINT>(s, r0, 1, r1 - r0, lane, xk, cnt, PlainLoader<HINT>{});
+    if (ADD) {
+      unsigned long long *dst = rq.out;
+      fold_counts(cnt, w, rot, lane, [&](uint32_t j, unsigned long long v) {
+        if (v) atomicAdd(dst + j, v);
+      });
+      continue;
+    }
     const uint32_t slot = P.slot0 + k;
     unsigned long long *out = P.counts + 64ull * slot;
     fold_counts(cnt, w, rot, lane, [&](uint32_t j, unsigned long long v) {
@@ -92,5 +104,13 @@ static const Variant kServe[] = {POSPOP_FAMILY(POSPOP_SERV)};
 
 int serve_variant_count() { return (int)(sizeof(kServe) / sizeof(kServe[0])); }
 const Variant &serve_variant(int i) { return kServe[i]; }
+
+#define POSPOP_MULTI(BS, MINB, D, H) \
+  Variant{reinterpret_cast<const void *>(&serve_kernel<BS, MINB, D, H, true>), BS, MINB, D, H}
+
+static const Variant kMulti[] = {POSPOP_FAMILY(POSPOP_MULTI)};
+
+int multi_variant_count() { return (int)(sizeof(kMulti) / sizeof(kMulti[0])); }
+const Variant &multi_variant(int i) { return kMulti[i]; }
 
 }  // namespace pospop

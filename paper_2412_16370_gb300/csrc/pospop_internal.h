@@ -33,6 +33,15 @@ struct StreamParams {
   uint32_t regroup;             // w = 8 warps with <= 3 rows use the per-lane bit regroup
 };
 
+// Size classes of the arrays of a batched count, by rows of 512 bytes: at
+// most 4 rows (2 KiB), 64 (32 KiB), 2048 (1 MiB), and above.  The tune table
+// gives each class its own work-item rows; the planning and counting kernels
+// both take an array's class from its row count.
+constexpr int kBatchClasses = 4;
+__host__ __device__ constexpr int batch_class(uint64_t rows) {
+  return rows <= 4 ? 0 : rows <= 64 ? 1 : rows <= 2048 ? 2 : 3;
+}
+
 // Sources of a batched count (the template parameter SRC of the batch kernels).
 constexpr int kSrcCsr = 0;      // m arrays at base + offsets[a] .. base + offsets[a+1], one w
 constexpr int kSrcGather = 2;   // regions ptrs[a], lens[a], all counted into one counter array
@@ -48,7 +57,7 @@ struct BatchParams {
   const uint64_t *item_start;   // m + 1 exclusive prefix sums of work items (workspace)
   unsigned long long *next;     // dynamic work counter (workspace)
   const int *status;            // planning status (workspace)
-  uint32_t item_rows;           // rows of 512 B per work item
+  uint32_t item_rows[kBatchClasses];   // rows of 512 B per work item, by array size class
   uint32_t grab;                // work items taken per atomic
   uint32_t regroup;             // w = 8 items of <= 3 rows use the per-lane bit regroup
 };
@@ -65,6 +74,7 @@ struct ServeReq {
   uint64_t nbytes;
   int32_t w;
   uint32_t items;               // work items of this request
+  unsigned long long *out;      // add-into form (pospopcnt_multi): this count's w counters
 };
 
 struct ServeParams {
@@ -91,7 +101,7 @@ struct PlanParams {
   uint64_t *block_sum;          // one per planning block
   unsigned long long *next;
   int *status;
-  uint32_t item_rows;
+  uint32_t item_rows[kBatchClasses];   // rows per work item, by array size class
   uint32_t nblocks;
 };
 
@@ -148,6 +158,10 @@ const Variant &roofline_variant(int i);
 
 int serve_variant_count();
 const Variant &serve_variant(int i);
+// The serving kernel's add-into form (pospopcnt_multi): same launch shapes,
+// each count added into its own counters, no completion tracking.
+int multi_variant_count();
+const Variant &multi_variant(int i);
 int gather_variant_count();
 const Variant &gather_variant(int i);
 int gather256_variant_count();

@@ -32,7 +32,7 @@ struct StreamTune {
 struct BatchTune {
   int variant;
   int ctas_per_sm;
-  uint32_t item_rows;       // rows per work item
+  uint32_t item_rows[kBatchClasses];   // rows per work item, by array size class
   uint32_t grab;            // work items per atomic
 };
 struct RoofTune {
@@ -43,9 +43,8 @@ struct RoofTune {
 // 16 MiB, 128 MiB, and above).
 constexpr int kServeClasses = 4;
 struct ServeTune {
-  uint32_t light_rows;      // work-item rows while the server is lightly loaded (0 = spread the
-                            // batch over every SM: the fewest rows that give each resident warp
-                            // of the GPU two items, at most `rows`)
+  uint32_t light_rows;      // most work-item rows while the server is lightly loaded (0 = rows;
+                            // items are then wave-aligned and at least half that long)
   uint32_t rows;            // work-item rows otherwise
   uint32_t streams;         // batch streams of the class that may run at once
   uint32_t cap;             // requests per batch
@@ -179,6 +178,19 @@ int launch_roofline_with(const DevCtx &ctx, const RoofTune &rt, const void *byte
 // managed memory, or pinned host memory mapped into the device's address
 // space); *devptr receives the address to give a kernel.
 bool device_addressable(const void *p, int device, const void **devptr);
+
+// Serving kernel helpers (pospop_serve.cu), shared by the serving loop and
+// the autotuner.  Rows of 512 B of the byte span [ptr, ptr + nbytes):
+uint64_t serve_rows(const void *ptr, uint64_t nbytes);
+// Light-load work-item rows of a batch of `rows` rows: at most `most`, at
+// least `least` (0: half of `most`, at least 8), the number of items a whole
+// multiple of the resident warps of serve variant `variant` where the batch
+// is large enough.
+uint32_t serve_light_rows(const DevCtx &ctx, int variant, uint64_t rows, uint32_t most,
+                          uint32_t least = 0);
+// Launch serve variant v on the planned parameter block P (nothing if P
+// has no work items).
+int serve_launch(const Variant &v, const ServeParams &P, cudaStream_t stream);
 
 // Device address of the no-allocation batch's scratch array on the current
 // device (pospop_noalloc.cu); called once per device when its context is

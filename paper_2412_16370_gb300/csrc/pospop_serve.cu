@@ -24,11 +24,23 @@
 // by the kernel; the warp that finishes a request publishes its counts to
 // mapped pinned memory and raises its flag, which the loop polls.  All
 // waits are bounded.
+//
+// Host input.  A server made by pospop_server_create_pooled owns a device
+// staging pool of mem_budget bytes, allocated once.  Requests submitted with
+// pospop_server_submit_host name host memory: such a request is admitted
+// only when a contiguous range of the pool (first fit, 256-byte granules)
+// is free for it, so the budget bounds memory that is really allocated; an
+// uploader thread copies each admitted request into its range
+// (cudaMemcpyAsync on the server's copy stream, then an event that the
+// request's batch stream waits for) and hands it to the loop.  The range is
+// released when the request completes, that is, after the kernel has read
+// it.
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
 #include <deque>
+#include <map>
 #include <mutex>
 #include <thread>
 #include <vector>
@@ -48,11 +60,17 @@ int64_t now_ns() {
 struct Request {
   uint64_t id;
   int w;
-  const void *dptr;
+  const void *dptr;            // device address of the input (the pool range for host input)
   size_t nbytes;
   uint64_t *result;
   pospop_completion rec;
+  const void *host = nullptr;  // host input, copied into the pool before counting
+  uint64_t pool_off = 0;
+  uint64_t pool_len = 0;       // 0: no pool range held
+  cudaEvent_t ev = nullptr;    // the upload's completion (waited for by the batch stream)
 };
+
+constexpr uint64_t kPoolGranule = 256;
 
 struct Batch {
   cudaStream_t s = nullptr;
@@ -80,7 +98,7 @@ constexpr size_t kClassBound[kServeClasses - 1] = {size_t(1) << 20, size_t(16) <
 constexpr int kServeWidthGroup = width_group(32);
 constexpr size_t kBatchCap = 1024;      // requests per batch, at most (4 launches of kServeMax)
 constexpr uint64_t kMaxServeGrid = uint64_t(1) << 20;
-constexpr uint32_t kMinItemRows = 8;    // the shortest work item of a spread batch
+constexpr uint32_t kMinItemRows = 8;    // the shortest light-load work item
 
 // The tune-table entries the loop works with (copied once per loop pass).
 struct LoopTune {
@@ -96,6 +114,44 @@ int request_class(size_t nbytes, int levels) {
 }
 
 }  // namespace
+
+uint64_t serve_rows(const void *ptr, uint64_t nbytes) {
+  if (nbytes == 0) return 0;
+  const uint64_t s0 = (uint64_t)ptr, e0 = s0 + nbytes;
+  const uint64_t G = (((e0 + 15u) & ~15ull) - (s0 & ~15ull)) >> 4;
+  return (G + 31u) >> 5;
+}
+
+uint32_t serve_light_rows(const DevCtx &ctx, int variant, uint64_t rows, uint32_t most,
+                          uint32_t least_rows) {
+  const uint64_t m = most ? most : 1;
+  const uint64_t least = least_rows ? std::min<uint64_t>(least_rows, m)
+                                    : std::max<uint64_t>(std::min<uint64_t>(kMinItemRows, m), m / 2);
+  const Variant &v = serve_variant(variant);
+  const uint64_t warps =
+      (uint64_t)ctx.sms * (uint64_t)ctx.occ_serve[variant] * (uint64_t)(v.bs / 32);
+  const uint64_t waves = (rows + warps * m - 1) / (warps * m);   // >= 1 (rows > 0)
+  const uint64_t want = waves ? (rows + waves * warps - 1) / (waves * warps) : m;
+  return (uint32_t)std::min(m, std::max(least, want));
+}
+
+int serve_launch(const Variant &v, const ServeParams &P, cudaStream_t stream) {
+  // one work item per warp: blocks retire as their items finish, so a
+  // smaller class's pending blocks can take the SM (the grid-stride loop in
+  // the kernel covers any cap)
+  const uint64_t wpb = (uint64_t)v.bs / 32;
+  uint64_t grid = (P.total + wpb - 1) / wpb;
+  if (grid > kMaxServeGrid) grid = kMaxServeGrid;
+  if (grid == 0) return POSPOP_OK;
+  void *args[] = {const_cast<ServeParams *>(&P)};
+  if (cudaLaunchKernel(v.fn, dim3((unsigned)grid), dim3(v.bs), args, 0, stream) != cudaSuccess) {
+    cudaGetLastError();
+    return POSPOP_ECUDA;
+  }
+  note_launches(1);
+  return POSPOP_OK;
+}
+
 }  // namespace pospop
 
 struct pospop_server {
@@ -117,6 +173,18 @@ struct pospop_server {
   bool stop = false;
   int loop_error = POSPOP_OK;
   std::thread loop;
+
+  // device staging pool for host input (pospop_server_create_pooled)
+  uint8_t *pool = nullptr;
+  uint64_t pool_bytes = 0, pool_used = 0, pool_hwm = 0;
+  std::map<uint64_t, uint64_t> pool_free;      // offset -> length of the free ranges
+  std::deque<pospop::Request *> uploads;       // admitted host input, copy not yet enqueued
+  int uploading = 0;                           // taken by the uploader, not yet admitted
+  std::vector<cudaEvent_t> spare_events;
+  cudaStream_t up_stream = nullptr;
+  std::condition_variable cv_up;
+  bool stop_uploads = false;
+  std::thread uploader;
 };
 
 namespace pospop {
@@ -133,29 +201,25 @@ void free_batch(Batch &b) {
   cudaGetLastError();
 }
 
-uint64_t request_rows(const Request *r) {
-  if (r->nbytes == 0) return 0;
-  const uint64_t s0 = (uint64_t)r->dptr, e0 = s0 + r->nbytes;
-  const uint64_t G = (((e0 + 15u) & ~15ull) - (s0 & ~15ull)) >> 4;
-  return (G + 31u) >> 5;
-}
+uint64_t request_rows(const Request *r) { return serve_rows(r->dptr, r->nbytes); }
 
-// Work-item rows of a batch of `rows` rows of class `level`.  While the
-// server is lightly loaded, items are shorter, so that a request is spread
-// over many warps instead of a few (its latency is then a few short items):
-// the class's light_rows, or with light_rows 0 the fewest rows that still
-// give every resident warp of the GPU two items.  Under load the class's
-// `rows` stay, since the extra blocks would only delay the requests behind.
+// Work-item rows of a batch of `rows` rows of class `level`.  Under load
+// the class's `rows`.  While the server is lightly loaded, shorter items
+// spread a request over more warps, so its latency is a few short items:
+// at most the class's light_rows L (0: `rows`) and at least half of that,
+// chosen so that the number of items is a whole multiple of the GPU's
+// resident warps where the batch is large enough (every SM takes part and
+// there is no partial last wave).  Much shorter items than that cost more
+// than they gain: each warp then runs more item set-ups and final
+// accumulations for the same bytes (measured on GB300 for a lone 128 MiB
+// request: 54-row items in two waves took 35.4 us against 29.8 us for
+// 127-row items in one).
 uint32_t batch_item_rows(const pospop_server &srv, const LoopTune &lt, int level, uint64_t rows,
                          size_t load_bytes) {
   const ServeTune &st = lt.cls[level];
   if (load_bytes >= lt.light) return st.rows;
-  if (st.light_rows > 0) return std::min(st.light_rows, st.rows);
-  const Variant &v = serve_variant(lt.bt.variant);
-  const uint64_t warps = (uint64_t)srv.ctx->sms * (uint64_t)srv.ctx->occ_serve[lt.bt.variant] *
-                         (uint64_t)(v.bs / 32);
-  const uint64_t want = (rows + 2 * warps - 1) / (2 * warps);
-  return (uint32_t)std::min<uint64_t>(st.rows, std::max<uint64_t>(kMinItemRows, want));
+  return serve_light_rows(*srv.ctx, lt.bt.variant, rows,
+                          std::min(st.light_rows ? st.light_rows : st.rows, st.rows));
 }
 
 // Enqueue one batch of the requests in b.reqs on b.s (loop thread only):
@@ -169,9 +233,13 @@ int launch_batch(pospop_server &srv, Batch &b, const LoopTune &lt, size_t load_b
   uint64_t rows = 0;
   for (const Request *r : b.reqs) rows += request_rows(r);
   const uint32_t ir = batch_item_rows(srv, lt, b.level, rows, load_bytes);
-  const BatchTune &bt = lt.bt;
-  const Variant &v = serve_variant(bt.variant);
-  const uint64_t wpb = (uint64_t)v.bs / 32;
+  const Variant &v = serve_variant(lt.bt.variant);
+  // host input: the batch stream waits for the requests' copies into the pool
+  for (const Request *r : b.reqs)
+    if (r->ev && cudaStreamWaitEvent(b.s, r->ev, 0) != cudaSuccess) {
+      cudaGetLastError();
+      return POSPOP_ECUDA;
+    }
   static thread_local ServeParams P;   // about 8 KiB: not on the loop thread's stack
   for (int k0 = 0; k0 < n; k0 += kServeMax) {
     const int cnt = std::min(kServeMax, n - k0);
@@ -198,17 +266,8 @@ int launch_batch(pospop_server &srv, Batch &b, const LoopTune &lt, size_t load_b
     P.item_start[cnt] = items;
     P.total = items;
     if (items == 0) continue;
-    // one work item per warp: blocks retire as their items finish, so a
-    // smaller class's pending blocks can take the SM (the grid-stride loop
-    // in the kernel covers any cap)
-    uint64_t grid = (items + wpb - 1) / wpb;
-    if (grid > kMaxServeGrid) grid = kMaxServeGrid;
-    void *args[] = {&P};
-    if (cudaLaunchKernel(v.fn, dim3((unsigned)grid), dim3(v.bs), args, 0, b.s) != cudaSuccess) {
-      cudaGetLastError();
-      return POSPOP_ECUDA;
-    }
-    note_launches(1);
+    const int rc = serve_launch(v, P, b.s);
+    if (rc != POSPOP_OK) return rc;
   }
   if (cudaEventRecord(b.done, b.s) != cudaSuccess) {
     cudaGetLastError();
@@ -217,8 +276,44 @@ int launch_batch(pospop_server &srv, Batch &b, const LoopTune &lt, size_t load_b
   return POSPOP_OK;
 }
 
+// First fit of `len` bytes (a multiple of kPoolGranule) in the pool's free
+// ranges; caller holds srv.mu.
+bool pool_take(pospop_server &srv, uint64_t len, uint64_t *off) {
+  for (auto it = srv.pool_free.begin(); it != srv.pool_free.end(); ++it) {
+    if (it->second < len) continue;
+    *off = it->first;
+    const uint64_t rest = it->second - len, at = it->first + len;
+    srv.pool_free.erase(it);
+    if (rest) srv.pool_free.emplace(at, rest);
+    srv.pool_used += len;
+    srv.pool_hwm = std::max(srv.pool_hwm, srv.pool_used);
+    return true;
+  }
+  return false;
+}
+
+// Return a range to the pool, merged with free neighbours; caller holds srv.mu.
+void pool_give(pospop_server &srv, uint64_t off, uint64_t len) {
+  srv.pool_used -= len;
+  auto next = srv.pool_free.lower_bound(off);
+  if (next != srv.pool_free.end() && off + len == next->first) {
+    len += next->second;
+    next = srv.pool_free.erase(next);
+  }
+  if (next != srv.pool_free.begin()) {
+    auto prev = std::prev(next);
+    if (prev->first + prev->second == off) {
+      prev->second += len;
+      return;
+    }
+  }
+  srv.pool_free.emplace(off, len);
+}
+
 // Bookkeeping of a finished request; caller holds srv.mu.
 void complete(pospop_server &srv, Request *r, int status, int64_t t) {
+  if (r->pool_len) pool_give(srv, r->pool_off, r->pool_len);
+  if (r->ev) srv.spare_events.push_back(r->ev);
   r->rec.status = status;
   r->rec.t_done_ns = t;
   srv.inflight -= 1;
@@ -306,17 +401,38 @@ void serve_loop(pospop_server *srv) {
         progress = true;
         srv->cv_done.notify_all();
       }
-      // 2. admission by device memory and slots (FIFO)
+      // 2. admission by device memory and slots (FIFO); host input also
+      //    needs a free range of the staging pool, and goes to the uploader
+      bool to_uploader = false;
       while (!srv->pending.empty() && srv->inflight < srv->max_inflight &&
              srv->inflight_bytes + srv->pending.front()->nbytes <= srv->budget) {
         Request *r = srv->pending.front();
+        if (r->host && r->nbytes > 0) {
+          const uint64_t len = (r->nbytes + kPoolGranule - 1) / kPoolGranule * kPoolGranule;
+          uint64_t off = 0;
+          if (!pool_take(*srv, len, &off)) break;   // wait for pool space
+          r->pool_off = off;
+          r->pool_len = len;
+          r->dptr = srv->pool + off;
+          if (!srv->spare_events.empty()) {
+            r->ev = srv->spare_events.back();
+            srv->spare_events.pop_back();
+          }
+        }
         srv->pending.pop_front();
         r->rec.t_admit_ns = tnow;
         srv->inflight += 1;
         srv->inflight_bytes += r->nbytes;
-        srv->admitted.push_back(r);
+        if (r->host) {
+          srv->uploads.push_back(r);
+          srv->uploading += 1;
+          to_uploader = true;
+        } else {
+          srv->admitted.push_back(r);
+        }
         progress = true;
       }
+      if (to_uploader) srv->cv_up.notify_one();
       // 3. admitted requests go, by size class and in admission order, into
       //    the next free batch of their class (while fewer than the class's
       //    `streams` batches are running; at most `cap` requests a batch)
@@ -352,7 +468,9 @@ void serve_loop(pospop_server *srv) {
       load_bytes = srv->inflight_bytes;
       const bool busy = std::any_of(srv->batches.begin(), srv->batches.end(),
                                     [](const Batch &b) { return b.busy; });
-      if (srv->stop && !busy && srv->admitted.empty() && srv->pending.empty()) stop_now = true;
+      if (srv->stop && !busy && srv->admitted.empty() && srv->pending.empty() &&
+          srv->uploading == 0)
+        stop_now = true;
       // idle: keep polling for a short while (a new request is picked up
       // within a microsecond), then block on the condition variable
       if (progress || busy) last_activity = tnow;
@@ -385,14 +503,55 @@ void serve_loop(pospop_server *srv) {
   }
 }
 
+// The uploader: copies admitted host input into its pool range on the copy
+// stream, records the copy's event and hands the request to the loop.  A
+// pageable source makes cudaMemcpyAsync wait until the bytes are staged, so
+// this runs on its own thread, not on the loop's.
+void upload_loop(pospop_server *srv) {
+  cudaSetDevice(srv->ctx->device);
+  while (true) {
+    Request *r = nullptr;
+    {
+      std::unique_lock<std::mutex> lk(srv->mu);
+      srv->cv_up.wait(lk, [&] { return srv->stop_uploads || !srv->uploads.empty(); });
+      if (srv->uploads.empty()) break;   // stopping, nothing left
+      r = srv->uploads.front();
+      srv->uploads.pop_front();
+    }
+    int rc = POSPOP_OK;
+    if (!r->ev && cudaEventCreateWithFlags(&r->ev, cudaEventDisableTiming) != cudaSuccess)
+      rc = POSPOP_ECUDA;
+    if (rc == POSPOP_OK && r->nbytes > 0 &&
+        cudaMemcpyAsync(const_cast<void *>(r->dptr), r->host, r->nbytes, cudaMemcpyHostToDevice,
+                        srv->up_stream) != cudaSuccess)
+      rc = POSPOP_ECUDA;
+    if (rc == POSPOP_OK && cudaEventRecord(r->ev, srv->up_stream) != cudaSuccess)
+      rc = POSPOP_ECUDA;
+    if (rc != POSPOP_OK) cudaGetLastError();
+    {
+      std::lock_guard<std::mutex> g(srv->mu);
+      srv->uploading -= 1;
+      if (rc == POSPOP_OK) {
+        srv->admitted.push_back(r);
+      } else {
+        srv->loop_error = rc;
+        complete(*srv, r, rc, now_ns());
+        srv->cv_done.notify_all();
+      }
+    }
+    srv->cv_loop.notify_one();
+  }
+}
+
 // Queue one request.  `t_arrival` is its arrival time (the submit time, or a
 // load generator's scheduled arrival, so that latency includes any delay in
 // submitting it).
 int submit_impl(pospop_server *srv, int w, const void *dptr, size_t nbytes, uint64_t *result,
-                uint64_t *id, int64_t t_arrival) {
+                uint64_t *id, int64_t t_arrival, const void *host = nullptr) {
   Request *r = new Request();
   r->w = w;
   r->dptr = dptr;
+  r->host = host;
   r->nbytes = nbytes;
   r->result = result;
   memset(&r->rec, 0, sizeof r->rec);
@@ -440,15 +599,19 @@ int request_ptr(pospop_server *srv, const void *bytes, size_t nbytes, const void
   return POSPOP_EPTR;
 }
 
-}  // namespace
-}  // namespace pospop
+// Free what a server holds on the device and the host (its threads have
+// stopped, nothing of it is in flight).
+void free_server(pospop_server *srv) {
+  for (Batch &x : srv->batches) free_batch(x);
+  for (cudaEvent_t e : srv->spare_events) cudaEventDestroy(e);
+  if (srv->pool) cudaFree(srv->pool);
+  if (srv->up_stream) cudaStreamDestroy(srv->up_stream);
+  cudaGetLastError();
+  delete srv;
+}
 
-using namespace pospop;
-
-extern "C" {
-
-int pospop_server_create(size_t mem_budget, int max_inflight, int max_batches,
-                         pospop_server **out) {
+int create_server(size_t mem_budget, int max_inflight, int max_batches, bool pooled,
+                  pospop_server **out) {
   if (!out || mem_budget == 0 || max_inflight < 1 || max_inflight > (1 << 20) || max_batches < 1 ||
       max_batches > 64)
     return POSPOP_EINVAL;
@@ -489,20 +652,76 @@ int pospop_server_create(size_t mem_budget, int max_inflight, int max_batches,
         cudaHostGetDevicePointer(reinterpret_cast<void **>(&b.dflags), b.hflags, 0) !=
             cudaSuccess) {
       cudaGetLastError();
-      for (Batch &x : srv->batches) free_batch(x);
-      delete srv;
+      free_server(srv);
       return POSPOP_ENOMEM;
     }
     memset(b.hflags, 0, fbytes);   // seq starts at 1
   }
+  if (pooled) {
+    // the staging pool for host input: allocated once, the whole budget
+    if (cudaMalloc(&srv->pool, mem_budget) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&srv->up_stream, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      free_server(srv);
+      return POSPOP_ENOMEM;
+    }
+    srv->pool_bytes = mem_budget;
+    srv->pool_free.emplace(0, mem_budget / kPoolGranule * kPoolGranule);
+  }
   if (cudaDeviceSynchronize() != cudaSuccess) {   // the zeroed slots are in place
     cudaGetLastError();
-    for (Batch &x : srv->batches) free_batch(x);
-    delete srv;
+    free_server(srv);
     return POSPOP_ECUDA;
   }
   srv->loop = std::thread(serve_loop, srv);
+  if (pooled) srv->uploader = std::thread(upload_loop, srv);
   *out = srv;
+  return POSPOP_OK;
+}
+
+}  // namespace
+}  // namespace pospop
+
+using namespace pospop;
+
+extern "C" {
+
+int pospop_server_create(size_t mem_budget, int max_inflight, int max_batches,
+                         pospop_server **out) {
+  return create_server(mem_budget, max_inflight, max_batches, false, out);
+}
+
+int pospop_server_create_pooled(size_t mem_budget, int max_inflight, int max_batches,
+                                pospop_server **out) {
+  return create_server(mem_budget, max_inflight, max_batches, true, out);
+}
+
+int pospop_server_submit_host(pospop_server *srv, int w, const void *bytes, size_t nbytes,
+                              uint64_t *result, uint64_t *id) {
+  if (!srv || !valid_width(w)) return POSPOP_EINVAL;
+  if (!srv->pool) return POSPOP_EINVAL;   // not a pooled server
+  if (nbytes > 0 && !bytes) return POSPOP_EINVAL;
+  if (nbytes > srv->budget) return POSPOP_ERANGE;
+  if (nbytes > 0) {
+    // host memory only (pinned or pageable); device input goes through
+    // pospop_server_submit
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      return POSPOP_EPTR;
+    }
+    if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) return POSPOP_EPTR;
+  }
+  static const uint8_t kEmpty = 0;
+  return submit_impl(srv, w, nullptr, nbytes, result, id, now_ns(), nbytes ? bytes : &kEmpty);
+}
+
+int pospop_server_pool_stats(pospop_server *srv, uint64_t stats[3]) {
+  if (!srv || !stats) return POSPOP_EINVAL;
+  std::lock_guard<std::mutex> g(srv->mu);
+  stats[0] = srv->pool_bytes;
+  stats[1] = srv->pool_used;
+  stats[2] = srv->pool_hwm;
   return POSPOP_OK;
 }
 
@@ -607,12 +826,17 @@ int pospop_server_destroy(pospop_server *srv) {
     srv->stop = true;
   }
   srv->cv_loop.notify_all();
-  if (srv->loop.joinable()) srv->loop.join();
-  for (Batch &b : srv->batches) {
-    if (b.s) cudaStreamSynchronize(b.s);
-    free_batch(b);
+  if (srv->loop.joinable()) srv->loop.join();   // every request has finished
+  {
+    std::lock_guard<std::mutex> g(srv->mu);
+    srv->stop_uploads = true;
   }
-  delete srv;
+  srv->cv_up.notify_all();
+  if (srv->uploader.joinable()) srv->uploader.join();
+  for (Batch &b : srv->batches)
+    if (b.s) cudaStreamSynchronize(b.s);
+  if (srv->up_stream) cudaStreamSynchronize(srv->up_stream);
+  free_server(srv);
   return POSPOP_OK;
 }
 

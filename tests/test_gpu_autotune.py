@@ -1,10 +1,12 @@
 """The autotuner (pospopcnt_autotune) on the GPU.
 
 It times the launch candidates of the single-array kernel per width group
-and size class, of the batched kernel on a ragged batch per width group and
-of the roofline read kernels,
-installs the fastest and writes the table.  The written table must load
-back, and counts made with it must still equal the oracle's.
+and size class, of the batched kernel per width group (launch shape on a mix
+of batches, work-item rows per array size class), of the serving kernel per
+serving size class and of the roofline read kernels, installs the fastest
+and writes the table.  The written table must load back entry for entry, and
+counts made with it (single array, batch, served requests) must still equal
+the oracle's.
 """
 import re
 
@@ -20,6 +22,10 @@ from _gpu import WORD_W, counts_np
 pytestmark = pytest.mark.gpu
 
 
+def _entries(text):
+    return [l for l in text.splitlines() if l and not l.startswith("#")]
+
+
 def test_autotune_writes_a_loadable_table_and_counts_stay_exact(gpu, orc, tmp_path):
     saved = tmp_path / "saved.txt"
     saved.write_text(pp.pospopcnt_tune_describe())
@@ -32,8 +38,12 @@ def test_autotune_writes_a_loadable_table_and_counts_stay_exact(gpu, orc, tmp_pa
             assert kind in text, kind
         for cls in range(5):   # each size class, for every width or per width
             assert re.search(rf"^stream (\d+ )?{cls} ", text, re.M), cls
+        for k in range(4):     # each serving size class
+            assert re.search(rf"^serve {k} \d+ \d+ \d+ \d+$", text, re.M), k
         assert "autotuned" in pp.pospopcnt_tune_describe()
         pp.pospopcnt_tune_load(str(out))          # the written table parses
+        # ... and loads back entry for entry
+        assert _entries(pp.pospopcnt_tune_describe()) == _entries(text)
         # counts under the tuned table: a single array and a ragged batch
         host = synth.random_bytes((3 << 20) + 11, seed=91)
         data = torch.from_numpy(host).to(gpu)[5:]
@@ -49,6 +59,17 @@ def test_autotune_writes_a_loadable_table_and_counts_stay_exact(gpu, orc, tmp_pa
         cb = torch.zeros((len(sizes), 16), dtype=torch.int64, device=gpu)
         pp.pospopcnt_batch(16, cb, base, torch.from_numpy(offs.view(np.int64)).to(gpu))
         assert np.array_equal(counts_np(cb), orc.batch(16, bh, offs))
+        # served requests of every serving class small enough for the buffer
+        srv = pp.pospop_server_create(1 << 30, 64, 2)
+        try:
+            res = np.zeros((4, 64), dtype=np.uint64)
+            for k, nb in enumerate((1000, 3 << 20)):
+                pp.pospop_server_submit(srv, 32, data.data_ptr(), nb, res[k])
+            assert pp.pospop_server_drain(srv, 10000) == pp.POSPOP_OK
+        finally:
+            pp.pospop_server_destroy(srv)
+        for k, nb in enumerate((1000, 3 << 20)):
+            assert np.array_equal(res[k, :32], orc.bytes(32, host[5:5 + nb])), nb
     finally:
         pp.pospopcnt_tune_load(str(saved))
 

@@ -112,6 +112,33 @@ def test_every_variant_and_item_size(gpu, orc, tune_override):
                         assert np.array_equal(counts_np(c), exp[w]), (bs, depth, hint, item_rows, w)
 
 
+def test_per_class_item_rows(gpu, orc, tune_override):
+    """Work-item rows per array size class (tune entry batch_rows): arrays of
+    every class (up to 2 KiB, 32 KiB, 1 MiB, above) in one batch, each class
+    with its own item size, bit-exact for several tables and widths."""
+    sizes = np.concatenate([synth.log_uniform_sizes(400, 1, 2048, seed=41),
+                            synth.log_uniform_sizes(300, 2049, 32768, seed=42),
+                            synth.log_uniform_sizes(100, 32769, 1 << 20, seed=43),
+                            synth.log_uniform_sizes(12, (1 << 20) + 1, 6 << 20, seed=44)])
+    rng = np.random.default_rng(45)
+    sizes = sizes[rng.permutation(sizes.size)]
+    sizes[::53] = 0
+    offs = synth.csr_offsets(sizes)
+    host = synth.random_bytes(int(offs[-1]), seed=46)
+    base = torch.empty(host.size + 32, dtype=torch.uint8, device=gpu)[9:9 + host.size]
+    base.copy_(torch.from_numpy(host))
+    offs_d = torch.from_numpy(offs.view(np.int64)).to(gpu)
+    exp = {w: orc.batch(w, host, offs) for w in (8, 32, 256)}
+    for rows in ("1 2 3 4", "4 64 2048 4095", "2 7 100 1000", "3 31 255 63"):
+        tune_override(f"batch 512 1 16 1 1 127 2\nbatch_rows {rows}\n")
+        assert f"batch_rows {rows}" in pp.pospopcnt_tune_describe()
+        for w in (8, 32, 256):
+            c = torch.zeros((len(sizes), w), dtype=torch.int64, device=gpu)
+            pp.pospopcnt_batch(w, c, base, offs_d)
+            assert pp.pospopcnt_batch_status() == pp.POSPOP_OK
+            assert np.array_equal(counts_np(c), exp[w]), (rows, w)
+
+
 def test_short_sweep_back_to_back(gpu, orc):
     """The short/unaligned sweep's arrays laid back to back in one batch."""
     for w in WORD_W:

@@ -4,7 +4,8 @@ Requests of mixed width and size over a device-resident pool must give the
 same counts in the mix as alone (and as the CPU oracle), admission must keep
 the in-flight input bytes within the budget and the admitted requests within
 the slot cap, later arrivals must be launched while earlier batches are still
-running, and every wait must end with a status.
+running, the tune table's per-class serving entries must take effect, and
+every wait must end with a status.
 """
 import numpy as np
 import pytest
@@ -125,6 +126,153 @@ def test_later_arrivals_overlap_running_batches(gpu, pool):
     exp = _solo(pool, w[:2], nbytes[:2], offs[:2])
     for k in range(n):
         assert np.array_equal(results[k, :16], exp[k % 2, :16])
+
+
+@pytest.fixture
+def serve_tune(gpu, tmp_path):
+    saved = tmp_path / "saved_tune.txt"
+    saved.write_text(pp.pospopcnt_tune_describe())
+    keep = [l for l in saved.read_text().splitlines() if not l.startswith(("serve ", "serve_light"))]
+
+    def install(*lines):
+        f = tmp_path / "tune.txt"
+        f.write_text("\n".join(keep + list(lines)) + "\n")
+        pp.pospopcnt_tune_load(str(f))
+
+    yield install
+    pp.pospopcnt_tune_load(str(saved))
+
+
+def test_lone_large_request(gpu, orc, pool):
+    """One 128 MiB request on an idle server (its work items are spread over
+    every SM): the result equals the oracle's count."""
+    srv = pp.pospop_server_create(1 << 30, 16, 2)
+    try:
+        res = np.zeros(64, dtype=np.uint64)
+        p0 = pool.data_ptr() + 13
+        pp.pospop_server_submit(srv, 16, p0, 128 * MIB, res)
+        assert pp.pospop_server_drain(srv, 10000) == pp.POSPOP_OK
+        recs = pp.pospop_server_poll(srv, timeout_ms=100)
+        assert len(recs) == 1 and recs[0].status == 0
+    finally:
+        pp.pospop_server_destroy(srv)
+    seg = pool[13:13 + 128 * MIB].cpu().numpy()
+    assert np.array_equal(res[:16], orc.bytes(16, seg))
+
+
+def test_class_streams_and_cap_entries(gpu, pool, serve_tune):
+    """`serve 3 0 127 1 1`: requests from 128 MiB run one batch at a time, one
+    request a batch; `serve 0 8 127 64 2`: small requests at most two a batch."""
+    serve_tune("serve 3 0 127 1 1", "serve 0 8 127 64 2")
+    nb, ns = 12, 40
+    w = np.concatenate([np.full(nb, 32), np.full(ns, 8)]).astype(np.int32)
+    nbytes = np.concatenate([np.full(nb, 128 * MIB), np.full(ns, 4096)]).astype(np.uint64)
+    offs = np.concatenate([np.arange(nb) % 3 * 32 * MIB, np.arange(ns) * 4099]).astype(np.uint64)
+    arrival = np.zeros(nb + ns, dtype=np.int64)
+    srv = pp.pospop_server_create(64 << 30, 4096, 8)
+    try:
+        results = np.zeros((nb + ns, 64), dtype=np.uint64)
+        recs = pp.pospop_server_run_trace(srv, arrival, w, pool.data_ptr() + offs, nbytes, results)
+    finally:
+        pp.pospop_server_destroy(srv)
+    assert (recs["status"] == 0).all()
+    big = recs[:nb]
+    order = np.argsort(big["t_launch_ns"])
+    launches = big["t_launch_ns"][order].astype(np.int64)
+    dones = big["t_done_ns"][order].astype(np.int64)
+    assert len(set(launches.tolist())) == nb                 # one request per batch
+    assert (launches[1:] >= dones[:-1]).all()                # one batch at a time
+    small = recs[nb:]
+    _, per_launch = np.unique(small["t_launch_ns"], return_counts=True)
+    assert per_launch.max() <= 2
+    solo = _solo(pool, w, nbytes, offs)
+    for k in range(nb + ns):
+        assert np.array_equal(results[k, :w[k]], solo[k, :w[k]]), k
+
+
+def test_host_input_admitted_by_pool_space(gpu, orc):
+    """A pooled server stages host input into its device pool: with a budget
+    (the pool) far smaller than the sum of the requests, admission waits for
+    pool space, the pool's high-water mark stays within the budget, and every
+    result equals the oracle's count.  Pinned and pageable sources mixed."""
+    budget = 48 * MIB
+    n = 60
+    sizes = synth.log_uniform_sizes(n, 1 * MIB, 16 * MIB, seed=31)
+    sizes[::11] = 0
+    sizes[5::13] = 4099
+    widths = np.array([8, 16, 32, 64, 1, 4], dtype=np.int32)[np.arange(n) % 6]
+    bufs = []
+    for k in range(n):
+        data = synth.random_bytes(int(sizes[k]) + 3, seed=400 + k)[3:]
+        if k % 2:
+            t = torch.empty(data.size, dtype=torch.uint8, pin_memory=True)
+            t.numpy()[:] = data
+            bufs.append((t, data))
+        else:
+            bufs.append((data, data))
+    assert int(sizes.sum()) > 4 * budget
+    srv = pp.pospop_server_create_pooled(budget, 4096, 4)
+    results = np.zeros((n, 64), dtype=np.uint64)
+    try:
+        ids = [pp.pospop_server_submit_host(srv, int(widths[k]), bufs[k][0], int(sizes[k]),
+                                            results[k]) for k in range(n)]
+        assert pp.pospop_server_drain(srv, 60000) == pp.POSPOP_OK
+        recs = []
+        while len(recs) < n:
+            got = pp.pospop_server_poll(srv, n, 1000)
+            assert got
+            recs += got
+        pool_bytes, used, hwm = pp.pospop_server_pool_stats(srv)
+    finally:
+        pp.pospop_server_destroy(srv)
+    assert pool_bytes == budget and used == 0 and 0 < hwm <= budget
+    by_id = {r.id: r for r in recs}
+    rec = [by_id[i] for i in ids]
+    assert all(r.status == 0 for r in rec)
+    # admission waited for space: admitted bytes in flight never exceed the budget,
+    # and some request was admitted only after another had finished
+    ev = sorted([(r.t_admit_ns, int(r.nbytes)) for r in rec] + [(r.t_done_ns, -int(r.nbytes)) for r in rec],
+                key=lambda x: (x[0], x[1]))
+    cur = peak = 0
+    for _, d in ev:
+        cur += d
+        peak = max(peak, cur)
+    assert peak <= budget
+    assert max(r.t_admit_ns for r in rec) > min(r.t_done_ns for r in rec)
+    for k in range(n):
+        w = int(widths[k])
+        assert np.array_equal(results[k, :w], orc.bytes(w, bufs[k][1])), k
+
+
+def test_pooled_server_errors_and_device_requests(gpu, orc, pool):
+    srv = pp.pospop_server_create(1 * MIB, 4, 1)
+    try:
+        host = np.zeros(64, dtype=np.uint8)
+        rc = pp.lib().pospop_server_submit_host(srv, 8, host.ctypes.data, 64, None, None)
+        assert rc == pp.POSPOP_EINVAL                   # not a pooled server
+        assert pp.pospop_server_pool_stats(srv) == (0, 0, 0)
+    finally:
+        pp.pospop_server_destroy(srv)
+    srv = pp.pospop_server_create_pooled(4 * MIB, 64, 2)
+    try:
+        L = pp.lib()
+        host = np.zeros(64, dtype=np.uint8)
+        assert L.pospop_server_submit_host(srv, 8, pool.data_ptr(), 64, None,
+                                           None) == pp.POSPOP_EPTR
+        assert L.pospop_server_submit_host(srv, 8, host.ctypes.data, 5 * MIB, None,
+                                           None) == pp.POSPOP_ERANGE
+        # device-pointer requests still work on a pooled server, beside host ones
+        r_dev = np.zeros(64, dtype=np.uint64)
+        r_host = np.zeros(64, dtype=np.uint64)
+        data = synth.random_bytes(3 * MIB + 5, seed=71)
+        pp.pospop_server_submit(srv, 32, pool.data_ptr() + 7, 3 * MIB, r_dev)
+        pp.pospop_server_submit_host(srv, 16, data, data.size, r_host)
+        assert pp.pospop_server_drain(srv, 10000) == pp.POSPOP_OK
+        assert pp.pospop_server_pool_stats(srv)[1] == 0
+    finally:
+        pp.pospop_server_destroy(srv)
+    assert np.array_equal(r_dev[:32], orc.bytes(32, pool[7:7 + 3 * MIB].cpu().numpy()))
+    assert np.array_equal(r_host[:16], orc.bytes(16, data))
 
 
 def test_errors_and_bounded_waits(gpu, pool):

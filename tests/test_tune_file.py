@@ -41,7 +41,7 @@ def test_per_width_and_every_width_entries(pp, tmp_path):
     lines += ["batch 256 2 16 0 2 63 4", "pdl 0", "staged 0", "short 1", "split 1024",
               "roofline 256 1 18", "wait 0", "wait 2147483648",
               "serve 0 8 127 64 1024", "serve 3 0 127 1 1", "serve_light 0",
-              "serve_light 536870912",
+              "serve_light 536870912", "batch_rows 1 8 127 511", "batch_rows 16 2 16 255 2047",
               "stream 4 512 1 16 0 3 1   # trailing comment"]
     assert _check(pp, tmp_path, "\n".join(lines) + "\n") == 0
     assert _check(pp, tmp_path, "\r\n".join(lines) + "\r\n") == 0   # CRLF line ends
@@ -74,6 +74,8 @@ def test_per_width_and_every_width_entries(pp, tmp_path):
     "serve 0 8 127 65 1024",             # streams above 64
     "serve 0 8 127 8 1025",              # batch cap above 1024
     "serve 0 8 127 8", "serve_light", "serve_light -5",
+    "batch_rows 1 8 127", "batch_rows 24 1 8 127 511", "batch_rows 0 8 127 511",
+    "batch_rows 1 8 127 2097152", "batch_rows 16 1 8 127 511 9",
 ])
 def test_malformed_line_is_reported_with_its_number(pp, tmp_path, bad):
     text = "# header\nstream 0 256 2 16 1 1 2\n\n" + bad + "\npdl 1\n"
