@@ -205,24 +205,22 @@ def _verify_counts(counts, data, launches):
             "oracle_s": round(time.perf_counter() - t0, 1)}
 
 
-def _cpu_baseline(data_dev, budget_s: float = 12.0, runs: int = 5):
-    """The oracle as it stands on a bounded sample of the array: all host
-    cores and one thread, each the median of `runs` timed passes (every pass
-    counts the sample once per w)."""
+def _cpu_baseline(data_dev, budget_s: float = 12.0, runs: int = 5, sample: int = GIB):
+    """The oracle as it stands on a bounded sample of the array (its first
+    `sample` bytes, the same sample size as the reference arm's default):
+    all host cores and one thread, each the median of `runs` timed passes
+    (every pass counts the sample once per w), with the spread of the runs."""
     import torch
     import oracle
     orc = oracle.load()
     cores = os.cpu_count() or 1
-    probe = 16 << 20
-    host = data_dev[:probe].cpu().numpy()
-    orc.bytes_mt(16, host, cores)                     # warm-up
-    t0 = time.perf_counter()
-    orc.bytes_mt(16, host, cores)
-    rate = probe / max(time.perf_counter() - t0, 1e-6)
-    # about budget_s for all runs on all cores, and a fifth of that on one thread
-    sample = int(min(GIB, max(probe, rate * budget_s / (runs * len(WIDTHS)))))
+    sample = min(sample, data_dev.numel())
     sample -= sample % 64
     host = data_dev[:sample].cpu().numpy()
+    orc.bytes_mt(16, host[:16 << 20], cores)          # warm-up
+    t0 = time.perf_counter()
+    orc.bytes_mt(16, host[:16 << 20], cores)
+    rate = (16 << 20) / max(time.perf_counter() - t0, 1e-6)
     one = int(min(sample, max(1 << 20, rate / cores * budget_s / 5 / (runs * len(WIDTHS)))))
     one -= one % 64
 
@@ -232,10 +230,12 @@ def _cpu_baseline(data_dev, budget_s: float = 12.0, runs: int = 5):
             orc.bytes_mt(w, host[:nbytes], threads)
         return nbytes * len(WIDTHS) / (time.perf_counter() - t1) / 1e9
 
-    all_cores = float(np.median([timed(sample, cores) for _ in range(runs)]))
+    all_runs = [timed(sample, cores) for _ in range(runs)]
+    all_cores = float(np.median(all_runs))
     one_thread = float(np.median([timed(one, 1) for _ in range(runs)]))
     del torch
     return {"value": round(all_cores, 4), "unit": "GB/s", "cores": cores, "kind": "oracle",
+            "runs_GBps": [round(x, 4) for x in all_runs],
             "one_thread_GBps": round(one_thread, 4),
             "cpu_model": _cpu_model(),
             "sample": f"first {sample >> 20} MiB of the 8 GiB array, counted once per w in "
@@ -383,8 +383,8 @@ def run_ours(args):
         counts_ok = {"all": bool(torch.equal(e, counts)),
                      "how": "all-reduced counters of the last step == the sum over ranks of "
                             "the CPU oracle's count of each rank's shard"}
-    elif rank == 0 and not args.no_verify:
-        counts_ok = _verify_counts(counts, data, args.warmup + args.steps)
+    # (the replicas' check against the oracle runs after every other section:
+    # its seconds of all-core host work must not disturb their measurements)
 
     # roofline read kernel on the same array
     rsum = torch.zeros(1, dtype=torch.int64, device=dev)
@@ -442,6 +442,8 @@ def run_ours(args):
                     extra[key] = fn()
                 except Exception as e:  # report, keep the line
                     extra[key] = {"error": f"{type(e).__name__}: {e}"}
+    if rank == 0 and not args.shard and not args.no_verify:
+        counts_ok = _verify_counts(counts, data, args.warmup + args.steps)
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
@@ -1064,10 +1066,13 @@ def run_reference(args):
     host = synth.bernoulli_bytes(sample, 0.5, seed=0)
     for _ in range(args.warmup):
         orc.bytes_mt(16, host[:1 << 20], cores)
+    step_rates = []
     t0 = time.perf_counter()
     for _ in range(args.steps):
+        t1 = time.perf_counter()
         for w in WIDTHS:
             orc.bytes_mt(w, host, cores)
+        step_rates.append(sample * len(WIDTHS) / (time.perf_counter() - t1) / 1e9)
     dt = time.perf_counter() - t0
     value = sample * len(WIDTHS) * args.steps / dt / 1e9
     desc = (f"first {args.ref_sample_mib} MiB of the 8 GiB Bernoulli(0.5) array (seed 0), "
@@ -1080,7 +1085,10 @@ def run_reference(args):
             "config": {"workload": WORKLOAD, "parallelism": "host cores",
                        "sample_bytes_per_step": sample * len(WIDTHS)},
             "cpu_baseline": {"value": round(value, 4), "unit": "GB/s", "cores": cores,
-                             "kind": "oracle", "sample": desc, "cpu_model": _cpu_model()},
+                             "kind": "oracle", "sample": desc, "cpu_model": _cpu_model(),
+                             "step_GBps_min_median_max": [round(min(step_rates), 4),
+                                                          round(float(np.median(step_rates)), 4),
+                                                          round(max(step_rates), 4)]},
             "e2e": {"value": round(value, 4), "unit": "GB/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -1096,7 +1104,9 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--batched-m", type=int, default=200000,
                     help="arrays in the batched section (200000 = the workload)")
-    ap.add_argument("--ref-sample-mib", type=int, default=16)
+    ap.add_argument("--ref-sample-mib", type=int, default=1024,
+                    help="sample of the array the reference arm counts per step (MiB; "
+                         "the same size as cpu_baseline's sample)")
     ap.add_argument("--shard", action="store_true",
                     help="split one array across the ranks (strong scaling) instead of "
                          "independent replicas")

@@ -93,12 +93,17 @@ TuneTable default_tune() {
   t.wait_cycles = kBulkWaitCycles;
   // serving (measured on GB300, Poisson traces at 0.3 / 0.6 / 0.9 of the
   // large-array rate): longer items for the larger classes under load, short
-  // wave-aligned items while lightly loaded
+  // wave-aligned items while lightly loaded; the largest class one request
+  // a batch, the smallest waiting request first
   t.serve[0] = ServeTune{8, 127, 64, 1024};
   t.serve[1] = ServeTune{32, 255, 64, 1024};
   t.serve[2] = ServeTune{127, 511, 64, 1024};
-  t.serve[3] = ServeTune{127, 511, 64, 1024};
+  t.serve[3] = ServeTune{0, 511, 64, 1};
   t.serve_light = uint64_t(512) << 20;
+  t.serve_strided = 0;
+  t.serve_order = 1;
+  t.multi_rows = 1024;
+  t.multi_strided = 1;
   t.set_source("built-in defaults");
   return t;
 }
@@ -134,6 +139,12 @@ TuneTable default_tune() {
 //                                  requests per batch (1 .. 1024))
 //   serve_light <bytes>           (in-flight input bytes below which the server counts
 //                                  as lightly loaded)
+//   serve_strided <0|1>           (1: a serving work item of a request of K items
+//                                  counts every K-th row; 0: a contiguous run)
+//   serve_order <0|1>             (a class's next batch takes its admitted requests in
+//                                  admission order (0) or smallest first (1))
+//   multi <rows> <0|1>            (pospopcnt_multi: most work-item rows, 8 .. 2^20,
+//                                  and 1 = items take every K-th row of their count)
 //   wait <cycles>                 (0 .. 2^31: how long a staged kernel waits for a
 //                                  stage's bulk copy, in SM clock cycles, before it
 //                                  reports POSPOP_ETIMEDOUT and leaves; default 2^31,
@@ -240,6 +251,16 @@ int parse_tune(const char *text, TuneTable *out, int *bad_line) {
     } else if (strcmp(kind, "serve_light") == 0) {
       if (n != 1 || a[0] < 0) return POSPOP_EINVAL;
       t.serve_light = (uint64_t)a[0];
+    } else if (strcmp(kind, "serve_strided") == 0) {
+      if (n != 1 || a[0] < 0 || a[0] > 1) return POSPOP_EINVAL;
+      t.serve_strided = (uint32_t)a[0];
+    } else if (strcmp(kind, "serve_order") == 0) {
+      if (n != 1 || a[0] < 0 || a[0] > 1) return POSPOP_EINVAL;
+      t.serve_order = (uint32_t)a[0];
+    } else if (strcmp(kind, "multi") == 0) {
+      if (n != 2 || a[0] < 8 || a[0] > (1 << 20) || a[1] < 0 || a[1] > 1) return POSPOP_EINVAL;
+      t.multi_rows = (uint32_t)a[0];
+      t.multi_strided = (uint32_t)a[1];
     } else if (strcmp(kind, "wait") == 0) {
       if (n != 1 || a[0] < 0 || a[0] > kBulkWaitCycles) return POSPOP_EINVAL;
       t.wait_cycles = a[0];
@@ -339,7 +360,11 @@ std::string format_tune(const DevCtx &ctx, const TuneTable &t) {
              e.cap);
     s += line;
   }
-  snprintf(line, sizeof line, "serve_light %llu\n", (unsigned long long)t.serve_light);
+  snprintf(line, sizeof line, "serve_light %llu\nserve_strided %u\nserve_order %u\n",
+           (unsigned long long)t.serve_light, t.serve_strided, t.serve_order);
+  s += line;
+  snprintf(line, sizeof line, "# multi <most item rows> <0 contiguous | 1 strided items>\nmulti %u %u\n",
+           t.multi_rows, t.multi_strided);
   s += line;
   if (t.wait_cycles != kBulkWaitCycles) {
     snprintf(line, sizeof line, "wait %lld\n", t.wait_cycles);
@@ -426,6 +451,15 @@ static int init_ctx(DevCtx &c, int device) {
       return POSPOP_ECUDA;
     }
     c.occ_serve[i] = n > 0 ? n : 1;
+  }
+  for (int i = 0; i < multi_variant_count(); i++) {
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, multi_variant(i).fn,
+                                                      multi_variant(i).bs, 0) != cudaSuccess) {
+      cudaGetLastError();
+      return POSPOP_ECUDA;
+    }
+    c.occ_multi[i] = n > 0 ? n : 1;
   }
   for (int i = 0; i < roofline_variant_count(); i++) {
     const Variant &v = roofline_variant(i);
@@ -1286,17 +1320,23 @@ int pospopcnt_multi(size_t n, const int *w, uint64_t *const *counts, const void 
     std::lock_guard<std::mutex> g(c->mu);
     t = c->tune;
   }
-  // the launch shape of the w = 32 batch entry (counts mix widths); work
-  // items of at most kMultiItemRows rows and at least 8, wave-aligned over
-  // the whole group, so that a group of small counts still spreads over the
-  // GPU and a group of large ones runs in whole waves
-  constexpr uint32_t kMultiItemRows = 127;
-  const int vi = t.batch[width_group(32)].variant;
+  // the launch shape of the single-array entry for the group's mean count
+  // size (w = 32 group: counts mix widths); work items of at most the tune
+  // entry's rows and at least 8, wave-aligned over the whole group, so that
+  // a group of small counts still spreads over the GPU and a group of large
+  // ones runs in whole waves of long items (the per-item set-up and final
+  // accumulation then cost little per byte); contiguous or strided items
+  // per the entry
+  const Variant &sv =
+      stream_variant(t.stream[width_group(32)][size_class(rows / reqs.size())].variant);
+  int vi = find_variant(true, sv.bs, sv.minb, sv.depth, sv.hint);
+  if (vi < 0) vi = t.batch[width_group(32)].variant;
   const Variant &v = multi_variant(vi);
-  const uint32_t ir = serve_light_rows(*c, vi, rows, kMultiItemRows, 8);
+  const uint32_t ir = serve_light_rows(*c, vi, rows, t.multi_rows, 8);
   static thread_local ServeParams P;   // about 10 KiB: not on the caller's stack
   memset(&P, 0, offsetof(ServeParams, req));
   P.item_rows = ir;
+  P.strided = t.multi_strided;
   const uint64_t wpb = (uint64_t)v.bs / 32;
   for (size_t k0 = 0; k0 < reqs.size(); k0 += kServeMax) {
     const size_t cnt = std::min<size_t>(kServeMax, reqs.size() - k0);
@@ -1311,8 +1351,12 @@ int pospopcnt_multi(size_t n, const int *w, uint64_t *const *counts, const void 
     P.item_start[cnt] = items;
     P.n = (uint32_t)cnt;
     P.total = items;
-    // one work item per warp (the kernel's grid-stride loop covers a cap)
-    const uint64_t grid = std::min<uint64_t>((items + wpb - 1) / wpb, uint64_t(1) << 20);
+    // a persistent grid of at most one wave: each warp takes items i, i + NW,
+    // ... in the kernel's grid-stride loop (four 1 GiB counts in one launch:
+    // one item per warp in 28 waves of short-lived blocks read at 6.78 TB/s
+    // against 7.13 TB/s for four single launches)
+    const uint64_t wave = (uint64_t)c->sms * (uint64_t)c->occ_multi[vi];
+    const uint64_t grid = std::min<uint64_t>((items + wpb - 1) / wpb, wave);
     void *args[] = {&P};
     if (launch_kernel(v.fn, dim3((unsigned)grid), dim3(v.bs), args,
                       static_cast<cudaStream_t>(stream), t.pdl != 0) != cudaSuccess) {

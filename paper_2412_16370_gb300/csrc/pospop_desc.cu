@@ -4,7 +4,10 @@
 // in place through the constant cache: no upload copy before the launch).
 //
 // Work items (item_rows rows of 512 B of one request, as in the batched
-// count) are dealt to warps round-robin; each is counted with the paper's
+// count: either a contiguous run of rows, or with `strided` every K-th row
+// of a request of K items, so that warps on neighbouring items read
+// neighbouring rows as the single-array kernel's warps do) are dealt to
+// warps round-robin; each is counted with the paper's
 // per-thread algorithm (Section 4) and folded into its request slot's
 // counters.  The warp that finishes a request's last work item reads and
 // clears its counters, resets the slot's completion counter, publishes the
@@ -60,10 +63,21 @@ __global__ void __launch_bounds__(BS, MINB) serve_kernel(const __grid_constant__
     const int w = rq.w;
     const uint32_t rot = (8u * s.head) & (uint32_t)(w - 1);
     const uint64_t R = span_rows(s);
-    const uint64_t r0 = (i - P.item_start[k]) * P.item_rows;
-    const uint64_t r1 = (r0 + P.item_rows < R) ? r0 + P.item_rows : R;
+    const uint64_t kk = i - P.item_start[k];   // the item's index within its request
+    uint64_t r0, stride, nrows;
+    if (P.strided) {
+      // rows kk, kk + K, ...: at most ceil(R / K) <= item_rows of them
+      const uint64_t K = rq.items;
+      r0 = kk;
+      stride = K;
+      nrows = R > kk ? (R - kk + K - 1) / K : 0;
+    } else {
+      r0 = kk * P.item_rows;
+      stride = 1;
+      nrows = ((r0 + P.item_rows < R) ? r0 + P.item_rows : R) - r0;
+    }
     uint32_t cnt[4] = {0u, 0u, 0u, 0u};
-    count_rows<DEPTH, HINT>(s, r0, 1, r1 - r0, lane, xk, cnt, PlainLoader<HINT>{});
+    count_rows<DEPTH, HINT>(s, r0, stride, nrows, lane, xk, cnt, PlainLoader<HINT>{});
     if (ADD) {
       unsigned long long *dst = rq.out;
       fold_counts(cnt, w, rot, lane, [&](uint32_t j, unsigned long long v) {

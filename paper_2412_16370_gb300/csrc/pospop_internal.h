@@ -87,6 +87,9 @@ struct ServeParams {
   unsigned int *flags;          // one per request slot (mapped pinned host memory)
   uint32_t seq;                 // value written to a finished request's flag
   uint32_t slot0;               // request slot of req[0]
+  uint32_t strided;             // 1: item k of a request of K items counts rows k, k + K, ...
+                                // (warps on neighbouring items read neighbouring rows);
+                                // 0: item k counts rows k * item_rows .. + item_rows - 1
   ServeReq req[kServeMax];
   uint64_t item_start[kServeMax + 1];
 };

@@ -66,6 +66,11 @@ struct TuneTable {
                                 // bulk-copy staging with ring shape k - 1
   ServeTune serve[kServeClasses];
   uint64_t serve_light;         // in-flight input bytes below which the server counts as light
+  uint32_t serve_strided;       // 1: serving work items take every K-th row of a request
+  uint32_t serve_order;         // 0: a class's batch takes admitted requests in admission
+                                // order; 1: smallest first
+  uint32_t multi_rows;          // pospopcnt_multi: most work-item rows (wave-aligned, at least 8)
+  uint32_t multi_strided;       // pospopcnt_multi: 1 = items take every K-th row of their count
   long long wait_cycles;        // limit of a staged kernel's wait for a bulk copy (SM clock
                                 // cycles, 0 .. kBulkWaitCycles; 0 = give up at once)
   char source[240];             // where the table came from (copied with the table: no heap)
@@ -123,6 +128,7 @@ struct DevCtx {
   int occ_roof[16] = {0};
   int occ_select_staged[16] = {0};
   int occ_serve[64] = {0};
+  int occ_multi[64] = {0};
 };
 
 // Returns the context of the current device, setting it up if needed, or

@@ -105,6 +105,8 @@ struct LoopTune {
   BatchTune bt;
   ServeTune cls[kServeClasses];
   uint64_t light;
+  uint32_t strided;
+  uint32_t order;
 };
 
 int request_class(size_t nbytes, int levels) {
@@ -251,6 +253,7 @@ int launch_batch(pospop_server &srv, Batch &b, const LoopTune &lt, size_t load_b
     P.flags = b.dflags;
     P.seq = b.seq;
     P.slot0 = (uint32_t)k0;
+    P.strided = lt.strided;
     uint64_t items = 0;
     for (int k = 0; k < cnt; k++) {
       const Request *r = b.reqs[k0 + k];
@@ -341,6 +344,8 @@ void serve_loop(pospop_server *srv) {
       lt.bt = srv->ctx->tune.batch[kServeWidthGroup];
       for (int k = 0; k < kServeClasses; k++) lt.cls[k] = srv->ctx->tune.serve[k];
       lt.light = srv->ctx->tune.serve_light;
+      lt.strided = srv->ctx->tune.serve_strided;
+      lt.order = srv->ctx->tune.serve_order;
     }
     // 1. completions, without the lock: requests whose flag the device has
     //    raised, and whole batches whose event has fired (which frees the
@@ -451,11 +456,23 @@ void serve_loop(pospop_server *srv) {
         std::deque<Request *> keep;
         for (Request *r : srv->admitted) {
           const int k = request_class(r->nbytes, srv->levels);
-          const size_t cap = std::min<size_t>(kBatchCap, lt.cls[k].cap);
-          if (free_b[k] && take[k].size() < cap)
-            take[k].push_back(r);
+          if (free_b[k])
+            take[k].push_back(r);   // candidates, trimmed to the class's cap below
           else
             keep.push_back(r);
+        }
+        for (int k = 0; k < kServeClasses; k++) {
+          const size_t cap = std::min<size_t>(kBatchCap, lt.cls[k].cap);
+          if (take[k].size() <= cap) continue;
+          // serve_order 1: the smallest requests of the class first
+          // (shortest-remaining-first among the waiting), else admission order
+          if (lt.order)
+            std::stable_sort(take[k].begin(), take[k].end(), [](const Request *x,
+                                                                 const Request *y) {
+              return x->nbytes < y->nbytes;
+            });
+          for (size_t j = cap; j < take[k].size(); j++) keep.push_back(take[k][j]);
+          take[k].resize(cap);
         }
         srv->admitted.swap(keep);
         for (int k = 0; k < kServeClasses; k++) {

@@ -248,7 +248,7 @@ extern "C" int pospopcnt_autotune(size_t max_bytes, const char *path) {
     const double hi[kServeClasses] = {1048576, 16777216, 134217728, 268435456};
     const std::vector<uint32_t> rows_set[kServeClasses] = {
         {31, 63, 127}, {63, 127, 255}, {127, 255, 511}, {127, 255, 511}};
-    const uint32_t light_set[] = {8, 16, 32, 63, 127};
+    const uint32_t light_set[] = {8, 16, 32, 63, 127, 0};   // 0: the class's `rows`
     const int sv = best.batch[width_group(32)].variant;   // the server's launch shape
     const Variant &v = serve_variant(sv);
     std::unique_ptr<ServeParams> P(new ServeParams());
@@ -269,6 +269,7 @@ extern "C" int pospopcnt_autotune(size_t max_bytes, const char *path) {
       P->flags = dflags;
       P->seq = 1;
       P->slot0 = 0;
+      P->strided = best.serve_strided;
       uint64_t items = 0;
       for (size_t k = 0; k < reqs.size(); k++) {
         const uint64_t it = (serve_rows(reqs[k].ptr, reqs[k].nbytes) + ir - 1) / ir;

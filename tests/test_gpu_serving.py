@@ -143,6 +143,28 @@ def serve_tune(gpu, tmp_path):
     pp.pospopcnt_tune_load(str(saved))
 
 
+def test_strided_items_mix_equals_oracle(gpu, orc, pool, serve_tune):
+    """Tune entry `serve_strided 1` (a work item takes every K-th row of its
+    request) at light and full load: every result equals the oracle's."""
+    n = 400
+    w, nbytes, offs = _requests(n, 21, 1, 24 * MIB, 256 * MIB)
+    nbytes[::41] = 0
+    host = pool.cpu().numpy()
+    for light in ("serve_light 0", "serve_light 68719476736"):
+        serve_tune("serve_strided 1", light)
+        srv = pp.pospop_server_create(1 << 30, 512, 4)
+        try:
+            results = np.zeros((n, 64), dtype=np.uint64)
+            recs = pp.pospop_server_run_trace(srv, (np.arange(n) * 3000).astype(np.int64), w,
+                                              pool.data_ptr() + offs, nbytes, results)
+        finally:
+            pp.pospop_server_destroy(srv)
+        assert (recs["status"] == 0).all()
+        for k in range(n):
+            seg = host[int(offs[k]):int(offs[k]) + int(nbytes[k])]
+            assert np.array_equal(results[k, :w[k]], orc.bytes(int(w[k]), seg)), (light, k)
+
+
 def test_lone_large_request(gpu, orc, pool):
     """One 128 MiB request on an idle server (its work items are spread over
     every SM): the result equals the oracle's count."""
