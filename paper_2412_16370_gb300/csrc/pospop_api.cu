@@ -102,6 +102,7 @@ TuneTable default_tune() {
   t.serve_light = uint64_t(512) << 20;
   t.serve_strided = 0;
   t.serve_order = 1;
+  t.serve_promote_us = 0;
   t.multi_rows = 1024;
   t.multi_strided = 1;
   t.set_source("built-in defaults");
@@ -143,6 +144,9 @@ TuneTable default_tune() {
 //                                  counts every K-th row; 0: a contiguous run)
 //   serve_order <0|1>             (a class's next batch takes its admitted requests in
 //                                  admission order (0) or smallest first (1))
+//   serve_promote <us>            (0 = off; else requests of a class that have waited
+//                                  this long since they arrived may run as a batch on a
+//                                  free stream of the next smaller class, 1 .. 10^7)
 //   multi <rows> <0|1>            (pospopcnt_multi: most work-item rows, 8 .. 2^20,
 //                                  and 1 = items take every K-th row of their count)
 //   wait <cycles>                 (0 .. 2^31: how long a staged kernel waits for a
@@ -254,6 +258,9 @@ int parse_tune(const char *text, TuneTable *out, int *bad_line) {
     } else if (strcmp(kind, "serve_strided") == 0) {
       if (n != 1 || a[0] < 0 || a[0] > 1) return POSPOP_EINVAL;
       t.serve_strided = (uint32_t)a[0];
+    } else if (strcmp(kind, "serve_promote") == 0) {
+      if (n != 1 || a[0] < 0 || a[0] > 10000000) return POSPOP_EINVAL;
+      t.serve_promote_us = (uint32_t)a[0];
     } else if (strcmp(kind, "serve_order") == 0) {
       if (n != 1 || a[0] < 0 || a[0] > 1) return POSPOP_EINVAL;
       t.serve_order = (uint32_t)a[0];
@@ -360,8 +367,10 @@ std::string format_tune(const DevCtx &ctx, const TuneTable &t) {
              e.cap);
     s += line;
   }
-  snprintf(line, sizeof line, "serve_light %llu\nserve_strided %u\nserve_order %u\n",
-           (unsigned long long)t.serve_light, t.serve_strided, t.serve_order);
+  snprintf(line, sizeof line,
+           "serve_light %llu\nserve_strided %u\nserve_order %u\nserve_promote %u\n",
+           (unsigned long long)t.serve_light, t.serve_strided, t.serve_order,
+           t.serve_promote_us);
   s += line;
   snprintf(line, sizeof line, "# multi <most item rows> <0 contiguous | 1 strided items>\nmulti %u %u\n",
            t.multi_rows, t.multi_strided);

@@ -107,6 +107,7 @@ struct LoopTune {
   uint64_t light;
   uint32_t strided;
   uint32_t order;
+  int64_t promote_ns;
 };
 
 int request_class(size_t nbytes, int levels) {
@@ -234,7 +235,10 @@ int launch_batch(pospop_server &srv, Batch &b, const LoopTune &lt, size_t load_b
   b.seq = b.seq + 1 == 0 ? 1 : b.seq + 1;
   uint64_t rows = 0;
   for (const Request *r : b.reqs) rows += request_rows(r);
-  const uint32_t ir = batch_item_rows(srv, lt, b.level, rows, load_bytes);
+  // item rows of the requests' class (a promoted batch runs on a smaller
+  // class's stream); all requests of a batch are of one class
+  const int cls = b.reqs.empty() ? b.level : request_class(b.reqs[0]->nbytes, srv.levels);
+  const uint32_t ir = batch_item_rows(srv, lt, cls, rows, load_bytes);
   const Variant &v = serve_variant(lt.bt.variant);
   // host input: the batch stream waits for the requests' copies into the pool
   for (const Request *r : b.reqs)
@@ -346,6 +350,7 @@ void serve_loop(pospop_server *srv) {
       lt.light = srv->ctx->tune.serve_light;
       lt.strided = srv->ctx->tune.serve_strided;
       lt.order = srv->ctx->tune.serve_order;
+      lt.promote_ns = (int64_t)srv->ctx->tune.serve_promote_us * 1000;
     }
     // 1. completions, without the lock: requests whose flag the device has
     //    raised, and whole batches whose event has fired (which frees the
@@ -474,11 +479,40 @@ void serve_loop(pospop_server *srv) {
           for (size_t j = cap; j < take[k].size(); j++) keep.push_back(take[k][j]);
           take[k].resize(cap);
         }
+        // serve_promote: a class whose oldest waiting request has waited
+        // longer than the limit may use a free stream of the next smaller
+        // class (a higher stream priority) that this pass leaves unused
+        Batch *up_b[kServeClasses] = {nullptr, nullptr, nullptr, nullptr};
+        std::vector<Request *> up[kServeClasses];
+        if (lt.promote_ns > 0) {
+          for (int k = kServeClasses - 1; k >= 1; k--) {
+            if (!free_b[k - 1] || !take[k - 1].empty() || up_b[k - 1]) continue;
+            const size_t cap = std::min<size_t>(kBatchCap, lt.cls[k].cap);
+            std::deque<Request *> rest;
+            for (Request *r : keep) {
+              if (up[k].size() < cap && request_class(r->nbytes, srv->levels) == k &&
+                  tnow - r->rec.t_submit_ns > lt.promote_ns)
+                up[k].push_back(r);
+              else
+                rest.push_back(r);
+            }
+            if (!up[k].empty()) {
+              up_b[k - 1] = free_b[k - 1];
+              keep.swap(rest);
+            }
+          }
+        }
         srv->admitted.swap(keep);
         for (int k = 0; k < kServeClasses; k++) {
           if (take[k].empty()) continue;
           free_b[k]->busy = true;
           to_launch.emplace_back(free_b[k], std::move(take[k]));
+          progress = true;
+        }
+        for (int k = 1; k < kServeClasses; k++) {
+          if (up[k].empty()) continue;
+          up_b[k - 1]->busy = true;
+          to_launch.emplace_back(up_b[k - 1], std::move(up[k]));
           progress = true;
         }
       }

@@ -14,7 +14,7 @@ import torch
 from paper_2412_16370_gb300 import binding as pp
 from paper_2412_16370_gb300 import synth, synth_device
 
-from _gpu import counts_np
+from _gpu import counts_np, oracle_device_bytes
 
 pytestmark = pytest.mark.gpu
 
@@ -76,6 +76,23 @@ def test_large_group_in_whole_waves(gpu, orc, pool):
     for i in range(n):
         seg = host[3 + i * span:3 + (i + 1) * span]
         assert np.array_equal(got[i, :w[i]], orc.bytes(w[i], seg)), i
+
+
+def test_group_larger_than_l2(gpu, orc):
+    """Four 96 MiB counts (384 MiB, well past the 129 MB L2) in one launch,
+    unaligned starts, widths 8..64: each equals the oracle's count."""
+    span = 96 << 20
+    buf = torch.empty(4 * span + 64, dtype=torch.uint8, device=gpu)
+    synth_device.random_(buf, 778)
+    w = [8, 16, 32, 64]
+    c = torch.zeros((4, 64), dtype=torch.int64, device=gpu)
+    pp.pospopcnt_multi(w, [c[i] for i in range(4)],
+                       [buf.data_ptr() + 7 + i * span for i in range(4)], [span] * 4)
+    got = counts_np(c)
+    exp = {i: oracle_device_bytes(orc, (w[i],), buf[7 + i * span:7 + (i + 1) * span])[w[i]]
+           for i in range(4)}
+    for i in range(4):
+        assert np.array_equal(got[i, :w[i]], exp[i]), i
 
 
 def test_errors_count_nothing(gpu, orc, pool):

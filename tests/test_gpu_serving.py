@@ -165,6 +165,26 @@ def test_strided_items_mix_equals_oracle(gpu, orc, pool, serve_tune):
             assert np.array_equal(results[k, :w[k]], orc.bytes(int(w[k]), seg)), (light, k)
 
 
+def test_promoted_batches_equal_solo(gpu, pool, serve_tune):
+    """Tune entry `serve_promote 1` (requests that waited over 1 us may run on
+    the next smaller class's stream) with `serve_order 1`: a loaded trace of
+    mixed sizes still gives every request its single-array count."""
+    serve_tune("serve_promote 1", "serve_order 1", "serve 3 0 511 2 1", "serve 2 127 511 2 4")
+    n = 300
+    w, nbytes, offs = _requests(n, 23, 4096, 96 * MIB, 150 * MIB)
+    srv = pp.pospop_server_create(8 << 30, 1024, 2)
+    try:
+        results = np.zeros((n, 64), dtype=np.uint64)
+        recs = pp.pospop_server_run_trace(srv, (np.arange(n) * 2000).astype(np.int64), w,
+                                          pool.data_ptr() + offs, nbytes, results)
+    finally:
+        pp.pospop_server_destroy(srv)
+    assert (recs["status"] == 0).all()
+    solo = _solo(pool, w, nbytes, offs)
+    for k in range(n):
+        assert np.array_equal(results[k, :w[k]], solo[k, :w[k]]), k
+
+
 def test_lone_large_request(gpu, orc, pool):
     """One 128 MiB request on an idle server (its work items are spread over
     every SM): the result equals the oracle's count."""
