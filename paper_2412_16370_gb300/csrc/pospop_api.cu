@@ -103,6 +103,10 @@ TuneTable default_tune() {
   t.serve_strided = 0;
   t.serve_order = 1;
   t.serve_promote_us = 0;
+  // load variant 0 (the variant-1 serving kernels keep part of their state
+  // in local memory, 80-88 bytes a thread) and flush depth 32 (measured on
+  // GB300: 0.9-load p99 367-370 us against 395-397 us at depth 16)
+  t.serve_shape = find_variant(true, 512, 1, 32, 0);
   t.multi_rows = 1024;
   t.multi_strided = 1;
   t.set_source("built-in defaults");
@@ -144,6 +148,8 @@ TuneTable default_tune() {
 //                                  counts every K-th row; 0: a contiguous run)
 //   serve_order <0|1>             (a class's next batch takes its admitted requests in
 //                                  admission order (0) or smallest first (1))
+//   serve_shape <bs> <minb> <depth> <hint>
+//                                 (the serving kernel's launch shape)
 //   serve_promote <us>            (0 = off; else requests of a class that have waited
 //                                  this long since they arrived may run as a batch on a
 //                                  free stream of the next smaller class, 1 .. 10^7)
@@ -258,6 +264,11 @@ int parse_tune(const char *text, TuneTable *out, int *bad_line) {
     } else if (strcmp(kind, "serve_strided") == 0) {
       if (n != 1 || a[0] < 0 || a[0] > 1) return POSPOP_EINVAL;
       t.serve_strided = (uint32_t)a[0];
+    } else if (strcmp(kind, "serve_shape") == 0) {
+      if (n != 4) return POSPOP_EINVAL;
+      const int v = find_variant(true, (int)a[0], (int)a[1], (int)a[2], (int)a[3]);
+      if (v < 0) return POSPOP_EINVAL;
+      t.serve_shape = v;
     } else if (strcmp(kind, "serve_promote") == 0) {
       if (n != 1 || a[0] < 0 || a[0] > 10000000) return POSPOP_EINVAL;
       t.serve_promote_us = (uint32_t)a[0];
@@ -372,6 +383,11 @@ std::string format_tune(const DevCtx &ctx, const TuneTable &t) {
            (unsigned long long)t.serve_light, t.serve_strided, t.serve_order,
            t.serve_promote_us);
   s += line;
+  {
+    const Variant &v = serve_variant(t.serve_shape);
+    snprintf(line, sizeof line, "serve_shape %d %d %d %d\n", v.bs, v.minb, v.depth, v.hint);
+    s += line;
+  }
   snprintf(line, sizeof line, "# multi <most item rows> <0 contiguous | 1 strided items>\nmulti %u %u\n",
            t.multi_rows, t.multi_strided);
   s += line;
@@ -1330,14 +1346,48 @@ int pospopcnt_multi(size_t n, const int *w, uint64_t *const *counts, const void 
     t = c->tune;
   }
   // the launch shape of the single-array entry for the group's mean count
-  // size (w = 32 group: counts mix widths); work items of at most the tune
-  // entry's rows and at least 8, wave-aligned over the whole group, so that
-  // a group of small counts still spreads over the GPU and a group of large
-  // ones runs in whole waves of long items (the per-item set-up and final
-  // accumulation then cost little per byte); contiguous or strided items
-  // per the entry
-  const Variant &sv =
-      stream_variant(t.stream[width_group(32)][size_class(rows / reqs.size())].variant);
+  // size (w = 32 group: counts mix widths)
+  const StreamTune &st = t.stream[width_group(32)][size_class(rows / reqs.size())];
+  const Variant &sv = stream_variant(st.variant);
+  // Groups of large counts (every resident warp would get at least 32 rows
+  // of the mean count): the single-array kernel's grid-stride schedule over
+  // the group's rows, in the single-array entry's waves, one launch ramp and
+  // one tail for the whole group.
+  {
+    const uint64_t resident =
+        (uint64_t)c->sms * (uint64_t)c->occ_stream[st.variant] * (uint64_t)(sv.bs / 32);
+    const uint64_t nw = (uint64_t)c->sms * (uint64_t)std::max(1, st.ctas_per_sm) *
+                        (uint64_t)(sv.bs / 32);
+    uint64_t max_rows = 0;
+    for (const ServeReq &r : reqs) max_rows = std::max(max_rows, serve_rows(r.ptr, r.nbytes));
+    if (rows / reqs.size() >= 32 * resident && max_rows / nw < t.max_rows_per_warp &&
+        max_rows < (uint64_t(1) << 32) && nw < (uint64_t(1) << 32)) {
+      const Variant &mv = multi_stream_variant(st.variant);
+      static thread_local ServeParams Q;   // about 10 KiB: not on the caller's stack
+      memset(&Q, 0, offsetof(ServeParams, req));
+      for (size_t k0 = 0; k0 < reqs.size(); k0 += kServeMax) {
+        const size_t cnt = std::min<size_t>(kServeMax, reqs.size() - k0);
+        uint64_t first = 0;   // row 0 of count k in this launch's row sequence
+        for (size_t k = 0; k < cnt; k++) {
+          Q.req[k] = reqs[k0 + k];
+          Q.req[k].items = (uint32_t)(first % nw);   // the kernel's starting phase
+          first += serve_rows(Q.req[k].ptr, Q.req[k].nbytes);
+        }
+        Q.n = (uint32_t)cnt;
+        void *args[] = {&Q};
+        if (launch_kernel(mv.fn, dim3((unsigned)(nw / (sv.bs / 32))), dim3(mv.bs), args,
+                          static_cast<cudaStream_t>(stream), t.pdl != 0) != cudaSuccess) {
+          cudaGetLastError();
+          return POSPOP_ECUDA;
+        }
+        note_launches(1);
+      }
+      return POSPOP_OK;
+    }
+  }
+  // Otherwise work items of at most the `multi` entry's rows and at least
+  // 8, wave-aligned over the whole group, so that a group of small counts
+  // still spreads over the GPU; contiguous or strided items per the entry.
   int vi = find_variant(true, sv.bs, sv.minb, sv.depth, sv.hint);
   if (vi < 0) vi = t.batch[width_group(32)].variant;
   const Variant &v = multi_variant(vi);
@@ -1345,7 +1395,10 @@ int pospopcnt_multi(size_t n, const int *w, uint64_t *const *counts, const void 
   static thread_local ServeParams P;   // about 10 KiB: not on the caller's stack
   memset(&P, 0, offsetof(ServeParams, req));
   P.item_rows = ir;
-  P.strided = t.multi_strided;
+  // strided items use 32-bit row arithmetic in the kernel
+  uint64_t biggest = 0;
+  for (const ServeReq &r : reqs) biggest = std::max(biggest, serve_rows(r.ptr, r.nbytes));
+  P.strided = (t.multi_strided && biggest < (uint64_t(1) << 32)) ? 1u : 0u;
   const uint64_t wpb = (uint64_t)v.bs / 32;
   for (size_t k0 = 0; k0 < reqs.size(); k0 += kServeMax) {
     const size_t cnt = std::min<size_t>(kServeMax, reqs.size() - k0);

@@ -67,10 +67,12 @@ __global__ void __launch_bounds__(BS, MINB) serve_kernel(const __grid_constant__
     uint64_t r0, stride, nrows;
     if (P.strided) {
       // rows kk, kk + K, ...: at most ceil(R / K) <= item_rows of them
-      const uint64_t K = rq.items;
+      // (32-bit: the host keeps strided requests below 2^32 rows, and a
+      // 64-bit division's call would spill the CSA state)
+      const uint32_t K = rq.items, k32 = (uint32_t)kk, R32 = (uint32_t)R;
       r0 = kk;
       stride = K;
-      nrows = R > kk ? (R - kk + K - 1) / K : 0;
+      nrows = R32 > k32 ? (R32 - k32 - 1) / K + 1 : 0;
     } else {
       r0 = kk * P.item_rows;
       stride = 1;

@@ -165,6 +165,11 @@ const Variant &serve_variant(int i);
 // each count added into its own counters, no completion tracking.
 int multi_variant_count();
 const Variant &multi_variant(int i);
+// pospopcnt_multi for groups of large counts: the single-array kernel's
+// grid-stride schedule over the group's rows (same order as the stream
+// kernel table).
+int multi_stream_variant_count();
+const Variant &multi_stream_variant(int i);
 int gather_variant_count();
 const Variant &gather_variant(int i);
 int gather256_variant_count();

@@ -71,6 +71,8 @@ struct TuneTable {
                                 // order; 1: smallest first
   uint32_t serve_promote_us;    // > 0: requests that have waited this long since they arrived
                                 // may run on a free stream of the next smaller class
+  int serve_shape;              // serving kernel's launch shape (index into the serve and
+                                // batch families: block size, flush depth, load variant)
   uint32_t multi_rows;          // pospopcnt_multi: most work-item rows (wave-aligned, at least 8)
   uint32_t multi_strided;       // pospopcnt_multi: 1 = items take every K-th row of their count
   long long wait_cycles;        // limit of a staged kernel's wait for a bulk copy (SM clock

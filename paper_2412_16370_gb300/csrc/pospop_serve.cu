@@ -93,16 +93,13 @@ struct Batch {
 // otherwise, batch streams running at once, requests per batch).
 constexpr size_t kClassBound[kServeClasses - 1] = {size_t(1) << 20, size_t(16) << 20,
                                                    size_t(128) << 20};
-// batches mix widths 8..64: they take the w = 32 batch entry of the tune table
-// (block shape, flush depth, load variant)
-constexpr int kServeWidthGroup = width_group(32);
 constexpr size_t kBatchCap = 1024;      // requests per batch, at most (4 launches of kServeMax)
 constexpr uint64_t kMaxServeGrid = uint64_t(1) << 20;
 constexpr uint32_t kMinItemRows = 8;    // the shortest light-load work item
 
 // The tune-table entries the loop works with (copied once per loop pass).
 struct LoopTune {
-  BatchTune bt;
+  int shape;   // the serving kernel's launch shape (tune entry serve_shape)
   ServeTune cls[kServeClasses];
   uint64_t light;
   uint32_t strided;
@@ -221,7 +218,7 @@ uint32_t batch_item_rows(const pospop_server &srv, const LoopTune &lt, int level
                          size_t load_bytes) {
   const ServeTune &st = lt.cls[level];
   if (load_bytes >= lt.light) return st.rows;
-  return serve_light_rows(*srv.ctx, lt.bt.variant, rows,
+  return serve_light_rows(*srv.ctx, lt.shape, rows,
                           std::min(st.light_rows ? st.light_rows : st.rows, st.rows));
 }
 
@@ -239,7 +236,7 @@ int launch_batch(pospop_server &srv, Batch &b, const LoopTune &lt, size_t load_b
   // class's stream); all requests of a batch are of one class
   const int cls = b.reqs.empty() ? b.level : request_class(b.reqs[0]->nbytes, srv.levels);
   const uint32_t ir = batch_item_rows(srv, lt, cls, rows, load_bytes);
-  const Variant &v = serve_variant(lt.bt.variant);
+  const Variant &v = serve_variant(lt.shape);
   // host input: the batch stream waits for the requests' copies into the pool
   for (const Request *r : b.reqs)
     if (r->ev && cudaStreamWaitEvent(b.s, r->ev, 0) != cudaSuccess) {
@@ -257,7 +254,7 @@ int launch_batch(pospop_server &srv, Batch &b, const LoopTune &lt, size_t load_b
     P.flags = b.dflags;
     P.seq = b.seq;
     P.slot0 = (uint32_t)k0;
-    P.strided = lt.strided;
+    P.strided = lt.strided;   // requests are at most the budget: far below 2^32 rows
     uint64_t items = 0;
     for (int k = 0; k < cnt; k++) {
       const Request *r = b.reqs[k0 + k];
@@ -345,7 +342,7 @@ void serve_loop(pospop_server *srv) {
     bool progress = false;
     {
       std::lock_guard<std::mutex> g(srv->ctx->mu);
-      lt.bt = srv->ctx->tune.batch[kServeWidthGroup];
+      lt.shape = srv->ctx->tune.serve_shape;
       for (int k = 0; k < kServeClasses; k++) lt.cls[k] = srv->ctx->tune.serve[k];
       lt.light = srv->ctx->tune.serve_light;
       lt.strided = srv->ctx->tune.serve_strided;

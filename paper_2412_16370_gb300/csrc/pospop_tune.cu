@@ -249,7 +249,7 @@ extern "C" int pospopcnt_autotune(size_t max_bytes, const char *path) {
     const std::vector<uint32_t> rows_set[kServeClasses] = {
         {31, 63, 127}, {63, 127, 255}, {127, 255, 511}, {127, 255, 511}};
     const uint32_t light_set[] = {8, 16, 32, 63, 127, 0};   // 0: the class's `rows`
-    const int sv = best.batch[width_group(32)].variant;   // the server's launch shape
+    const int sv = best.serve_shape;   // the server's launch shape
     const Variant &v = serve_variant(sv);
     std::unique_ptr<ServeParams> P(new ServeParams());
     unsigned long long *dres = nullptr;

@@ -43,7 +43,8 @@ def test_per_width_and_every_width_entries(pp, tmp_path):
               "serve 0 8 127 64 1024", "serve 3 0 127 1 1", "serve_light 0",
               "serve_light 536870912", "batch_rows 1 8 127 511", "batch_rows 16 2 16 255 2047",
               "serve_strided 1", "serve_strided 0", "serve_order 1", "multi 8 0",
-              "serve_promote 0", "serve_promote 250",
+              "serve_promote 0", "serve_promote 250", "serve_shape 512 1 16 0",
+              "serve_shape 256 2 32 1",
               "multi 1048576 1",
               "stream 4 512 1 16 0 3 1   # trailing comment"]
     assert _check(pp, tmp_path, "\n".join(lines) + "\n") == 0
@@ -82,6 +83,7 @@ def test_per_width_and_every_width_entries(pp, tmp_path):
     "serve_strided 2", "serve_strided", "serve_strided 1 1",
     "serve_order 2", "serve_order", "multi 7 0", "multi 1048577 0", "multi 4096 2", "multi 4096",
     "serve_promote -1", "serve_promote 10000001", "serve_promote",
+    "serve_shape 500 1 16 0", "serve_shape 512 1 16", "serve_shape 512 1 24 0",
 ])
 def test_malformed_line_is_reported_with_its_number(pp, tmp_path, bad):
     text = "# header\nstream 0 256 2 16 1 1 2\n\n" + bad + "\npdl 1\n"
