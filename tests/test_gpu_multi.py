@@ -78,6 +78,25 @@ def test_large_group_in_whole_waves(gpu, orc, pool):
         assert np.array_equal(got[i, :w[i]], orc.bytes(w[i], seg)), i
 
 
+def test_large_counts_grid_stride(gpu, orc):
+    """A group of large counts (the grid-stride form: four 512 MiB counts,
+    unaligned starts, widths 8..64) with two tiny counts and an empty one in
+    it: every count equals the oracle's."""
+    span = 512 << 20
+    buf = torch.empty(4 * span + 4096, dtype=torch.uint8, device=gpu)
+    synth_device.random_(buf, 779)
+    w = [8, 16, 32, 64, 16, 8, 32]
+    starts = [3 + i * span for i in range(4)] + [4 * span + 5, 4 * span + 100, 0]
+    sizes = [span] * 4 + [1, 777, 0]
+    c = torch.zeros((7, 64), dtype=torch.int64, device=gpu)
+    pp.pospopcnt_multi(w, [c[i] for i in range(7)], [buf.data_ptr() + a for a in starts], sizes)
+    got = counts_np(c)
+    for i in range(7):
+        exp = (oracle_device_bytes(orc, (w[i],), buf[starts[i]:starts[i] + sizes[i]])[w[i]]
+               if sizes[i] else np.zeros(w[i], dtype=np.uint64))
+        assert np.array_equal(got[i, :w[i]], exp), i
+
+
 def test_group_larger_than_l2(gpu, orc):
     """Four 96 MiB counts (384 MiB, well past the 129 MB L2) in one launch,
     unaligned starts, widths 8..64: each equals the oracle's count."""
