@@ -843,11 +843,20 @@ def _serving(pp, synth, pool, pool_bytes, large_gbs, dev, loads=(0.3, 0.6, 0.9),
     import torch
     lo, hi = 64, 256 << 20
     mean = (hi - lo) / math.log((hi + 1) / lo)      # mean of the log-uniform size
+    tune = {l.split()[0]: l.split()[1:] for l in pp.pospopcnt_tune_describe().splitlines()
+            if l.startswith(("serve_mode", "serve_srf"))}
+    if tune.get("serve_mode", ["0"])[0] == "1":
+        b, nl, rows = tune["serve_srf"]
+        schedule = (f"dispatch by remaining bytes: smallest remaining first, {int(b) >> 20} MiB "
+                    f"of work items a launch, {min(8, int(nl))} launches in flight, "
+                    f"{rows} rows a work item under load")
+    else:
+        schedule = ("size classes below 1 MiB / 16 MiB / 128 MiB / above on prioritised "
+                    "streams, 8 batch streams a class")
     out = {"workload": "Poisson arrivals; w uniform in {8,16,32,64}; sizes log-uniform "
                        "64 B..256 MiB at uniform offsets of the resident 8 GiB array",
-           "mem_budget_bytes": budget, "max_inflight": 4096, "batch_streams_per_size_class": 8,
-           "size_classes": "below 1 MiB / 16 MiB / 128 MiB / above, on prioritised streams",
-           "loads": []}
+           "mem_budget_bytes": budget, "max_inflight": 4096, "max_batches": 8,
+           "schedule": schedule, "loads": []}
     for k, load in enumerate(loads):
         rate = load * large_gbs * 1e9 / mean
         n = max(100, int(rate * duration_s))

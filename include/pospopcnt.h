@@ -283,21 +283,34 @@ int pospopcnt_graph_destroy(void *graph);
  *
  * A request is admitted when the input bytes of all admitted, unfinished
  * requests plus its own fit `mem_budget` and fewer than `max_inflight` are
- * admitted.  Admitted requests fall into size classes (below 1 MiB, 16 MiB,
- * 128 MiB, and above; as many classes as the device has stream priority
- * levels, at most four), and each class has `max_batches` streams with a
- * priority that falls as the class grows.  A class's admitted requests are
- * gathered into one batch as soon as one of its streams is free, so requests
- * arriving while others run are counted in the next batch while earlier
- * batches are still on the device, and blocks of a smaller class run before
- * waiting blocks of a larger one.  The tune table's `serve` entry of each
- * class sets its work-item rows (while the server is lightly loaded, and
- * otherwise), how many of its batches may run at once (at most
- * `max_batches`) and how many requests a batch takes (at most 1024);
- * `serve_light` sets the in-flight bytes below which the server counts as
- * lightly loaded.  The server reads them as it goes.  Each result is the
- * same as the request's single-array count.  Waits are bounded by the
- * caller's timeouts.
+ * admitted (and, in the default mode, at most 16384 at once).  The tune
+ * table's `serve_mode` entry, read when a server is created, picks one of
+ * two schedules.
+ *
+ * `serve_mode 1` (the default): admitted requests are ordered by the bytes
+ * they still have to count, and whenever one of the server's highest-
+ * priority streams is free (`serve_srf`'s <launches> of them, at most
+ * `max_batches`) a launch takes work items of the smallest first, up to
+ * <bytes> of them, so a large request is counted over several launches and
+ * smaller arrivals overtake it at the next launch.  Each request keeps one
+ * server-wide slot of counters until its last item is done.
+ *
+ * `serve_mode 0`: admitted requests fall into size classes (below 1 MiB,
+ * 16 MiB, 128 MiB, and above; as many classes as the device has stream
+ * priority levels, at most four), and each class has `max_batches` streams
+ * with a priority that falls as the class grows.  A class's admitted
+ * requests are gathered into one batch as soon as one of its streams is
+ * free, so requests arriving while others run are counted in the next batch
+ * while earlier batches are still on the device, and blocks of a smaller
+ * class run before waiting blocks of a larger one.  The tune table's `serve`
+ * entry of each class sets its work-item rows (while the server is lightly
+ * loaded, and otherwise), how many of its batches may run at once (at most
+ * `max_batches`) and how many requests a batch takes (at most 1024).
+ *
+ * In both modes `serve_light` sets the in-flight bytes below which the
+ * server counts as lightly loaded (work items then spread a request over
+ * every SM), each result is the same as the request's single-array count,
+ * and waits are bounded by the caller's timeouts.
  * ---------------------------------------------------------------------------
  */
 typedef struct pospop_server pospop_server;

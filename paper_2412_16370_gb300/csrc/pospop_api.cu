@@ -107,6 +107,14 @@ TuneTable default_tune() {
   // in local memory, 80-88 bytes a thread) and flush depth 32 (measured on
   // GB300: 0.9-load p99 367-370 us against 395-397 us at depth 16)
   t.serve_shape = find_variant(true, 512, 1, 32, 0);
+  // dispatch by remaining bytes, 128 MiB of work items a launch, four
+  // launches in flight (measured on GB300 with a Poisson trace at 0.9 load:
+  // p99 261-265 us against 366-370 us for the size classes, and the same
+  // latency for a lone request)
+  t.serve_mode = 1;
+  t.srf_bytes = uint64_t(128) << 20;
+  t.srf_launches = 4;
+  t.srf_rows = 255;
   t.multi_rows = 1024;
   t.multi_strided = 1;
   t.set_source("built-in defaults");
@@ -150,6 +158,12 @@ TuneTable default_tune() {
 //                                  admission order (0) or smallest first (1))
 //   serve_shape <bs> <minb> <depth> <hint>
 //                                 (the serving kernel's launch shape)
+//   serve_mode <0|1>              (read when a server is created: 0 = size classes on
+//                                  prioritised streams; 1 = dispatch by remaining bytes)
+//   serve_srf <bytes> <launches> <rows>
+//                                 (serve_mode 1: work-item bytes per launch, at least one
+//                                  item; launches in flight, 1 .. 64; rows per item,
+//                                  1 .. 2^20)
 //   serve_promote <us>            (0 = off; else requests of a class that have waited
 //                                  this long since they arrived may run as a batch on a
 //                                  free stream of the next smaller class, 1 .. 10^7)
@@ -264,6 +278,15 @@ int parse_tune(const char *text, TuneTable *out, int *bad_line) {
     } else if (strcmp(kind, "serve_strided") == 0) {
       if (n != 1 || a[0] < 0 || a[0] > 1) return POSPOP_EINVAL;
       t.serve_strided = (uint32_t)a[0];
+    } else if (strcmp(kind, "serve_mode") == 0) {
+      if (n != 1 || a[0] < 0 || a[0] > 1) return POSPOP_EINVAL;
+      t.serve_mode = (uint32_t)a[0];
+    } else if (strcmp(kind, "serve_srf") == 0) {
+      if (n != 3 || a[2] < 1 || a[2] > (1 << 20) || a[1] < 1 || a[1] > 64 || a[0] < 512 * a[2])
+        return POSPOP_EINVAL;
+      t.srf_bytes = (uint64_t)a[0];
+      t.srf_launches = (uint32_t)a[1];
+      t.srf_rows = (uint32_t)a[2];
     } else if (strcmp(kind, "serve_shape") == 0) {
       if (n != 4) return POSPOP_EINVAL;
       const int v = find_variant(true, (int)a[0], (int)a[1], (int)a[2], (int)a[3]);
@@ -385,7 +408,9 @@ std::string format_tune(const DevCtx &ctx, const TuneTable &t) {
   s += line;
   {
     const Variant &v = serve_variant(t.serve_shape);
-    snprintf(line, sizeof line, "serve_shape %d %d %d %d\n", v.bs, v.minb, v.depth, v.hint);
+    snprintf(line, sizeof line, "serve_shape %d %d %d %d\nserve_mode %u\nserve_srf %llu %u %u\n",
+             v.bs, v.minb, v.depth, v.hint, t.serve_mode, (unsigned long long)t.srf_bytes,
+             t.srf_launches, t.srf_rows);
     s += line;
   }
   snprintf(line, sizeof line, "# multi <most item rows> <0 contiguous | 1 strided items>\nmulti %u %u\n",
@@ -1330,7 +1355,7 @@ int pospopcnt_multi(size_t n, const int *w, uint64_t *const *counts, const void 
     if (!device_addressable(counts[i], c->device, &dc) ||
         !device_addressable(ptrs[i], c->device, &dp))
       return POSPOP_EPTR;
-    ServeReq r;
+    ServeReq r{};   // item0 0: every item of the count is in this launch
     r.ptr = dp;
     r.nbytes = nbytes[i];
     r.w = w[i];
@@ -1395,7 +1420,6 @@ int pospopcnt_multi(size_t n, const int *w, uint64_t *const *counts, const void 
   const uint32_t ir = serve_light_rows(*c, vi, rows, t.multi_rows, 8);
   static thread_local ServeParams P;   // about 10 KiB: not on the caller's stack
   memset(&P, 0, offsetof(ServeParams, req));
-  P.item_rows = ir;
   // strided items use 32-bit row arithmetic in the kernel
   uint64_t biggest = 0;
   for (const ServeReq &r : reqs) biggest = std::max(biggest, serve_rows(r.ptr, r.nbytes));
@@ -1407,6 +1431,7 @@ int pospopcnt_multi(size_t n, const int *w, uint64_t *const *counts, const void 
     for (size_t k = 0; k < cnt; k++) {
       ServeReq r = reqs[k0 + k];
       r.items = (uint32_t)((serve_rows(r.ptr, r.nbytes) + ir - 1) / ir);
+      r.rows = ir;
       P.item_start[k] = items;
       P.req[k] = r;
       items += r.items;

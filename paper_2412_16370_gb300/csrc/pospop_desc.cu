@@ -3,7 +3,10 @@
 // of mixed width and size, passed by value in the kernel's parameter block (a __grid_constant__ struct of about 8 KiB, read
 // in place through the constant cache: no upload copy before the launch).
 //
-// Work items (item_rows rows of 512 B of one request, as in the batched
+// A launch counts work items [item0, item0 + its items here) of each
+// request, so one request's items may be spread over several launches; its
+// slot's completion counter counts them all.  Work items (req.rows rows of
+// 512 B of one request, as in the batched
 // count: either a contiguous run of rows, or with `strided` every K-th row
 // of a request of K items, so that warps on neighbouring items read
 // neighbouring rows as the single-array kernel's warps do) are dealt to
@@ -63,10 +66,10 @@ __global__ void __launch_bounds__(BS, MINB) serve_kernel(const __grid_constant__
     const int w = rq.w;
     const uint32_t rot = (8u * s.head) & (uint32_t)(w - 1);
     const uint64_t R = span_rows(s);
-    const uint64_t kk = i - P.item_start[k];   // the item's index within its request
+    const uint64_t kk = rq.item0 + (i - P.item_start[k]);   // the item's index within its request
     uint64_t r0, stride, nrows;
     if (P.strided) {
-      // rows kk, kk + K, ...: at most ceil(R / K) <= item_rows of them
+      // rows kk, kk + K, ...: at most ceil(R / K) <= rq.rows of them
       // (32-bit: the host keeps strided requests below 2^32 rows, and a
       // 64-bit division's call would spill the CSA state)
       const uint32_t K = rq.items, k32 = (uint32_t)kk, R32 = (uint32_t)R;
@@ -74,9 +77,9 @@ __global__ void __launch_bounds__(BS, MINB) serve_kernel(const __grid_constant__
       stride = K;
       nrows = R32 > k32 ? (R32 - k32 - 1) / K + 1 : 0;
     } else {
-      r0 = kk * P.item_rows;
+      r0 = kk * rq.rows;
       stride = 1;
-      nrows = ((r0 + P.item_rows < R) ? r0 + P.item_rows : R) - r0;
+      nrows = ((r0 + rq.rows < R) ? r0 + rq.rows : R) - r0;
     }
     uint32_t cnt[4] = {0u, 0u, 0u, 0u};
     count_rows<DEPTH, HINT>(s, r0, stride, nrows, lane, xk, cnt, PlainLoader<HINT>{});
@@ -87,7 +90,7 @@ __global__ void __launch_bounds__(BS, MINB) serve_kernel(const __grid_constant__
       });
       continue;
     }
-    const uint32_t slot = P.slot0 + k;
+    const uint32_t slot = rq.slot;
     unsigned long long *out = P.counts + 64ull * slot;
     fold_counts(cnt, w, rot, lane, [&](uint32_t j, unsigned long long v) {
       if (v) atomicAdd(out + j, v);
@@ -106,7 +109,7 @@ __global__ void __launch_bounds__(BS, MINB) serve_kernel(const __grid_constant__
       __syncwarp();
       if (lane == 0) {
         __threadfence_system();
-        *reinterpret_cast<volatile unsigned int *>(P.flags + slot) = P.seq;
+        *reinterpret_cast<volatile unsigned int *>(P.flags + slot) = rq.seq;
         __threadfence_system();
       }
     }

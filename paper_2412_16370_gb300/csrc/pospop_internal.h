@@ -73,23 +73,26 @@ struct ServeReq {
   const void *ptr;              // first byte (device addressable, any alignment)
   uint64_t nbytes;
   int32_t w;
-  uint32_t items;               // work items of this request
+  uint32_t items;               // work items of the whole request
   unsigned long long *out;      // add-into form (pospopcnt_multi): this count's w counters
+  uint32_t item0;               // the request's first work item in this launch (a request's
+                                // items may be spread over several launches)
+  uint32_t slot;                // request slot (counters, completion counter, result, flag)
+  uint32_t seq;                 // value written to the slot's flag when the request completes
+  uint32_t rows;                // rows of 512 B per work item of this request
 };
 
 struct ServeParams {
   uint32_t n;                   // requests in this launch
-  uint32_t item_rows;
   uint64_t total;               // work items in this launch
   unsigned long long *counts;   // 64 per request slot (device, zero between uses)
   unsigned int *done;           // finished work items per request slot (device, zero between uses)
   unsigned long long *host_res; // 64 per request slot (mapped pinned host memory)
   unsigned int *flags;          // one per request slot (mapped pinned host memory)
-  uint32_t seq;                 // value written to a finished request's flag
-  uint32_t slot0;               // request slot of req[0]
   uint32_t strided;             // 1: item k of a request of K items counts rows k, k + K, ...
                                 // (warps on neighbouring items read neighbouring rows);
-                                // 0: item k counts rows k * item_rows .. + item_rows - 1
+                                // 0: item k counts rows k * rows .. + rows - 1 (rows: the
+                                // request's item rows)
   ServeReq req[kServeMax];
   uint64_t item_start[kServeMax + 1];
 };

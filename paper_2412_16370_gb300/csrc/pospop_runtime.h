@@ -73,6 +73,11 @@ struct TuneTable {
                                 // may run on a free stream of the next smaller class
   int serve_shape;              // serving kernel's launch shape (index into the serve and
                                 // batch families: block size, flush depth, load variant)
+  uint32_t serve_mode;          // 0: size classes on prioritised streams; 1: dispatch by
+                                // remaining bytes (read when a server is created)
+  uint64_t srf_bytes;           // serve_mode 1: bytes of work items per launch, at most
+  uint32_t srf_launches;        // serve_mode 1: launches in flight, at most
+  uint32_t srf_rows;            // serve_mode 1: rows per work item
   uint32_t multi_rows;          // pospopcnt_multi: most work-item rows (wave-aligned, at least 8)
   uint32_t multi_strided;       // pospopcnt_multi: 1 = items take every K-th row of their count
   long long wait_cycles;        // limit of a staged kernel's wait for a bulk copy (SM clock

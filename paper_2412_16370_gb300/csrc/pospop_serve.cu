@@ -68,6 +68,13 @@ struct Request {
   uint64_t pool_off = 0;
   uint64_t pool_len = 0;       // 0: no pool range held
   cudaEvent_t ev = nullptr;    // the upload's completion (waited for by the batch stream)
+  // dispatch by remaining bytes (serve_mode 1)
+  uint32_t gslot = UINT32_MAX; // server-wide request slot
+  uint32_t ir = 0;             // rows per work item (fixed at admission)
+  uint32_t items_total = 0;    // work items of ir rows
+  uint32_t items_next = 0;     // the first item not yet dispatched
+  int launches = 0;            // unfinished launches that hold some of its items
+  bool flagged = false;        // the device has published its counts
 };
 
 constexpr uint64_t kPoolGranule = 256;
@@ -96,6 +103,7 @@ constexpr size_t kClassBound[kServeClasses - 1] = {size_t(1) << 20, size_t(16) <
 constexpr size_t kBatchCap = 1024;      // requests per batch, at most (4 launches of kServeMax)
 constexpr uint64_t kMaxServeGrid = uint64_t(1) << 20;
 constexpr uint32_t kMinItemRows = 8;    // the shortest light-load work item
+constexpr size_t kGlobalSlots = 16384;  // serve_mode 1: request slots, at most
 
 // The tune-table entries the loop works with (copied once per loop pass).
 struct LoopTune {
@@ -185,6 +193,19 @@ struct pospop_server {
   std::condition_variable cv_up;
   bool stop_uploads = false;
   std::thread uploader;
+
+  // serve_mode 1 (read at creation): admitted requests are dispatched by
+  // remaining bytes in launches of at most srf_bytes, srf_launches at once,
+  // items of srf_rows rows; each request holds a server-wide slot
+  int mode = 0;
+  uint64_t srf_bytes = 0;
+  int srf_launches = 0;
+  uint32_t srf_rows = 0;
+  unsigned long long *g_dcounts = nullptr;   // 64 per slot (device, zero between uses)
+  unsigned int *g_ddone = nullptr;           // completion counter per slot (device)
+  unsigned long long *g_hres = nullptr, *g_dres = nullptr;   // mapped pinned results
+  unsigned int *g_hflags = nullptr, *g_dflags = nullptr;     // mapped pinned flags
+  std::vector<uint32_t> g_free;              // free slots
 };
 
 namespace pospop {
@@ -247,20 +268,18 @@ int launch_batch(pospop_server &srv, Batch &b, const LoopTune &lt, size_t load_b
   for (int k0 = 0; k0 < n; k0 += kServeMax) {
     const int cnt = std::min(kServeMax, n - k0);
     P.n = (uint32_t)cnt;
-    P.item_rows = ir;
     P.counts = b.dcounts;
     P.done = b.ddone;
     P.host_res = b.dres;
     P.flags = b.dflags;
-    P.seq = b.seq;
-    P.slot0 = (uint32_t)k0;
     P.strided = lt.strided;   // requests are at most the budget: far below 2^32 rows
     uint64_t items = 0;
     for (int k = 0; k < cnt; k++) {
       const Request *r = b.reqs[k0 + k];
       const uint64_t it = (request_rows(r) + ir - 1) / ir;
       P.item_start[k] = items;
-      P.req[k] = ServeReq{r->dptr, (uint64_t)r->nbytes, r->w, (uint32_t)it};
+      P.req[k] = ServeReq{r->dptr, (uint64_t)r->nbytes, r->w, (uint32_t)it, nullptr,
+                          0u, (uint32_t)(k0 + k), b.seq, ir};
       items += it;
       if (it == 0) {   // nothing to count: done as soon as the loop looks
         memset(b.hres + 64 * (size_t)(k0 + k), 0, 64 * sizeof(unsigned long long));
@@ -317,6 +336,7 @@ void pool_give(pospop_server &srv, uint64_t off, uint64_t len) {
 // Bookkeeping of a finished request; caller holds srv.mu.
 void complete(pospop_server &srv, Request *r, int status, int64_t t) {
   if (r->pool_len) pool_give(srv, r->pool_off, r->pool_len);
+  if (r->gslot != UINT32_MAX) srv.g_free.push_back(r->gslot);
   if (r->ev) srv.spare_events.push_back(r->ev);
   r->rec.status = status;
   r->rec.t_done_ns = t;
@@ -325,6 +345,50 @@ void complete(pospop_server &srv, Request *r, int status, int64_t t) {
   srv.completed += 1;
   srv.finished.push_back(r->rec);
   delete r;
+}
+
+// Admission by device memory and slots, FIFO (caller holds srv.mu):
+// requests leave `pending` while their bytes fit the budget and a slot is
+// free (with serve_mode 1 also a server-wide request slot); host input also
+// needs a free range of the staging pool and goes to the uploader, the rest
+// to `admitted`.  Returns whether any request was admitted.
+bool admit(pospop_server &srv, int64_t tnow) {
+  bool any = false, to_uploader = false;
+  while (!srv.pending.empty() && srv.inflight < srv.max_inflight &&
+         srv.inflight_bytes + srv.pending.front()->nbytes <= srv.budget) {
+    Request *r = srv.pending.front();
+    if (srv.mode == 1 && srv.g_free.empty()) break;   // wait for a request slot
+    if (r->host && r->nbytes > 0) {
+      const uint64_t len = (r->nbytes + kPoolGranule - 1) / kPoolGranule * kPoolGranule;
+      uint64_t off = 0;
+      if (!pool_take(srv, len, &off)) break;   // wait for pool space
+      r->pool_off = off;
+      r->pool_len = len;
+      r->dptr = srv.pool + off;
+      if (!srv.spare_events.empty()) {
+        r->ev = srv.spare_events.back();
+        srv.spare_events.pop_back();
+      }
+    }
+    srv.pending.pop_front();
+    if (srv.mode == 1) {
+      r->gslot = srv.g_free.back();
+      srv.g_free.pop_back();
+    }
+    r->rec.t_admit_ns = tnow;
+    srv.inflight += 1;
+    srv.inflight_bytes += r->nbytes;
+    if (r->host) {
+      srv.uploads.push_back(r);
+      srv.uploading += 1;
+      to_uploader = true;
+    } else {
+      srv.admitted.push_back(r);
+    }
+    any = true;
+  }
+  if (to_uploader) srv.cv_up.notify_one();
+  return any;
 }
 
 // The loop thread owns the batches and every request it has taken out of
@@ -408,38 +472,8 @@ void serve_loop(pospop_server *srv) {
         progress = true;
         srv->cv_done.notify_all();
       }
-      // 2. admission by device memory and slots (FIFO); host input also
-      //    needs a free range of the staging pool, and goes to the uploader
-      bool to_uploader = false;
-      while (!srv->pending.empty() && srv->inflight < srv->max_inflight &&
-             srv->inflight_bytes + srv->pending.front()->nbytes <= srv->budget) {
-        Request *r = srv->pending.front();
-        if (r->host && r->nbytes > 0) {
-          const uint64_t len = (r->nbytes + kPoolGranule - 1) / kPoolGranule * kPoolGranule;
-          uint64_t off = 0;
-          if (!pool_take(*srv, len, &off)) break;   // wait for pool space
-          r->pool_off = off;
-          r->pool_len = len;
-          r->dptr = srv->pool + off;
-          if (!srv->spare_events.empty()) {
-            r->ev = srv->spare_events.back();
-            srv->spare_events.pop_back();
-          }
-        }
-        srv->pending.pop_front();
-        r->rec.t_admit_ns = tnow;
-        srv->inflight += 1;
-        srv->inflight_bytes += r->nbytes;
-        if (r->host) {
-          srv->uploads.push_back(r);
-          srv->uploading += 1;
-          to_uploader = true;
-        } else {
-          srv->admitted.push_back(r);
-        }
-        progress = true;
-      }
-      if (to_uploader) srv->cv_up.notify_one();
+      // 2. admission by device memory and slots (FIFO)
+      if (admit(*srv, tnow)) progress = true;
       // 3. admitted requests go, by size class and in admission order, into
       //    the next free batch of their class (while fewer than the class's
       //    `streams` batches are running; at most `cap` requests a batch)
@@ -551,6 +585,213 @@ void serve_loop(pospop_server *srv) {
   }
 }
 
+// serve_mode 1: dispatch by remaining bytes.  Admitted requests wait in
+// `queue` ordered by the bytes they have not yet had dispatched; whenever
+// one of the first srf_launches highest-priority batch streams is free, a
+// launch takes work items from the front of the queue (smallest remaining
+// first) up to srf_bytes, so a large request is counted over several
+// launches while smaller arrivals overtake it at the next launch.  Every
+// request holds a server-wide slot for its whole life (its counters and
+// completion counter add up across launches); the warp that finishes its
+// last item publishes the counts and raises the slot's flag with the
+// request's tag.  The loop thread owns `queue`, `active` and the dispatch
+// batches; the mutex guards only the server's queues and counters.
+void serve_loop_srf(pospop_server *srv) {
+  cudaSetDevice(srv->ctx->device);
+  std::vector<Request *> queue;     // admitted, items left to dispatch
+  std::vector<Request *> active;    // dispatched in part or whole, not yet finished
+  std::vector<Request *> done_reqs;
+  std::vector<Batch *> disp;        // the dispatch batches (streams)
+  for (Batch &b : srv->batches)
+    if (b.level == 0 && (int)disp.size() < srv->srf_launches) disp.push_back(&b);
+  static thread_local ServeParams P;   // about 14 KiB: not on the loop thread's stack
+  int64_t last_activity = now_ns();
+  while (true) {
+    bool progress = false;
+    int shape;
+    uint32_t strided;
+    ServeTune cls[kServeClasses];
+    uint64_t light;
+    {
+      std::lock_guard<std::mutex> g(srv->ctx->mu);
+      shape = srv->ctx->tune.serve_shape;
+      strided = srv->ctx->tune.serve_strided;
+      for (int k = 0; k < kServeClasses; k++) cls[k] = srv->ctx->tune.serve[k];
+      light = srv->ctx->tune.serve_light;
+    }
+    // 1. finished launches free their streams; flagged requests are done;
+    //    a request whose launches all finished unflagged failed on the device
+    done_reqs.clear();
+    for (Batch *b : disp) {
+      if (!b->busy) continue;
+      const cudaError_t q = cudaEventQuery(b->done);
+      if (q == cudaErrorNotReady) continue;
+      if (q != cudaSuccess) cudaGetLastError();
+      for (Request *r : b->reqs) r->launches -= 1;
+      b->reqs.clear();
+      b->busy = false;
+      progress = true;
+    }
+    for (size_t k = 0; k < active.size();) {
+      Request *r = active[k];
+      if (!r->flagged &&
+          __atomic_load_n(srv->g_hflags + r->gslot, __ATOMIC_ACQUIRE) == (uint32_t)r->id) {
+        if (r->result)
+          for (int j = 0; j < r->w; j++) r->result[j] = srv->g_hres[64 * (size_t)r->gslot + j];
+        r->flagged = true;
+        r->rec.status = POSPOP_OK;
+      } else if (!r->flagged && r->launches == 0 && r->items_next == r->items_total) {
+        r->rec.status = POSPOP_ECUDA;   // every launch finished, no result
+      } else {
+        k++;
+        continue;
+      }
+      if (r->launches > 0 && r->rec.status == POSPOP_OK) {
+        // its slot is written no more, but launches still hold the pointer:
+        // complete now, and the launches only drop their references
+        for (Batch *b : disp)
+          for (Request *&x : b->reqs)
+            if (x == r) x = nullptr;
+      }
+      done_reqs.push_back(r);
+      active[k] = active.back();
+      active.pop_back();
+      progress = true;
+    }
+    for (Batch *b : disp) {
+      std::vector<Request *> keep;
+      for (Request *r : b->reqs)
+        if (r) keep.push_back(r);
+      b->reqs.swap(keep);
+    }
+    // 2. under the lock: completions, admission, newly admitted requests
+    std::vector<Request *> incoming;
+    bool stop_now = false;
+    size_t load_bytes = 0;
+    {
+      std::unique_lock<std::mutex> lk(srv->mu);
+      const int64_t tnow = now_ns();
+      for (Request *r : done_reqs) complete(*srv, r, r->rec.status, tnow);
+      if (!done_reqs.empty()) srv->cv_done.notify_all();
+      if (admit(*srv, tnow)) progress = true;
+      load_bytes = srv->inflight_bytes;
+      incoming.assign(srv->admitted.begin(), srv->admitted.end());
+      srv->admitted.clear();
+      const bool busy = !queue.empty() || !active.empty() || !incoming.empty() ||
+                        std::any_of(disp.begin(), disp.end(), [](Batch *b) { return b->busy; });
+      if (srv->stop && !busy && srv->pending.empty() && srv->uploading == 0) stop_now = true;
+      if (progress || busy) last_activity = tnow;
+      if (!progress && !busy && !stop_now && tnow - last_activity > 200000)
+        srv->cv_loop.wait_for(lk, std::chrono::milliseconds(50));
+    }
+    // 3. newly admitted requests join the queue (empty ones are done at
+    //    once); while the server is lightly loaded a request's items follow
+    //    its class's light-load rule, else they have srf_rows rows
+    for (Request *r : incoming) {
+      const uint64_t rrows = serve_rows(r->dptr, r->nbytes);
+      if (load_bytes < light) {
+        const ServeTune &st = cls[request_class(r->nbytes, srv->levels)];
+        r->ir = serve_light_rows(*srv->ctx, shape, rrows,
+                                 std::min(st.light_rows ? st.light_rows : st.rows, st.rows));
+      } else {
+        r->ir = srv->srf_rows;
+      }
+      r->items_total = (uint32_t)((rrows + r->ir - 1) / r->ir);
+      if (r->items_total == 0) {
+        if (r->result)
+          for (int j = 0; j < r->w; j++) r->result[j] = 0;
+        r->rec.status = POSPOP_OK;
+        std::lock_guard<std::mutex> g(srv->mu);
+        complete(*srv, r, POSPOP_OK, now_ns());
+        srv->cv_done.notify_all();
+        continue;
+      }
+      queue.push_back(r);
+      progress = true;
+    }
+    // 4. dispatch: one launch per free dispatch stream, smallest remaining first
+    for (Batch *b : disp) {
+      if (b->busy || queue.empty()) continue;
+      std::stable_sort(queue.begin(), queue.end(), [](const Request *x, const Request *y) {
+        return (uint64_t)(x->items_total - x->items_next) * x->ir <
+               (uint64_t)(y->items_total - y->items_next) * y->ir;
+      });
+      uint64_t budget = srv->srf_bytes;
+      uint64_t items = 0;
+      uint32_t n = 0;
+      size_t taken = 0;
+      for (Request *r : queue) {
+        if (n == (uint32_t)kServeMax || budget == 0) break;
+        const uint64_t item_bytes = (uint64_t)r->ir * 512u;
+        const uint64_t left = r->items_total - r->items_next;
+        const uint64_t take = std::min<uint64_t>(left, std::max<uint64_t>(1, budget / item_bytes));
+        P.req[n] = ServeReq{r->dptr, (uint64_t)r->nbytes, r->w, r->items_total, nullptr,
+                            r->items_next, r->gslot, (uint32_t)r->id, r->ir};
+        P.item_start[n] = items;
+        items += take;
+        budget -= std::min<uint64_t>(budget, take * item_bytes);
+        r->items_next += (uint32_t)take;
+        r->launches += 1;
+        if (r->items_next == (uint32_t)take) {
+          r->rec.t_launch_ns = now_ns();   // its first launch
+          active.push_back(r);
+        }
+        b->reqs.push_back(r);
+        if (r->ev && cudaStreamWaitEvent(b->s, r->ev, 0) != cudaSuccess) cudaGetLastError();
+        n++;
+        taken++;
+        if (r->items_next < r->items_total) break;   // the budget is spent
+      }
+      // requests with every item dispatched leave the queue
+      queue.erase(std::remove_if(queue.begin(), queue.end(),
+                                 [](const Request *r) { return r->items_next == r->items_total; }),
+                  queue.end());
+      P.n = n;
+      P.total = items;
+      P.counts = srv->g_dcounts;
+      P.done = srv->g_ddone;
+      P.host_res = srv->g_dres;
+      P.flags = srv->g_dflags;
+      P.strided = strided;
+      P.item_start[n] = items;
+      int rc = serve_launch(serve_variant(shape), P, b->s);
+      if (rc == POSPOP_OK && cudaEventRecord(b->done, b->s) != cudaSuccess) rc = POSPOP_ECUDA;
+      b->busy = true;
+      if (rc != POSPOP_OK) {
+        // the launch did not reach the device in a usable state: wait for
+        // every dispatch stream (nothing may still write a slot), retire the
+        // other launches, then the requests this launch held get no more
+        // dispatches and, unflagged, fail in the next pass
+        cudaGetLastError();
+        for (Batch *x : disp) cudaStreamSynchronize(x->s);
+        cudaGetLastError();
+        for (Batch *x : disp) {
+          if (x == b || !x->busy) continue;
+          for (Request *r : x->reqs) r->launches -= 1;
+          x->reqs.clear();
+          x->busy = false;
+        }
+        for (Request *r : b->reqs) {
+          r->launches = 0;
+          r->items_next = r->items_total;
+        }
+        b->reqs.clear();
+        b->busy = false;
+        queue.erase(std::remove_if(queue.begin(), queue.end(),
+                                   [](const Request *r) {
+                                     return r->items_next == r->items_total;
+                                   }),
+                    queue.end());
+        std::lock_guard<std::mutex> g(srv->mu);
+        srv->loop_error = rc;
+      }
+      progress = true;
+    }
+    if (stop_now) break;
+    if (!progress) std::this_thread::yield();
+  }
+}
+
 // The uploader: copies admitted host input into its pool range on the copy
 // stream, records the copy's event and hands the request to the loop.  A
 // pageable source makes cudaMemcpyAsync wait until the bytes are staged, so
@@ -651,6 +892,10 @@ int request_ptr(pospop_server *srv, const void *bytes, size_t nbytes, const void
 // stopped, nothing of it is in flight).
 void free_server(pospop_server *srv) {
   for (Batch &x : srv->batches) free_batch(x);
+  if (srv->g_dcounts) cudaFree(srv->g_dcounts);
+  if (srv->g_ddone) cudaFree(srv->g_ddone);
+  if (srv->g_hres) cudaFreeHost(srv->g_hres);
+  if (srv->g_hflags) cudaFreeHost(srv->g_hflags);
   for (cudaEvent_t e : srv->spare_events) cudaEventDestroy(e);
   if (srv->pool) cudaFree(srv->pool);
   if (srv->up_stream) cudaStreamDestroy(srv->up_stream);
@@ -705,6 +950,35 @@ int create_server(size_t mem_budget, int max_inflight, int max_batches, bool poo
     }
     memset(b.hflags, 0, fbytes);   // seq starts at 1
   }
+  {
+    std::lock_guard<std::mutex> g(c->mu);
+    srv->mode = c->tune.serve_mode;
+    srv->srf_bytes = c->tune.srf_bytes;
+    srv->srf_launches = std::max(1, std::min(max_batches, (int)c->tune.srf_launches));
+    srv->srf_rows = c->tune.srf_rows;
+  }
+  if (srv->mode == 1) {
+    // server-wide request slots: a request keeps one for its whole life
+    const size_t slots = std::min<size_t>((size_t)max_inflight, kGlobalSlots);
+    const size_t cbytes = 64 * sizeof(unsigned long long) * slots;
+    const size_t fbytes = sizeof(unsigned int) * slots;
+    if (cudaMalloc(&srv->g_dcounts, cbytes) != cudaSuccess ||
+        cudaMalloc(&srv->g_ddone, fbytes) != cudaSuccess ||
+        cudaMemset(srv->g_dcounts, 0, cbytes) != cudaSuccess ||
+        cudaMemset(srv->g_ddone, 0, fbytes) != cudaSuccess ||
+        cudaHostAlloc(&srv->g_hres, cbytes, cudaHostAllocMapped) != cudaSuccess ||
+        cudaHostAlloc(&srv->g_hflags, fbytes, cudaHostAllocMapped) != cudaSuccess ||
+        cudaHostGetDevicePointer(reinterpret_cast<void **>(&srv->g_dres), srv->g_hres, 0) !=
+            cudaSuccess ||
+        cudaHostGetDevicePointer(reinterpret_cast<void **>(&srv->g_dflags), srv->g_hflags, 0) !=
+            cudaSuccess) {
+      cudaGetLastError();
+      free_server(srv);
+      return POSPOP_ENOMEM;
+    }
+    memset(srv->g_hflags, 0, fbytes);
+    for (size_t k = slots; k > 0; k--) srv->g_free.push_back((uint32_t)(k - 1));
+  }
   if (pooled) {
     // the staging pool for host input: allocated once, the whole budget
     if (cudaMalloc(&srv->pool, mem_budget) != cudaSuccess ||
@@ -721,7 +995,7 @@ int create_server(size_t mem_budget, int max_inflight, int max_batches, bool poo
     free_server(srv);
     return POSPOP_ECUDA;
   }
-  srv->loop = std::thread(serve_loop, srv);
+  srv->loop = std::thread(srv->mode == 1 ? serve_loop_srf : serve_loop, srv);
   if (pooled) srv->uploader = std::thread(upload_loop, srv);
   *out = srv;
   return POSPOP_OK;

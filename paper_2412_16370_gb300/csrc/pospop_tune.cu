@@ -262,13 +262,10 @@ extern "C" int pospopcnt_autotune(size_t max_bytes, const char *path) {
     // one launch over reqs with items of ir rows (counters left clean by the kernel)
     auto launch = [&](const std::vector<ServeReq> &reqs, uint32_t ir) {
       P->n = (uint32_t)reqs.size();
-      P->item_rows = ir;
       P->counts = counts;
       P->done = ddone;
       P->host_res = dres;
       P->flags = dflags;
-      P->seq = 1;
-      P->slot0 = 0;
       P->strided = best.serve_strided;
       uint64_t items = 0;
       for (size_t k = 0; k < reqs.size(); k++) {
@@ -276,6 +273,10 @@ extern "C" int pospopcnt_autotune(size_t max_bytes, const char *path) {
         P->item_start[k] = items;
         P->req[k] = reqs[k];
         P->req[k].items = (uint32_t)it;
+        P->req[k].item0 = 0;
+        P->req[k].slot = (uint32_t)k;
+        P->req[k].seq = 1;
+        P->req[k].rows = ir;
         items += it;
       }
       P->item_start[reqs.size()] = items;

@@ -5,7 +5,8 @@ same counts in the mix as alone (and as the CPU oracle), admission must keep
 the in-flight input bytes within the budget and the admitted requests within
 the slot cap, later arrivals must be launched while earlier batches are still
 running, the tune table's per-class serving entries must take effect, and
-every wait must end with a status.
+every wait must end with a status.  The general tests run under both
+schedules (size classes, and dispatch by remaining bytes).
 """
 import numpy as np
 import pytest
@@ -28,6 +29,29 @@ def pool(gpu):
     return t
 
 
+@pytest.fixture
+def serve_tune(gpu, tmp_path):
+    saved = tmp_path / "saved_tune.txt"
+    saved.write_text(pp.pospopcnt_tune_describe())
+    keep = [l for l in saved.read_text().splitlines() if not l.startswith(("serve ", "serve_light"))]
+
+    def install(*lines):
+        f = tmp_path / "tune.txt"
+        f.write_text("\n".join(keep + list(lines)) + "\n")
+        pp.pospopcnt_tune_load(str(f))
+
+    yield install
+    pp.pospopcnt_tune_load(str(saved))
+
+
+@pytest.fixture(params=(0, 1), ids=("classes", "remaining"))
+def mode(serve_tune, request):
+    """Run a test under both schedules: size classes (`serve_mode 0`) and
+    dispatch by remaining bytes (`serve_mode 1`, the default)."""
+    serve_tune(f"serve_mode {request.param}")
+    return request.param
+
+
 def _requests(n, seed, lo, hi, pool_bytes):
     r = synth.poisson_requests(n, 1.0, seed, lo, hi, pool_bytes=pool_bytes)
     return r["w"].astype(np.int32), r["nbytes"].astype(np.uint64), r["offset"].astype(np.uint64)
@@ -42,7 +66,7 @@ def _solo(pool, w, nbytes, offs):
     return out.cpu().numpy().view(np.uint64)
 
 
-def test_mix_equals_solo_and_oracle(gpu, orc, pool):
+def test_mix_equals_solo_and_oracle(gpu, orc, pool, mode):
     n = 3000
     w, nbytes, offs = _requests(n, 11, 1, 8 * MIB, 256 * MIB)
     nbytes[::97] = 0   # some empty requests
@@ -82,7 +106,7 @@ def _max_overlap(recs, start_key, weight=None):
     return best
 
 
-def test_budget_and_slots_respected(gpu, pool):
+def test_budget_and_slots_respected(gpu, pool, mode):
     n = 400
     w, nbytes, offs = _requests(n, 12, 1 * MIB, 4 * MIB, 256 * MIB)
     budget = 6 * MIB
@@ -101,8 +125,8 @@ def test_budget_and_slots_respected(gpu, pool):
         assert np.array_equal(results[k, :w[k]], solo[k, :w[k]]), k
 
 
-def test_later_arrivals_overlap_running_batches(gpu, pool):
-    """Continuous batching: requests are launched while earlier batches run."""
+def test_later_arrivals_overlap_running_batches(gpu, pool, mode):
+    """Continuous batching: requests are launched while earlier launches run."""
     n = 64
     w = np.full(n, 16, dtype=np.int32)
     nbytes = np.full(n, 128 * MIB, dtype=np.uint64)
@@ -128,21 +152,6 @@ def test_later_arrivals_overlap_running_batches(gpu, pool):
         assert np.array_equal(results[k, :16], exp[k % 2, :16])
 
 
-@pytest.fixture
-def serve_tune(gpu, tmp_path):
-    saved = tmp_path / "saved_tune.txt"
-    saved.write_text(pp.pospopcnt_tune_describe())
-    keep = [l for l in saved.read_text().splitlines() if not l.startswith(("serve ", "serve_light"))]
-
-    def install(*lines):
-        f = tmp_path / "tune.txt"
-        f.write_text("\n".join(keep + list(lines)) + "\n")
-        pp.pospopcnt_tune_load(str(f))
-
-    yield install
-    pp.pospopcnt_tune_load(str(saved))
-
-
 def test_strided_items_mix_equals_oracle(gpu, orc, pool, serve_tune):
     """Tune entry `serve_strided 1` (a work item takes every K-th row of its
     request) at light and full load: every result equals the oracle's."""
@@ -151,7 +160,7 @@ def test_strided_items_mix_equals_oracle(gpu, orc, pool, serve_tune):
     nbytes[::41] = 0
     host = pool.cpu().numpy()
     for light in ("serve_light 0", "serve_light 68719476736"):
-        serve_tune("serve_strided 1", light)
+        serve_tune("serve_mode 0", "serve_strided 1", light)
         srv = pp.pospop_server_create(1 << 30, 512, 4)
         try:
             results = np.zeros((n, 64), dtype=np.uint64)
@@ -169,7 +178,7 @@ def test_promoted_batches_equal_solo(gpu, pool, serve_tune):
     """Tune entry `serve_promote 1` (requests that waited over 1 us may run on
     the next smaller class's stream) with `serve_order 1`: a loaded trace of
     mixed sizes still gives every request its single-array count."""
-    serve_tune("serve_promote 1", "serve_order 1", "serve 3 0 511 2 1", "serve 2 127 511 2 4")
+    serve_tune("serve_mode 0", "serve_promote 1", "serve_order 1", "serve 3 0 511 2 1", "serve 2 127 511 2 4")
     n = 300
     w, nbytes, offs = _requests(n, 23, 4096, 96 * MIB, 150 * MIB)
     srv = pp.pospop_server_create(8 << 30, 1024, 2)
@@ -185,7 +194,57 @@ def test_promoted_batches_equal_solo(gpu, pool, serve_tune):
         assert np.array_equal(results[k, :w[k]], solo[k, :w[k]]), k
 
 
-def test_lone_large_request(gpu, orc, pool):
+@pytest.mark.parametrize("launch_bytes", (8 * MIB, 256 * MIB))
+def test_dispatch_by_remaining_bytes(gpu, orc, pool, serve_tune, launch_bytes):
+    """serve_mode 1: requests dispatched smallest-remaining first in launches
+    of at most `launch_bytes` (with 8 MiB a request of up to 24 MiB is
+    counted over several launches, its counters adding up in its slot):
+    every result equals the oracle's, empty requests included, and the
+    budget and slot cap hold."""
+    serve_tune("serve_mode 1", f"serve_srf {launch_bytes} 4 255")
+    n = 500
+    w, nbytes, offs = _requests(n, 25, 1, 24 * MIB, 256 * MIB)
+    nbytes[::53] = 0
+    budget = 64 * MIB
+    srv = pp.pospop_server_create(budget, 16, 4)
+    try:
+        results = np.zeros((n, 64), dtype=np.uint64)
+        recs = pp.pospop_server_run_trace(srv, (np.arange(n) * 1500).astype(np.int64), w,
+                                          pool.data_ptr() + offs, nbytes, results)
+        st = pp.pospop_server_stats(srv)
+        assert st["submitted"] == st["finished"] == n and st["inflight"] == 0
+    finally:
+        pp.pospop_server_destroy(srv)
+    assert (recs["status"] == 0).all()
+    assert _max_overlap(recs, "t_admit_ns", nbytes) <= budget
+    assert _max_overlap(recs, "t_admit_ns") <= 16
+    host = pool.cpu().numpy()
+    for k in range(n):
+        seg = host[int(offs[k]):int(offs[k]) + int(nbytes[k])]
+        assert np.array_equal(results[k, :w[k]], orc.bytes(int(w[k]), seg)), (launch_bytes, k)
+
+
+def test_dispatch_by_remaining_bytes_host_input(gpu, orc, serve_tune):
+    """serve_mode 1 on a pooled server: host input staged in the pool, counted
+    over several launches, equal to the oracle; the pool is released."""
+    serve_tune("serve_mode 1", f"serve_srf {4 * MIB} 2 127")
+    data = [synth.random_bytes(int(s), seed=600 + k)
+            for k, s in enumerate((5 * MIB + 3, 17, 0, 9 * MIB, 1 * MIB))]
+    srv = pp.pospop_server_create_pooled(12 * MIB, 8, 2)
+    res = np.zeros((len(data), 64), dtype=np.uint64)
+    try:
+        for k, d in enumerate(data):
+            pp.pospop_server_submit_host(srv, (8, 16, 32, 64, 8)[k], d, d.size, res[k])
+        assert pp.pospop_server_drain(srv, 30000) == pp.POSPOP_OK
+        assert pp.pospop_server_pool_stats(srv)[1] == 0
+    finally:
+        pp.pospop_server_destroy(srv)
+    for k, d in enumerate(data):
+        w = (8, 16, 32, 64, 8)[k]
+        assert np.array_equal(res[k, :w], orc.bytes(w, d)), k
+
+
+def test_lone_large_request(gpu, orc, pool, mode):
     """One 128 MiB request on an idle server (its work items are spread over
     every SM): the result equals the oracle's count."""
     srv = pp.pospop_server_create(1 << 30, 16, 2)
@@ -205,7 +264,7 @@ def test_lone_large_request(gpu, orc, pool):
 def test_class_streams_and_cap_entries(gpu, pool, serve_tune):
     """`serve 3 0 127 1 1`: requests from 128 MiB run one batch at a time, one
     request a batch; `serve 0 8 127 64 2`: small requests at most two a batch."""
-    serve_tune("serve 3 0 127 1 1", "serve 0 8 127 64 2")
+    serve_tune("serve_mode 0", "serve 3 0 127 1 1", "serve 0 8 127 64 2")
     nb, ns = 12, 40
     w = np.concatenate([np.full(nb, 32), np.full(ns, 8)]).astype(np.int32)
     nbytes = np.concatenate([np.full(nb, 128 * MIB), np.full(ns, 4096)]).astype(np.uint64)
@@ -232,7 +291,7 @@ def test_class_streams_and_cap_entries(gpu, pool, serve_tune):
         assert np.array_equal(results[k, :w[k]], solo[k, :w[k]]), k
 
 
-def test_host_input_admitted_by_pool_space(gpu, orc):
+def test_host_input_admitted_by_pool_space(gpu, orc, mode):
     """A pooled server stages host input into its device pool: with a budget
     (the pool) far smaller than the sum of the requests, admission waits for
     pool space, the pool's high-water mark stays within the budget, and every
@@ -317,7 +376,7 @@ def test_pooled_server_errors_and_device_requests(gpu, orc, pool):
     assert np.array_equal(r_host[:16], orc.bytes(16, data))
 
 
-def test_errors_and_bounded_waits(gpu, pool):
+def test_errors_and_bounded_waits(gpu, pool, mode):
     srv = pp.pospop_server_create(1 * MIB, 4, 1)
     try:
         L = pp.lib()
@@ -345,11 +404,12 @@ def test_errors_and_bounded_waits(gpu, pool):
         pp.pospop_server_destroy(srv)
 
 
-def test_small_requests_overtake_large_ones(gpu, pool):
-    """Size classes on prioritised streams: small requests that arrive while a
-    large batch runs finish long before it does."""
+def test_small_requests_overtake_large_ones(gpu, pool, mode):
+    """Small requests that arrive while large ones run finish long before
+    them: on a higher-priority stream (size classes), or at the next launch
+    (dispatch by remaining bytes)."""
     lo_prio, hi_prio = torch.cuda.Stream.priority_range()
-    if lo_prio == hi_prio:
+    if mode == 0 and lo_prio == hi_prio:
         pytest.skip("device has a single stream priority level")
     nb, ns = 64, 64        # 8 GiB of large requests (about 1.1 ms), small ones at 0.2..0.52 ms
     w = np.concatenate([np.full(nb, 16), np.full(ns, 8)]).astype(np.int32)
@@ -375,7 +435,7 @@ def test_small_requests_overtake_large_ones(gpu, pool):
     assert np.median(small_lat) < 0.25 * (big_done - t0)
 
 
-def test_every_width_in_one_mix(gpu, orc, pool):
+def test_every_width_in_one_mix(gpu, orc, pool, mode):
     """Requests of widths 1, 2, 4, 8, 16, 32 and 64 in the same batches."""
     n = 700
     widths = np.array([1, 2, 4, 8, 16, 32, 64], dtype=np.int32)
