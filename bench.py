@@ -1030,6 +1030,11 @@ def _sweep(pp, synth_device, data, nbytes, stream, hbm_peak, seed):
     cells = []
     ok = True
     warm, reps = 3, 10
+    # the read roofline at each size: the roofline read kernel, timed the same way
+    rsum = torch.zeros(1, dtype=torch.int64, device=data.device)
+    read_gbs = {size: size / (_time_ms(lambda: pp.pospopcnt_roofline_read(data, rsum, size, stream),
+                                        stream, reps=reps, warm=warm) / 1e3) / 1e9
+                for size in sizes}
     for p in (0.01, 0.5, 0.99, 1.0):
         if p == 1.0:
             synth_device.fill_(data, 0xFF, nbytes=sizes[-1], stream=stream)
@@ -1051,6 +1056,7 @@ def _sweep(pp, synth_device, data, nbytes, stream, hbm_peak, seed):
                 gbs = size / (ms / 1e3) / 1e9
                 cells.append({"w": w, "bytes": size, "p": "ones" if p == 1.0 else p,
                               "GBps": round(gbs, 1), "frac_of_hbm_peak": round(gbs / hbm_peak, 4),
+                              "frac_of_read_roofline": round(gbs / read_gbs[size], 4),
                               "counts_ok": good})
     synth_device.bernoulli_(data, 0.5, seed, stream=stream)
     torch.cuda.synchronize()
@@ -1059,6 +1065,8 @@ def _sweep(pp, synth_device, data, nbytes, stream, hbm_peak, seed):
                         "plus all-ones; 10 launches per cell after at least 3 warm-up launches "
                         "and 0.1 s",
             "min_frac_of_hbm_peak": min(fr), "max_frac_of_hbm_peak": max(fr),
+            "read_roofline_GBps": {str(z): round(g, 1) for z, g in read_gbs.items()},
+            "min_frac_of_read_roofline": min(c["frac_of_read_roofline"] for c in cells),
             "all_counts_ok": ok, "cells": cells}
 
 
