@@ -23,6 +23,9 @@ also carries:
 * multi: several counts in one launch (pospopcnt_multi): the plain
   configuration queued 16 counts a launch, and four 1 GiB arrays in one
   launch against four single launches;
+* sizes: one count of 1 MiB, 16 MiB, 128 MiB and 1 GiB, launched back to
+  back and alone, against the same count as a one-entry multi launch and
+  the roofline read kernel (the fixed cost of a launch);
 * serving: the continuous-batching server on Poisson request streams at
   0.3 / 0.6 / 0.9 of the large-array rate, GB/s and p50/p99 latency;
 * masked: the WHERE-selected count on the 8 GiB array as 32-bit words;
@@ -428,6 +431,7 @@ def run_ours(args):
                             ("short", lambda: _short(pp, synth, synth_device, dev, stream)),
                             ("multi", lambda: _multi(pp, synth_device, data, nbytes, dev, stream,
                                                      hbm_peak)),
+                            ("sizes", lambda: _sizes(pp, data, nbytes, stream, achieved)),
                             ("serving", lambda: _serving(pp, synth, data, nbytes, achieved, dev)),
                             ("masked", lambda: _masked(pp, synth_device, data, nbytes, dev,
                                                        stream, achieved, hbm_peak)),
@@ -835,6 +839,55 @@ def _multi(pp, synth_device, data, nbytes, dev, stream, hbm_peak, group=16):
     return out
 
 
+def _sizes(pp, data, nbytes, stream, large_gbs, sizes=(1 << 20, 16 << 20, 128 << 20, GIB)):
+    """One count of a given size: launches back to back (each on the next
+    slice of the resident array, so that arrays below the L2 size are read
+    from DRAM), for the single-array count, the same count as a one-entry
+    pospopcnt_multi and the roofline read kernel; plus the single-array
+    count timed alone (a synchronize before each launch, so that the time
+    includes the launch itself)."""
+    import torch
+    c = torch.zeros(64, dtype=torch.int64, device=data.device)
+    rsum = torch.zeros(1, dtype=torch.int64, device=data.device)
+    base = data.data_ptr()
+    out = {"workload": "w = 16 counts of one array of each size, 16-byte aligned slices of the "
+                       "resident array, 20 launches back to back after 5 warm-up launches",
+           "large_array_GBps": round(large_gbs, 1), "sizes": []}
+    for size in sizes:
+        if size > nbytes:
+            continue
+        slots = max(1, min(16, nbytes // size))
+        row = {"bytes": size}
+        for name, f in (("count", lambda o: pp.pospopcnt_async(16, c, base + o, size, stream)),
+                        ("multi_one", lambda o: pp.pospopcnt_multi([16], [c], [base + o], [size],
+                                                                   stream)),
+                        ("roofline_read", lambda o: pp.pospopcnt_roofline_read(base + o, rsum, size,
+                                                                               stream))):
+            k = [0]
+
+            def call():
+                f((k[0] % slots) * size)
+                k[0] += 1
+            us = _time_ms(call, stream, reps=20, warm=5, warm_s=0.02) * 1e3
+            row[name + "_us"] = round(us, 2)
+            row[name + "_GBps"] = round(size / us / 1e3, 1)
+        alone = []
+        for j in range(10):
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            pp.pospopcnt_async(16, c, base + (j % slots) * size, size, stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            alone.append(e0.elapsed_time(e1) * 1e3)
+        row["count_alone_us"] = round(float(np.median(alone)), 2)
+        row["count_frac_of_large_array"] = round(row["count_GBps"] / large_gbs, 4)
+        row["fixed_us"] = round(row["count_us"] - size / large_gbs / 1e3, 2)
+        out["sizes"].append(row)
+    return out
+
+
 def _serving(pp, synth, pool, pool_bytes, large_gbs, dev, loads=(0.3, 0.6, 0.9),
              duration_s=0.3, budget=32 << 30):
     """Poisson request streams at fractions of the large-array rate, served by
@@ -1131,10 +1184,10 @@ def main():
                     help="skip the oracle check of the timed counts (about 10 s of host work)")
     ap.add_argument("--quick", action="store_true",
                     help="skip every section after the headline (e2e, batched, plain, "
-                         "short, serving, masked, gather, cpu_baseline, sweep)")
+                         "short, multi, sizes, serving, masked, gather, cpu_baseline, sweep)")
     ap.add_argument("--sections", default="",
                     help="comma list of extra sections to run (e2e,batched,plain,short,multi,"
-                         "serving,masked,gather,cpu_baseline,sweep)")
+                         "sizes,serving,masked,gather,cpu_baseline,sweep)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")

@@ -284,6 +284,10 @@ int launch_batch(pospop_server &srv, Batch &b, const LoopTune &lt, size_t load_b
       if (it == 0) {   // nothing to count: done as soon as the loop looks
         memset(b.hres + 64 * (size_t)(k0 + k), 0, 64 * sizeof(unsigned long long));
         __atomic_store_n(b.hflags + k0 + k, b.seq, __ATOMIC_RELEASE);
+      } else {
+        // the slot may still hold this sequence number from 2^32 batches
+        // ago: only the kernel may raise it now (seq is never 0)
+        __atomic_store_n(b.hflags + k0 + k, 0u, __ATOMIC_RELAXED);
       }
     }
     P.item_start[cnt] = items;
@@ -706,6 +710,9 @@ void serve_loop_srf(pospop_server *srv) {
         srv->cv_done.notify_all();
         continue;
       }
+      // the slot's flag may hold this request's tag from 2^32 requests ago:
+      // clear it, so that only the kernel can raise it
+      __atomic_store_n(srv->g_hflags + r->gslot, ~(uint32_t)r->id, __ATOMIC_RELAXED);
       queue.push_back(r);
       progress = true;
     }
