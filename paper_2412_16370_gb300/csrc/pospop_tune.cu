@@ -134,37 +134,69 @@ extern "C" int pospopcnt_autotune(size_t max_bytes, const char *path) {
   TuneTable cand = best;
 
   // --- single-array kernel, per width group and size class ------------------
-  const size_t rep_bytes[kClasses] = {size_t(16) << 10, size_t(512) << 10, size_t(16) << 20,
-                                      size_t(512) << 20, max_bytes};
+  // Each class is scored on a spread of sizes inside it, each time relative
+  // to the incumbent's and summed (a shape that suits the top of a class can
+  // cost the bottom of it: one wave against two of the 32 MiB .. 1 GiB class
+  // differs by a fifth at 64 MiB and not at all at 1 GiB).  Calls rotate over
+  // slices of the scratch buffer, so arrays below the L2 size are still read
+  // from DRAM wherever the buffer holds several slices.
+  const size_t mix[kClasses][3] = {
+      {size_t(16) << 10, 0, 0},
+      {size_t(512) << 10, 0, 0},
+      {size_t(2) << 20, size_t(8) << 20, size_t(32) << 20},
+      {size_t(64) << 20, size_t(256) << 20, size_t(1) << 30},
+      {max_bytes, 0, 0}};
   const uint32_t minrows_set[] = {1, 2, 4, 8, 16, 32, 64, 128};
   for (int g = 0; g < kWidthGroups; g++) {
     const int w = kGroupWidth[g];
     for (int cls = 0; cls < kClasses; cls++) {
-      const size_t nbytes = std::min(rep_bytes[cls], max_bytes);
-      const uint64_t rows = (nbytes / 16 + 31) / 32;
-      if (size_class(rows) != cls) {   // scratch too small for this class: inherit
+      std::vector<size_t> sizes;
+      for (size_t z : mix[cls])
+        if (z > 0 && z <= max_bytes && size_class((z / 16 + 31) / 32) == cls) sizes.push_back(z);
+      if (sizes.empty()) {   // scratch too small for this class: inherit
         if (cls > 0) best.stream[g][cls] = best.stream[g][cls - 1];
         continue;
       }
-      // the incumbent is timed first; a candidate must beat it by 1% (ties
-      // and noise keep the current entry)
-      double best_ms =
-          tm.time([&] { return launch_stream_with(*c, best, w, counts, buf, nbytes, tm.s); });
-      if (best_ms <= 0) best_ms = 1e30;
+      auto run = [&](const TuneTable &t, size_t nbytes) {
+        const size_t slots = std::max<size_t>(1, std::min<size_t>(16, max_bytes / nbytes));
+        size_t k = 0;
+        return tm.time([&] {
+          const size_t off = (k++ % slots) * nbytes;
+          return launch_stream_with(*c, t, w, counts, buf + off, nbytes, tm.s);
+        });
+      };
+      // the incumbent is timed first; a candidate must beat it by 1% in the
+      // summed relative time (ties and noise keep the current entry)
+      std::vector<double> base_ms;
+      bool ok = true;
+      for (size_t z : sizes) {
+        const double ms = run(best, z);
+        ok = ok && ms > 0;
+        base_ms.push_back(ms);
+      }
+      if (!ok) continue;
+      double best_score = (double)sizes.size();
       for (int v = 0; v < stream_variant_count(); v++) {
         for (int cps = 1; cps <= std::max(4, c->occ_stream[v]); cps++) {
           unsigned last_grid = 0;
           for (uint32_t mr : minrows_set) {
             cand = best;
             cand.stream[g][cls] = StreamTune{v, cps, mr};
-            const StreamPlan pl = plan_stream(*c, cand, w, rows);
-            if (pl.grid == last_grid) continue;   // same launch as the previous min_rows
+            // skip a min_rows that gives the class's smallest size the same
+            // grid as the previous one (the larger sizes then mostly share
+            // the grid cap as well)
+            const StreamPlan pl = plan_stream(*c, cand, w, (sizes[0] / 16 + 31) / 32);
+            if (pl.grid == last_grid) continue;
             last_grid = pl.grid;
-            const double ms = tm.time([&] {
-              return launch_stream_with(*c, cand, w, counts, buf, nbytes, tm.s);
-            });
-            if (ms > 0 && ms < 0.99 * best_ms) {
-              best_ms = ms;
+            double score = 0;
+            bool good = true;
+            for (size_t i = 0; good && i < sizes.size(); i++) {
+              const double ms = run(cand, sizes[i]);
+              good = ms > 0;
+              score += ms / base_ms[i];
+            }
+            if (good && score < 0.99 * best_score) {
+              best_score = score;
               best.stream[g][cls] = cand.stream[g][cls];
             }
           }
