@@ -283,9 +283,9 @@ int pospopcnt_graph_destroy(void *graph);
  *
  * A request is admitted when the input bytes of all admitted, unfinished
  * requests plus its own fit `mem_budget` and fewer than `max_inflight` are
- * admitted (and, in the default mode, at most 16384 at once).  The tune
+ * admitted (and, in modes 1 and 2, at most 16384 at once).  The tune
  * table's `serve_mode` entry, read when a server is created, picks one of
- * two schedules.
+ * three schedules.
  *
  * `serve_mode 1` (the default): admitted requests are ordered by the bytes
  * they still have to count, and whenever one of the server's highest-
@@ -294,6 +294,12 @@ int pospopcnt_graph_destroy(void *graph);
  * <bytes> of them, so a large request is counted over several launches and
  * smaller arrivals overtake it at the next launch.  Each request keeps one
  * server-wide slot of counters until its last item is done.
+ *
+ * `serve_mode 2`: the same, per size class of the bytes a request has left
+ * (the classes below): a launch takes requests of one class only and runs
+ * on one of that class's <launches> streams, whose priority falls as the
+ * class grows, so blocks of smaller work overtake waiting blocks of larger
+ * work on the device.
  *
  * `serve_mode 0`: admitted requests fall into size classes (below 1 MiB,
  * 16 MiB, 128 MiB, and above; as many classes as the device has stream
@@ -307,7 +313,7 @@ int pospopcnt_graph_destroy(void *graph);
  * loaded, and otherwise), how many of its batches may run at once (at most
  * `max_batches`) and how many requests a batch takes (at most 1024).
  *
- * In both modes `serve_light` sets the in-flight bytes below which the
+ * In every mode `serve_light` sets the in-flight bytes below which the
  * server counts as lightly loaded (work items then spread a request over
  * every SM), each result is the same as the request's single-array count,
  * and waits are bounded by the caller's timeouts.

@@ -158,12 +158,16 @@ TuneTable default_tune() {
 //                                  admission order (0) or smallest first (1))
 //   serve_shape <bs> <minb> <depth> <hint>
 //                                 (the serving kernel's launch shape)
-//   serve_mode <0|1>              (read when a server is created: 0 = size classes on
-//                                  prioritised streams; 1 = dispatch by remaining bytes)
+//   serve_mode <0|1|2>            (read when a server is created: 0 = size classes on
+//                                  prioritised streams; 1 = dispatch by remaining bytes;
+//                                  2 = the same per size class of the bytes left, on the
+//                                  classes' prioritised streams)
 //   serve_srf <bytes> <launches> <rows>
-//                                 (serve_mode 1: work-item bytes per launch, at least one
-//                                  item; launches in flight, 1 .. 64; rows per item,
-//                                  1 .. 2^20)
+//                                 (serve_mode 1 and 2: work-item bytes per launch, at
+//                                  least one item; launches in flight (per class with
+//                                  mode 2), 1 .. 64; rows per item under load, 1 .. 2^20,
+//                                  or 0 for the `serve` entry's rows of the request's
+//                                  class; the bytes at least 512 x the rows)
 //   serve_promote <us>            (0 = off; else requests of a class that have waited
 //                                  this long since they arrived may run as a batch on a
 //                                  free stream of the next smaller class, 1 .. 10^7)
@@ -279,10 +283,11 @@ int parse_tune(const char *text, TuneTable *out, int *bad_line) {
       if (n != 1 || a[0] < 0 || a[0] > 1) return POSPOP_EINVAL;
       t.serve_strided = (uint32_t)a[0];
     } else if (strcmp(kind, "serve_mode") == 0) {
-      if (n != 1 || a[0] < 0 || a[0] > 1) return POSPOP_EINVAL;
+      if (n != 1 || a[0] < 0 || a[0] > 2) return POSPOP_EINVAL;
       t.serve_mode = (uint32_t)a[0];
     } else if (strcmp(kind, "serve_srf") == 0) {
-      if (n != 3 || a[2] < 1 || a[2] > (1 << 20) || a[1] < 1 || a[1] > 64 || a[0] < 512 * a[2])
+      if (n != 3 || a[2] < 0 || a[2] > (1 << 20) || a[1] < 1 || a[1] > 64 ||
+          a[0] < 512 * std::max<long long>(a[2], 1))
         return POSPOP_EINVAL;
       t.srf_bytes = (uint64_t)a[0];
       t.srf_launches = (uint32_t)a[1];

@@ -75,6 +75,7 @@ struct Request {
   uint32_t items_next = 0;     // the first item not yet dispatched
   int launches = 0;            // unfinished launches that hold some of its items
   bool flagged = false;        // the device has published its counts
+  bool finished = false;       // completed; freed once no launch holds it
 };
 
 constexpr uint64_t kPoolGranule = 256;
@@ -337,7 +338,10 @@ void pool_give(pospop_server &srv, uint64_t off, uint64_t len) {
   srv.pool_free.emplace(off, len);
 }
 
-// Bookkeeping of a finished request; caller holds srv.mu.
+// Bookkeeping of a finished request; caller holds srv.mu.  The request is
+// freed here unless a launch still holds it (serve_mode 1: a request's
+// counts can be published while the launch that counted its last item is
+// still counting others); the loop frees it when that launch ends.
 void complete(pospop_server &srv, Request *r, int status, int64_t t) {
   if (r->pool_len) pool_give(srv, r->pool_off, r->pool_len);
   if (r->gslot != UINT32_MAX) srv.g_free.push_back(r->gslot);
@@ -348,7 +352,18 @@ void complete(pospop_server &srv, Request *r, int status, int64_t t) {
   srv.inflight_bytes -= r->nbytes;
   srv.completed += 1;
   srv.finished.push_back(r->rec);
-  delete r;
+  r->finished = true;
+  if (r->launches == 0) delete r;
+}
+
+// serve_mode 1: a launch that held r has ended (loop thread only).
+void drop_launch(Request *r) {
+  if (--r->launches == 0 && r->finished) delete r;
+}
+
+// serve_mode 1 queue order: the rows a request has not yet had dispatched.
+uint64_t rows_left(const Request *r) {
+  return (uint64_t)(r->items_total - r->items_next) * r->ir;
 }
 
 // Admission by device memory and slots, FIFO (caller holds srv.mu):
@@ -361,7 +376,7 @@ bool admit(pospop_server &srv, int64_t tnow) {
   while (!srv.pending.empty() && srv.inflight < srv.max_inflight &&
          srv.inflight_bytes + srv.pending.front()->nbytes <= srv.budget) {
     Request *r = srv.pending.front();
-    if (srv.mode == 1 && srv.g_free.empty()) break;   // wait for a request slot
+    if (srv.mode >= 1 && srv.g_free.empty()) break;   // wait for a request slot
     if (r->host && r->nbytes > 0) {
       const uint64_t len = (r->nbytes + kPoolGranule - 1) / kPoolGranule * kPoolGranule;
       uint64_t off = 0;
@@ -375,7 +390,7 @@ bool admit(pospop_server &srv, int64_t tnow) {
       }
     }
     srv.pending.pop_front();
-    if (srv.mode == 1) {
+    if (srv.mode >= 1) {
       r->gslot = srv.g_free.back();
       srv.g_free.pop_back();
     }
@@ -594,7 +609,13 @@ void serve_loop(pospop_server *srv) {
 // one of the first srf_launches highest-priority batch streams is free, a
 // launch takes work items from the front of the queue (smallest remaining
 // first) up to srf_bytes, so a large request is counted over several
-// launches while smaller arrivals overtake it at the next launch.  Every
+// launches while smaller arrivals overtake it at the next launch.
+// serve_mode 2 does the same per level: the queue's requests fall into the
+// size classes by the bytes they have left (a contiguous run of the queue
+// each), a launch takes requests of one level only and runs on one of that
+// level's first srf_launches streams, whose priority falls as the level
+// grows, so blocks of smaller work overtake waiting blocks of larger work
+// on the device while more large work stays in flight.  Every
 // request holds a server-wide slot for its whole life (its counters and
 // completion counter add up across launches); the warp that finishes its
 // last item publishes the counts and raises the slot's flag with the
@@ -605,9 +626,19 @@ void serve_loop_srf(pospop_server *srv) {
   std::vector<Request *> queue;     // admitted, items left to dispatch
   std::vector<Request *> active;    // dispatched in part or whole, not yet finished
   std::vector<Request *> done_reqs;
-  std::vector<Batch *> disp;        // the dispatch batches (streams)
+  std::vector<Batch *> disp;        // the dispatch batches (streams), all levels
+  std::vector<Batch *> disp_lv[kServeClasses];
+  const bool leveled = srv->mode == 2;
+  const int nlev = leveled ? srv->levels : 1;
   for (Batch &b : srv->batches)
-    if (b.level == 0 && (int)disp.size() < srv->srf_launches) disp.push_back(&b);
+    if (b.level < nlev && (int)disp_lv[b.level].size() < srv->srf_launches) {
+      disp_lv[b.level].push_back(&b);
+      disp.push_back(&b);
+    }
+  // the level of a request in the queue, by the rows it has left
+  auto level_of = [&](const Request *r) {
+    return leveled ? request_class((size_t)rows_left(r) * 512u, srv->levels) : 0;
+  };
   static thread_local ServeParams P;   // about 14 KiB: not on the loop thread's stack
   int64_t last_activity = now_ns();
   while (true) {
@@ -631,7 +662,7 @@ void serve_loop_srf(pospop_server *srv) {
       const cudaError_t q = cudaEventQuery(b->done);
       if (q == cudaErrorNotReady) continue;
       if (q != cudaSuccess) cudaGetLastError();
-      for (Request *r : b->reqs) r->launches -= 1;
+      for (Request *r : b->reqs) drop_launch(r);
       b->reqs.clear();
       b->busy = false;
       progress = true;
@@ -650,23 +681,12 @@ void serve_loop_srf(pospop_server *srv) {
         k++;
         continue;
       }
-      if (r->launches > 0 && r->rec.status == POSPOP_OK) {
-        // its slot is written no more, but launches still hold the pointer:
-        // complete now, and the launches only drop their references
-        for (Batch *b : disp)
-          for (Request *&x : b->reqs)
-            if (x == r) x = nullptr;
-      }
+      // (a flagged request's slot is written no more: it completes now,
+      // and launches that still hold it free it when they end)
       done_reqs.push_back(r);
       active[k] = active.back();
       active.pop_back();
       progress = true;
-    }
-    for (Batch *b : disp) {
-      std::vector<Request *> keep;
-      for (Request *r : b->reqs)
-        if (r) keep.push_back(r);
-      b->reqs.swap(keep);
     }
     // 2. under the lock: completions, admission, newly admitted requests
     std::vector<Request *> incoming;
@@ -690,15 +710,17 @@ void serve_loop_srf(pospop_server *srv) {
     }
     // 3. newly admitted requests join the queue (empty ones are done at
     //    once); while the server is lightly loaded a request's items follow
-    //    its class's light-load rule, else they have srf_rows rows
+    //    its class's light-load rule, else they have srf_rows rows (with
+    //    srf_rows 0, the rows of their class's `serve` entry)
     for (Request *r : incoming) {
       const uint64_t rrows = serve_rows(r->dptr, r->nbytes);
       if (load_bytes < light) {
         const ServeTune &st = cls[request_class(r->nbytes, srv->levels)];
         r->ir = serve_light_rows(*srv->ctx, shape, rrows,
                                  std::min(st.light_rows ? st.light_rows : st.rows, st.rows));
-      } else {
-        r->ir = srv->srf_rows;
+      } else {   // srf_rows, or 0: the rows of the request's class under load
+        r->ir = srv->srf_rows ? srv->srf_rows
+                              : std::max<uint32_t>(1, cls[request_class(r->nbytes, srv->levels)].rows);
       }
       r->items_total = (uint32_t)((rrows + r->ir - 1) / r->ir);
       if (r->items_total == 0) {
@@ -713,86 +735,113 @@ void serve_loop_srf(pospop_server *srv) {
       // the slot's flag may hold this request's tag from 2^32 requests ago:
       // clear it, so that only the kernel can raise it
       __atomic_store_n(srv->g_hflags + r->gslot, ~(uint32_t)r->id, __ATOMIC_RELAXED);
-      queue.push_back(r);
+      // the queue stays ordered by rows left (after those with as many)
+      const uint64_t key = rows_left(r);
+      queue.insert(std::upper_bound(queue.begin(), queue.end(), key,
+                                    [](uint64_t k, const Request *x) { return k < rows_left(x); }),
+                   r);
       progress = true;
     }
-    // 4. dispatch: one launch per free dispatch stream, smallest remaining first
-    for (Batch *b : disp) {
-      if (b->busy || queue.empty()) continue;
-      std::stable_sort(queue.begin(), queue.end(), [](const Request *x, const Request *y) {
-        return (uint64_t)(x->items_total - x->items_next) * x->ir <
-               (uint64_t)(y->items_total - y->items_next) * y->ir;
-      });
-      uint64_t budget = srv->srf_bytes;
-      uint64_t items = 0;
-      uint32_t n = 0;
-      size_t taken = 0;
-      for (Request *r : queue) {
-        if (n == (uint32_t)kServeMax || budget == 0) break;
-        const uint64_t item_bytes = (uint64_t)r->ir * 512u;
-        const uint64_t left = r->items_total - r->items_next;
-        const uint64_t take = std::min<uint64_t>(left, std::max<uint64_t>(1, budget / item_bytes));
-        P.req[n] = ServeReq{r->dptr, (uint64_t)r->nbytes, r->w, r->items_total, nullptr,
-                            r->items_next, r->gslot, (uint32_t)r->id, r->ir};
+    // 4. dispatch: one launch per free dispatch stream, smallest remaining
+    //    first (per level with serve_mode 2)
+    for (int lv = 0; lv < nlev; lv++) {
+      for (Batch *b : disp_lv[lv]) {
+        if (b->busy) continue;
+        // the level's run of the queue: [lo, hi)
+        size_t lo = 0, hi = queue.size();
+        if (leveled) {   // the level grows with the rows left: binary searches
+          lo = (size_t)(std::partition_point(queue.begin(), queue.end(),
+                                             [&](const Request *x) { return level_of(x) < lv; }) -
+                        queue.begin());
+          hi = (size_t)(std::partition_point(queue.begin() + (std::ptrdiff_t)lo, queue.end(),
+                                             [&](const Request *x) { return level_of(x) <= lv; }) -
+                        queue.begin());
+        }
+        if (lo == hi) break;   // nothing of this level: its other streams too
+        // the launch takes a prefix of the run, all of it but the last
+        // request wholly; that one has fewer rows left than any request
+        // after it and goes back to its place in the queue
+        uint64_t budget = srv->srf_bytes;
+        uint64_t items = 0;
+        uint32_t n = 0;
+        size_t taken = 0;
+        for (size_t q = lo; q < hi; q++) {
+          Request *r = queue[q];
+          if (n == (uint32_t)kServeMax || budget == 0) break;
+          const uint64_t item_bytes = (uint64_t)r->ir * 512u;
+          const uint64_t left = r->items_total - r->items_next;
+          const uint64_t take =
+              std::min<uint64_t>(left, std::max<uint64_t>(1, budget / item_bytes));
+          P.req[n] = ServeReq{r->dptr, (uint64_t)r->nbytes, r->w, r->items_total, nullptr,
+                              r->items_next, r->gslot, (uint32_t)r->id, r->ir};
+          P.item_start[n] = items;
+          items += take;
+          budget -= std::min<uint64_t>(budget, take * item_bytes);
+          r->items_next += (uint32_t)take;
+          r->launches += 1;
+          if (r->items_next == (uint32_t)take) {
+            r->rec.t_launch_ns = now_ns();   // its first launch
+            active.push_back(r);
+          }
+          b->reqs.push_back(r);
+          if (r->ev && cudaStreamWaitEvent(b->s, r->ev, 0) != cudaSuccess) cudaGetLastError();
+          n++;
+          taken++;
+          if (r->items_next < r->items_total) break;   // the budget is spent
+        }
+        // requests with every item dispatched leave the queue
+        Request *part = queue[lo + taken - 1]->items_next < queue[lo + taken - 1]->items_total
+                            ? queue[lo + taken - 1]
+                            : nullptr;
+        queue.erase(queue.begin() + (std::ptrdiff_t)lo,
+                    queue.begin() + (std::ptrdiff_t)(lo + taken));
+        if (part)
+          queue.insert(std::upper_bound(queue.begin(), queue.end(), rows_left(part),
+                                        [](uint64_t k, const Request *x) {
+                                          return k < rows_left(x);
+                                        }),
+                       part);
+        P.n = n;
+        P.total = items;
+        P.counts = srv->g_dcounts;
+        P.done = srv->g_ddone;
+        P.host_res = srv->g_dres;
+        P.flags = srv->g_dflags;
+        P.strided = strided;
         P.item_start[n] = items;
-        items += take;
-        budget -= std::min<uint64_t>(budget, take * item_bytes);
-        r->items_next += (uint32_t)take;
-        r->launches += 1;
-        if (r->items_next == (uint32_t)take) {
-          r->rec.t_launch_ns = now_ns();   // its first launch
-          active.push_back(r);
+        int rc = serve_launch(serve_variant(shape), P, b->s);
+        if (rc == POSPOP_OK && cudaEventRecord(b->done, b->s) != cudaSuccess) rc = POSPOP_ECUDA;
+        b->busy = true;
+        if (rc != POSPOP_OK) {
+          // the launch did not reach the device in a usable state: wait for
+          // every dispatch stream (nothing may still write a slot), retire the
+          // other launches, then the requests this launch held get no more
+          // dispatches and, unflagged, fail in the next pass
+          cudaGetLastError();
+          for (Batch *x : disp) cudaStreamSynchronize(x->s);
+          cudaGetLastError();
+          for (Batch *x : disp) {
+            if (x == b || !x->busy) continue;
+            for (Request *r : x->reqs) drop_launch(r);
+            x->reqs.clear();
+            x->busy = false;
+          }
+          for (Request *r : b->reqs) {
+            if (!r->finished) r->items_next = r->items_total;
+            drop_launch(r);
+          }
+          b->reqs.clear();
+          b->busy = false;
+          queue.erase(std::remove_if(queue.begin(), queue.end(),
+                                     [](const Request *r) {
+                                       return r->items_next == r->items_total;
+                                     }),
+                      queue.end());
+          std::lock_guard<std::mutex> g(srv->mu);
+          srv->loop_error = rc;
         }
-        b->reqs.push_back(r);
-        if (r->ev && cudaStreamWaitEvent(b->s, r->ev, 0) != cudaSuccess) cudaGetLastError();
-        n++;
-        taken++;
-        if (r->items_next < r->items_total) break;   // the budget is spent
+        progress = true;
       }
-      // requests with every item dispatched leave the queue
-      queue.erase(std::remove_if(queue.begin(), queue.end(),
-                                 [](const Request *r) { return r->items_next == r->items_total; }),
-                  queue.end());
-      P.n = n;
-      P.total = items;
-      P.counts = srv->g_dcounts;
-      P.done = srv->g_ddone;
-      P.host_res = srv->g_dres;
-      P.flags = srv->g_dflags;
-      P.strided = strided;
-      P.item_start[n] = items;
-      int rc = serve_launch(serve_variant(shape), P, b->s);
-      if (rc == POSPOP_OK && cudaEventRecord(b->done, b->s) != cudaSuccess) rc = POSPOP_ECUDA;
-      b->busy = true;
-      if (rc != POSPOP_OK) {
-        // the launch did not reach the device in a usable state: wait for
-        // every dispatch stream (nothing may still write a slot), retire the
-        // other launches, then the requests this launch held get no more
-        // dispatches and, unflagged, fail in the next pass
-        cudaGetLastError();
-        for (Batch *x : disp) cudaStreamSynchronize(x->s);
-        cudaGetLastError();
-        for (Batch *x : disp) {
-          if (x == b || !x->busy) continue;
-          for (Request *r : x->reqs) r->launches -= 1;
-          x->reqs.clear();
-          x->busy = false;
-        }
-        for (Request *r : b->reqs) {
-          r->launches = 0;
-          r->items_next = r->items_total;
-        }
-        b->reqs.clear();
-        b->busy = false;
-        queue.erase(std::remove_if(queue.begin(), queue.end(),
-                                   [](const Request *r) {
-                                     return r->items_next == r->items_total;
-                                   }),
-                    queue.end());
-        std::lock_guard<std::mutex> g(srv->mu);
-        srv->loop_error = rc;
-      }
-      progress = true;
     }
     if (stop_now) break;
     if (!progress) std::this_thread::yield();
@@ -964,7 +1013,7 @@ int create_server(size_t mem_budget, int max_inflight, int max_batches, bool poo
     srv->srf_launches = std::max(1, std::min(max_batches, (int)c->tune.srf_launches));
     srv->srf_rows = c->tune.srf_rows;
   }
-  if (srv->mode == 1) {
+  if (srv->mode >= 1) {
     // server-wide request slots: a request keeps one for its whole life
     const size_t slots = std::min<size_t>((size_t)max_inflight, kGlobalSlots);
     const size_t cbytes = 64 * sizeof(unsigned long long) * slots;
@@ -1002,7 +1051,7 @@ int create_server(size_t mem_budget, int max_inflight, int max_batches, bool poo
     free_server(srv);
     return POSPOP_ECUDA;
   }
-  srv->loop = std::thread(srv->mode == 1 ? serve_loop_srf : serve_loop, srv);
+  srv->loop = std::thread(srv->mode >= 1 ? serve_loop_srf : serve_loop, srv);
   if (pooled) srv->uploader = std::thread(upload_loop, srv);
   *out = srv;
   return POSPOP_OK;

@@ -5,8 +5,9 @@ same counts in the mix as alone (and as the CPU oracle), admission must keep
 the in-flight input bytes within the budget and the admitted requests within
 the slot cap, later arrivals must be launched while earlier batches are still
 running, the tune table's per-class serving entries must take effect, and
-every wait must end with a status.  The general tests run under both
-schedules (size classes, and dispatch by remaining bytes).
+every wait must end with a status.  The general tests run under each
+schedule (size classes, dispatch by remaining bytes, and the same per size
+class of the bytes left).
 """
 import numpy as np
 import pytest
@@ -44,10 +45,11 @@ def serve_tune(gpu, tmp_path):
     pp.pospopcnt_tune_load(str(saved))
 
 
-@pytest.fixture(params=(0, 1), ids=("classes", "remaining"))
+@pytest.fixture(params=(0, 1, 2), ids=("classes", "remaining", "remaining_by_class"))
 def mode(serve_tune, request):
-    """Run a test under both schedules: size classes (`serve_mode 0`) and
-    dispatch by remaining bytes (`serve_mode 1`, the default)."""
+    """Run a test under each schedule: size classes (`serve_mode 0`),
+    dispatch by remaining bytes (`serve_mode 1`) and the same per size class
+    of the bytes left (`serve_mode 2`)."""
     serve_tune(f"serve_mode {request.param}")
     return request.param
 
@@ -194,14 +196,16 @@ def test_promoted_batches_equal_solo(gpu, pool, serve_tune):
         assert np.array_equal(results[k, :w[k]], solo[k, :w[k]]), k
 
 
+@pytest.mark.parametrize("srf_mode", (1, 2))
 @pytest.mark.parametrize("launch_bytes", (8 * MIB, 256 * MIB))
-def test_dispatch_by_remaining_bytes(gpu, orc, pool, serve_tune, launch_bytes):
-    """serve_mode 1: requests dispatched smallest-remaining first in launches
-    of at most `launch_bytes` (with 8 MiB a request of up to 24 MiB is
-    counted over several launches, its counters adding up in its slot):
-    every result equals the oracle's, empty requests included, and the
-    budget and slot cap hold."""
-    serve_tune("serve_mode 1", f"serve_srf {launch_bytes} 4 255")
+def test_dispatch_by_remaining_bytes(gpu, orc, pool, serve_tune, launch_bytes, srf_mode):
+    """serve_mode 1 and 2: requests dispatched smallest-remaining first in
+    launches of at most `launch_bytes` (with 8 MiB a request of up to 24 MiB
+    is counted over several launches, its counters adding up in its slot,
+    and with mode 2 its later launches move to smaller classes' streams as
+    its bytes left shrink): every result equals the oracle's, empty requests
+    included, and the budget and slot cap hold."""
+    serve_tune(f"serve_mode {srf_mode}", f"serve_srf {launch_bytes} 4 255")
     n = 500
     w, nbytes, offs = _requests(n, 25, 1, 24 * MIB, 256 * MIB)
     nbytes[::53] = 0
@@ -221,13 +225,14 @@ def test_dispatch_by_remaining_bytes(gpu, orc, pool, serve_tune, launch_bytes):
     host = pool.cpu().numpy()
     for k in range(n):
         seg = host[int(offs[k]):int(offs[k]) + int(nbytes[k])]
-        assert np.array_equal(results[k, :w[k]], orc.bytes(int(w[k]), seg)), (launch_bytes, k)
+        assert np.array_equal(results[k, :w[k]], orc.bytes(int(w[k]), seg)), (launch_bytes, srf_mode, k)
 
 
-def test_dispatch_by_remaining_bytes_host_input(gpu, orc, serve_tune):
-    """serve_mode 1 on a pooled server: host input staged in the pool, counted
-    over several launches, equal to the oracle; the pool is released."""
-    serve_tune("serve_mode 1", f"serve_srf {4 * MIB} 2 127")
+@pytest.mark.parametrize("srf_mode", (1, 2))
+def test_dispatch_by_remaining_bytes_host_input(gpu, orc, serve_tune, srf_mode):
+    """serve_mode 1 and 2 on a pooled server: host input staged in the pool,
+    counted over several launches, equal to the oracle; the pool is released."""
+    serve_tune(f"serve_mode {srf_mode}", f"serve_srf {4 * MIB} 2 127")
     data = [synth.random_bytes(int(s), seed=600 + k)
             for k, s in enumerate((5 * MIB + 3, 17, 0, 9 * MIB, 1 * MIB))]
     srv = pp.pospop_server_create_pooled(12 * MIB, 8, 2)
