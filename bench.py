@@ -36,6 +36,8 @@ also carries:
 * cpu_baseline: the CPU oracle on the host cores on a bounded sample;
 * sweep: every w at 1 GiB and 8 GiB over Bernoulli(0.01/0.5/0.99) and
   all-ones bits, each cell's counts checked;
+* tuned (only with --sections tuned): the autotuner's table against the
+  shipped one on the batch, single counts and the serving trace;
 * clocks: SM clocks and throttle reasons sampled during the timed region.
 
 ``--impl reference`` times the CPU oracle on the same workload instead.
@@ -439,9 +441,11 @@ def run_ours(args):
                                                        achieved, hbm_peak)),
                             ("cpu_baseline", lambda: _cpu_baseline(data)),
                             ("sweep", lambda: _sweep(pp, synth_device, data, nbytes, stream,
-                                                     hbm_peak, 0 + rank))):
-                if not want(key):
-                    continue
+                                                     hbm_peak, 0 + rank)),
+                            ("tuned", lambda: _tuned(pp, synth, synth_device, data, nbytes, dev,
+                                                     stream, achieved))):
+                if not want(key) or (key == "tuned" and sections is None):
+                    continue   # (the autotuner comparison runs only when asked for)
                 try:
                     extra[key] = fn()
                 except Exception as e:  # report, keep the line
@@ -1073,6 +1077,70 @@ def _gather(pp, synth, data, nbytes, dev, stream, large_gbs, hbm_peak, m=100000)
             "frac_of_large_array": round(gbs / large_gbs, 4)}
 
 
+def _tuned(pp, synth, synth_device, data, nbytes, dev, stream, large_gbs, max_bytes=GIB):
+    """The autotuner's table against the shipped one: pospopcnt_autotune on
+    max_bytes of scratch, then, with each table installed in turn, the
+    200000-array ragged batch, counts of 128 MiB and 1 GiB (back to back on
+    rotating slices) and of the whole array, and the serving trace at 0.9
+    load.  The shipped table is installed again at the end."""
+    import tempfile
+    import torch
+    shipped = pp.pospopcnt_tune_describe()
+    with tempfile.NamedTemporaryFile("w", suffix=".txt", delete=False) as f:
+        f.write(shipped)
+        shipped_path = f.name
+    tuned_path = shipped_path + ".tuned"
+    t0 = time.perf_counter()
+    pp.pospopcnt_autotune(max_bytes, tuned_path)
+    tune_s = time.perf_counter() - t0
+    tuned = open(tuned_path).read()
+
+    def entries(text):
+        return {l for l in text.splitlines() if l and not l.startswith("#")}
+    m = 200000
+    sizes = synth.log_uniform_sizes(m, 1, 4 << 20, seed=3)
+    offs = synth.csr_offsets(sizes)
+    total = int(offs[-1])
+    base = torch.empty(total + 64, dtype=torch.uint8, device=dev)
+    synth_device.one_hot_(base, 4, nbytes=total)
+    offs_d = torch.from_numpy(offs.view(np.int64)).to(dev)
+    cb = torch.zeros((m, 8), dtype=torch.int64, device=dev)
+    c = torch.zeros(64, dtype=torch.int64, device=dev)
+    out = {"workload": f"pospopcnt_autotune on {max_bytes >> 20} MiB of scratch; each table: "
+                       "the 200000-array ragged batch (w = 8), w = 16 counts of 128 MiB and "
+                       "1 GiB on rotating slices and of the whole array, the serving trace at "
+                       "0.9 load",
+           "tune_s": round(tune_s, 1),
+           "only_shipped": sorted(entries(shipped) - entries(tuned)),
+           "only_tuned": sorted(entries(tuned) - entries(shipped))}
+    try:
+        for name, path in (("shipped", shipped_path), ("tuned", tuned_path)):
+            pp.pospopcnt_tune_load(path)
+            row = {}
+            ms = _time_ms(lambda: pp.pospopcnt_batch(8, cb, base, offs_d, m, stream), stream)
+            row["batch_GBps"] = round(total / ms / 1e6, 1)
+            for size in (128 << 20, GIB):
+                slots = max(1, min(16, nbytes // size))
+                k = [0]
+
+                def call():
+                    pp.pospopcnt_async(16, c, data.data_ptr() + (k[0] % slots) * size, size,
+                                       stream)
+                    k[0] += 1
+                row[f"count_{size >> 20}MiB_us"] = round(_time_ms(call, stream, reps=20) * 1e3, 2)
+            ms = _time_ms(lambda: pp.pospopcnt_async(16, c, data, nbytes, stream), stream)
+            row["count_whole_GBps"] = round(nbytes / ms / 1e6, 1)
+            sv = _serving(pp, synth, data, nbytes, large_gbs, dev, loads=(0.9,))
+            ld = sv["loads"][0]
+            row["serving_0.9"] = {k: ld[k] for k in ("GBps", "p50_us", "p99_us", "results_match_solo")}
+            out[name] = row
+    finally:
+        pp.pospopcnt_tune_load(shipped_path)
+        del base, cb
+        torch.cuda.empty_cache()
+    return out
+
+
 def _sweep(pp, synth_device, data, nbytes, stream, hbm_peak, seed):
     """The large-array sweep: w x {1 GiB, 8 GiB} x Bernoulli(p) for p in
     {0.01, 0.5, 0.99} plus all-ones, each cell timed like the headline launch
@@ -1187,7 +1255,7 @@ def main():
                          "short, multi, sizes, serving, masked, gather, cpu_baseline, sweep)")
     ap.add_argument("--sections", default="",
                     help="comma list of extra sections to run (e2e,batched,plain,short,multi,"
-                         "sizes,serving,masked,gather,cpu_baseline,sweep)")
+                         "sizes,serving,masked,gather,cpu_baseline,sweep,tuned)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")

@@ -107,13 +107,13 @@ TuneTable default_tune() {
   // in local memory, 80-88 bytes a thread) and flush depth 32 (measured on
   // GB300: 0.9-load p99 367-370 us against 395-397 us at depth 16)
   t.serve_shape = find_variant(true, 512, 1, 32, 0);
-  // dispatch by remaining bytes, 128 MiB of work items a launch, four
+  // dispatch by remaining bytes, 128 MiB of work items a launch, five
   // launches in flight (measured on GB300 with a Poisson trace at 0.9 load:
-  // p99 261-265 us against 366-370 us for the size classes, and the same
-  // latency for a lone request)
+  // p99 238-239 us against 271-284 us with four launches and 366-370 us
+  // for the size classes, and the same latency for a lone request)
   t.serve_mode = 1;
   t.srf_bytes = uint64_t(128) << 20;
-  t.srf_launches = 4;
+  t.srf_launches = 5;
   t.srf_rows = 255;
   t.multi_rows = 1024;
   t.multi_strided = 1;
