@@ -283,9 +283,9 @@ int pospopcnt_graph_destroy(void *graph);
  *
  * A request is admitted when the input bytes of all admitted, unfinished
  * requests plus its own fit `mem_budget` and fewer than `max_inflight` are
- * admitted (and, in modes 1 and 2, at most 16384 at once).  The tune
+ * admitted (and, in modes 1 to 3, at most 16384 at once).  The tune
  * table's `serve_mode` entry, read when a server is created, picks one of
- * three schedules.
+ * four schedules.
  *
  * `serve_mode 1` (the default): admitted requests are ordered by the bytes
  * they still have to count, and whenever one of the server's highest-
@@ -300,6 +300,18 @@ int pospopcnt_graph_destroy(void *graph);
  * on one of that class's <launches> streams, whose priority falls as the
  * class grows, so blocks of smaller work overtake waiting blocks of larger
  * work on the device.
+ *
+ * `serve_mode 3`: the order of mode 1 without a launch per batch.  One
+ * resident grid on every SM takes work items from a queue in device memory,
+ * item by item, and the server publishes runs of the smallest-remaining
+ * requests' items into that queue (through mapped host memory) whenever
+ * its unclaimed work is below `serve_srf`'s <bytes>.  The grid is launched
+ * when work arrives and told to leave after `serve_resident`'s idle time
+ * without work; it also leaves by itself after the entry's wait time
+ * without a new run, and then the requests it had not finished fail with
+ * POSPOP_ETIMEDOUT.  While the grid runs it holds every SM, so other
+ * kernels on the device start only after the server has been idle that
+ * long.
  *
  * `serve_mode 0`: admitted requests fall into size classes (below 1 MiB,
  * 16 MiB, 128 MiB, and above; as many classes as the device has stream

@@ -28,7 +28,7 @@ NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
 
 LIB_SOURCES = ["pospop_stream.cu", "pospop_batch.cu", "pospop_desc.cu", "pospop_api.cu",
                "pospop_tune.cu", "pospop_serve.cu", "pospop_noalloc.cu", "pospop_gather.cu",
-               "pospop_select.cu", "pospop_roofline.cu", "pospop_multi.cu"]
+               "pospop_select.cu", "pospop_roofline.cu", "pospop_multi.cu", "pospop_resident.cu"]
 SYNTH_SOURCES = ["synth.cu"]
 
 

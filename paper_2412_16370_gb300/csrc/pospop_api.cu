@@ -115,6 +115,8 @@ TuneTable default_tune() {
   t.srf_bytes = uint64_t(128) << 20;
   t.srf_launches = 5;
   t.srf_rows = 255;
+  t.res_idle_us = 2000;
+  t.res_wait_us = 200000;
   t.multi_rows = 1024;
   t.multi_strided = 1;
   t.set_source("built-in defaults");
@@ -158,10 +160,16 @@ TuneTable default_tune() {
 //                                  admission order (0) or smallest first (1))
 //   serve_shape <bs> <minb> <depth> <hint>
 //                                 (the serving kernel's launch shape)
-//   serve_mode <0|1|2>            (read when a server is created: 0 = size classes on
+//   serve_mode <0|1|2|3>          (read when a server is created: 0 = size classes on
 //                                  prioritised streams; 1 = dispatch by remaining bytes;
 //                                  2 = the same per size class of the bytes left, on the
-//                                  classes' prioritised streams)
+//                                  classes' prioritised streams; 3 = smallest remaining
+//                                  first through a device-side queue into one resident
+//                                  grid, serve_srf's <bytes> the queue's unclaimed work)
+//   serve_resident <idle_us> <wait_us>
+//                                 (serve_mode 3: the host stops the resident grid after
+//                                  idle_us without work; the grid leaves by itself after
+//                                  wait_us without a new run; 1 .. 10^7 each)
 //   serve_srf <bytes> <launches> <rows>
 //                                 (serve_mode 1 and 2: work-item bytes per launch, at
 //                                  least one item; launches in flight (per class with
@@ -283,7 +291,7 @@ int parse_tune(const char *text, TuneTable *out, int *bad_line) {
       if (n != 1 || a[0] < 0 || a[0] > 1) return POSPOP_EINVAL;
       t.serve_strided = (uint32_t)a[0];
     } else if (strcmp(kind, "serve_mode") == 0) {
-      if (n != 1 || a[0] < 0 || a[0] > 2) return POSPOP_EINVAL;
+      if (n != 1 || a[0] < 0 || a[0] > 3) return POSPOP_EINVAL;
       t.serve_mode = (uint32_t)a[0];
     } else if (strcmp(kind, "serve_srf") == 0) {
       if (n != 3 || a[2] < 0 || a[2] > (1 << 20) || a[1] < 1 || a[1] > 64 ||
@@ -292,6 +300,11 @@ int parse_tune(const char *text, TuneTable *out, int *bad_line) {
       t.srf_bytes = (uint64_t)a[0];
       t.srf_launches = (uint32_t)a[1];
       t.srf_rows = (uint32_t)a[2];
+    } else if (strcmp(kind, "serve_resident") == 0) {
+      if (n != 2 || a[0] < 1 || a[0] > 10000000 || a[1] < 1 || a[1] > 10000000)
+        return POSPOP_EINVAL;
+      t.res_idle_us = (uint32_t)a[0];
+      t.res_wait_us = (uint32_t)a[1];
     } else if (strcmp(kind, "serve_shape") == 0) {
       if (n != 4) return POSPOP_EINVAL;
       const int v = find_variant(true, (int)a[0], (int)a[1], (int)a[2], (int)a[3]);
@@ -413,9 +426,10 @@ std::string format_tune(const DevCtx &ctx, const TuneTable &t) {
   s += line;
   {
     const Variant &v = serve_variant(t.serve_shape);
-    snprintf(line, sizeof line, "serve_shape %d %d %d %d\nserve_mode %u\nserve_srf %llu %u %u\n",
+    snprintf(line, sizeof line,
+             "serve_shape %d %d %d %d\nserve_mode %u\nserve_srf %llu %u %u\nserve_resident %u %u\n",
              v.bs, v.minb, v.depth, v.hint, t.serve_mode, (unsigned long long)t.srf_bytes,
-             t.srf_launches, t.srf_rows);
+             t.srf_launches, t.srf_rows, t.res_idle_us, t.res_wait_us);
     s += line;
   }
   snprintf(line, sizeof line, "# multi <most item rows> <0 contiguous | 1 strided items>\nmulti %u %u\n",

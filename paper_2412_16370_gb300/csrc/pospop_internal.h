@@ -97,6 +97,65 @@ struct ServeParams {
   uint64_t item_start[kServeMax + 1];
 };
 
+// serve_mode 3: one resident grid fed through a device-side queue.  The host
+// publishes runs of a request's work items into a ring in mapped pinned
+// memory and raises `published`; one doorbell warp of the grid copies new
+// runs into a device ring, gives each run its first ticket, indexes the
+// tickets by blocks of 64 and releases the ticket count; every other warp
+// claims tickets one at a time and counts the ticket's item.
+struct ResRun {
+  const void *ptr;              // the request's first byte (device addressable)
+  uint64_t nbytes;              // the request's length
+  unsigned long long key;       // device ring: (first ticket << kResNBits) | items of the
+                                // run, written last, in one 8-byte store (0: no run)
+  int32_t w;
+  uint32_t items;               // work items of the whole request
+  uint32_t item0;               // the run's first item within the request
+  uint32_t n;                   // items in the run, below 2^kResNBits
+  uint32_t slot;                // request slot (counters, completion counter, result, flag)
+  uint32_t tag;                 // written to the slot's flag when the request completes
+  uint32_t rows;                // rows of 512 B per work item
+  unsigned int left;            // device ring: items of the run not yet counted
+  uint32_t pad[2];
+};
+static_assert(sizeof(ResRun) == 64, "a run is one 64-byte record");
+constexpr int kResNBits = 23;                       // items per run, below 2^23
+constexpr unsigned long long kResTicketLimit = 1ull << 40;   // tickets before a reset
+
+struct ResCtl {                 // mapped pinned host memory, one per server
+  unsigned long long published; // host: runs published so far (release store)
+  unsigned long long stop;      // host: the launch epoch that is to leave
+  unsigned long long head_seen; // device: tickets claimed so far (the doorbell's copy)
+  unsigned long long copied_seen;   // device: runs copied so far (the doorbell's copy)
+};
+
+struct ResState {               // device memory; lives across launches
+  unsigned long long head;      // next ticket to claim
+  unsigned long long tickets;   // tickets released (every run copied so far)
+  unsigned long long copied;    // runs copied
+  unsigned long long beat;      // %globaltimer when the doorbell last copied a run
+  unsigned int stop;            // 1: the grid is to leave (set by the doorbell)
+  unsigned int exited;          // warps that have left this launch
+  int status;                   // POSPOP_ETIMEDOUT when a wait for work ran out
+  unsigned int pad;
+};
+
+struct ResParams {
+  const ResRun *hruns;          // the host ring (device address of the mapped memory)
+  ResCtl *ctl;                  // device address of the mapped control block
+  ResRun *druns;                // the device ring (same length)
+  uint32_t *idx;                // ring position of the run holding ticket 64 b, by b
+  ResState *st;
+  unsigned long long *counts;   // 64 per request slot (device, zero between uses)
+  unsigned int *done;           // finished work items per request slot
+  unsigned long long *host_res; // 64 per request slot (mapped pinned host memory)
+  unsigned int *flags;          // one per request slot (mapped pinned host memory)
+  uint32_t C;                   // ring length (power of two)
+  uint32_t B;                   // index length (power of two)
+  unsigned long long epoch;     // this launch's number (the host stops it by writing it)
+  long long wait_ns;            // the doorbell leaves after this long without a new run
+};
+
 struct PlanParams {
   const uint64_t *gptrs;        // gathered regions
   const uint64_t *glens;
@@ -171,6 +230,10 @@ const Variant &multi_variant(int i);
 // pospopcnt_multi for groups of large counts: the single-array kernel's
 // grid-stride schedule over the group's rows (same order as the stream
 // kernel table).
+// serve_mode 3's resident grid, one per serving launch shape (same order as
+// the serving kernel table).
+int resident_variant_count();
+const Variant &resident_variant(int i);
 int multi_stream_variant_count();
 const Variant &multi_stream_variant(int i);
 int gather_variant_count();

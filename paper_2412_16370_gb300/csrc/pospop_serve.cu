@@ -105,6 +105,8 @@ constexpr size_t kBatchCap = 1024;      // requests per batch, at most (4 launch
 constexpr uint64_t kMaxServeGrid = uint64_t(1) << 20;
 constexpr uint32_t kMinItemRows = 8;    // the shortest light-load work item
 constexpr size_t kGlobalSlots = 16384;  // serve_mode 1: request slots, at most
+constexpr uint32_t kResRing = 1u << 14;  // serve_mode 3: runs in the queue's rings
+constexpr uint32_t kResIndex = 1u << 20; // serve_mode 3: 64-ticket blocks indexed
 
 // The tune-table entries the loop works with (copied once per loop pass).
 struct LoopTune {
@@ -207,6 +209,17 @@ struct pospop_server {
   unsigned long long *g_hres = nullptr, *g_dres = nullptr;   // mapped pinned results
   unsigned int *g_hflags = nullptr, *g_dflags = nullptr;     // mapped pinned flags
   std::vector<uint32_t> g_free;              // free slots
+
+  // serve_mode 3: the resident grid and its queue (see pospop_resident.cu)
+  pospop::ResRun *r_hruns = nullptr, *r_hruns_dev = nullptr;   // mapped host ring
+  pospop::ResCtl *r_hctl = nullptr, *r_hctl_dev = nullptr;     // mapped control block
+  pospop::ResRun *r_druns = nullptr;                           // device ring
+  uint32_t *r_idx = nullptr;
+  pospop::ResState *r_st = nullptr;
+  cudaStream_t r_stream = nullptr;
+  cudaEvent_t r_done = nullptr;
+  int r_variant = 0;
+  unsigned r_grid = 0;
 };
 
 namespace pospop {
@@ -848,6 +861,288 @@ void serve_loop_srf(pospop_server *srv) {
   }
 }
 
+// serve_mode 3: smallest remaining first through a device-side queue into
+// one resident grid (pospop_resident.cu).  The loop keeps the admitted
+// requests ordered by the rows they have left, as serve_mode 1 does, and
+// publishes runs of their work items from the front whenever the queue's
+// unclaimed work (what the grid has not yet taken, from its `head` that the
+// doorbell mirrors to host memory) is below serve_srf's <bytes>; the grid
+// claims the items in that order, so an arrival waits behind at most that
+// much work.  The grid is launched when work arrives and there is none on
+// the device, and is told to leave (by the epoch of its launch) after
+// serve_resident's idle time without work.  If it leaves for any other
+// reason (its own wait for a run ran out, or a device error), every request
+// with published items that has not completed fails, and the queue and the
+// slots are reset before the next launch.  A run goes into the host ring
+// only at a position the doorbell has already copied out of (the doorbell
+// mirrors its copy count), and the unclaimed tickets stay far below what
+// the 64-ticket index holds.
+void serve_loop_resident(pospop_server *srv) {
+  cudaSetDevice(srv->ctx->device);
+  std::vector<Request *> queue;     // admitted, items left to publish (rows left ascending)
+  std::vector<Request *> staging;   // host input whose copy into the pool has not finished
+  std::vector<Request *> active;    // published in part or whole, not yet finished
+  std::vector<Request *> done_reqs;
+  struct Pub {
+    uint64_t t0, t1, item_bytes;    // tickets [t0, t1) of one run
+  };
+  std::deque<Pub> pubs;             // published runs not yet wholly claimed
+  uint64_t pub_bytes = 0;           // their bytes
+  uint64_t published = 0, tickets = 0, epoch = 0;
+  bool running = false, stopping = false;
+  int64_t last_work = now_ns(), last_activity = now_ns();
+  auto fits = [](uint64_t k, const Request *x) { return k < rows_left(x); };
+  auto reset_queue = [&]() {
+    // the grid is gone: nothing reads the rings, the index or the slots
+    cudaMemsetAsync(srv->r_st, 0, sizeof(ResState), srv->r_stream);
+    cudaMemsetAsync(srv->r_druns, 0, sizeof(ResRun) * kResRing, srv->r_stream);
+    cudaMemsetAsync(srv->r_idx, 0, sizeof(uint32_t) * kResIndex, srv->r_stream);
+    const size_t slots = std::min<size_t>((size_t)srv->max_inflight, kGlobalSlots);
+    cudaMemsetAsync(srv->g_dcounts, 0, 64 * sizeof(unsigned long long) * slots, srv->r_stream);
+    cudaMemsetAsync(srv->g_ddone, 0, sizeof(unsigned int) * slots, srv->r_stream);
+    cudaStreamSynchronize(srv->r_stream);
+    cudaGetLastError();
+    __atomic_store_n(&srv->r_hctl->published, 0ull, __ATOMIC_RELEASE);
+    __atomic_store_n(&srv->r_hctl->head_seen, 0ull, __ATOMIC_RELAXED);
+    __atomic_store_n(&srv->r_hctl->copied_seen, 0ull, __ATOMIC_RELAXED);
+    published = tickets = 0;
+    pubs.clear();
+    pub_bytes = 0;
+  };
+  while (true) {
+    bool progress = false;
+    int shape;
+    ServeTune cls[kServeClasses];
+    uint64_t light;
+    int64_t idle_ns, wait_ns;
+    {
+      std::lock_guard<std::mutex> g(srv->ctx->mu);
+      shape = srv->r_variant;
+      for (int k = 0; k < kServeClasses; k++) cls[k] = srv->ctx->tune.serve[k];
+      light = srv->ctx->tune.serve_light;
+      idle_ns = (int64_t)srv->ctx->tune.res_idle_us * 1000;
+      wait_ns = (int64_t)srv->ctx->tune.res_wait_us * 1000;
+    }
+    // 1. flags of finished requests
+    done_reqs.clear();
+    for (size_t k = 0; k < active.size();) {
+      Request *r = active[k];
+      if (__atomic_load_n(srv->g_hflags + r->gslot, __ATOMIC_ACQUIRE) == (uint32_t)r->id) {
+        if (r->result)
+          for (int j = 0; j < r->w; j++) r->result[j] = srv->g_hres[64 * (size_t)r->gslot + j];
+        r->rec.status = POSPOP_OK;
+        done_reqs.push_back(r);
+        active[k] = active.back();
+        active.pop_back();
+        progress = true;
+      } else {
+        k++;
+      }
+    }
+    // 2. the grid has left
+    if (running) {
+      const cudaError_t q = cudaEventQuery(srv->r_done);
+      if (q != cudaErrorNotReady) {
+        if (q != cudaSuccess) cudaGetLastError();
+        int status = POSPOP_OK;
+        if (cudaMemcpy(&status, &srv->r_st->status, sizeof(int), cudaMemcpyDeviceToHost) !=
+            cudaSuccess) {
+          cudaGetLastError();
+          status = POSPOP_ECUDA;
+        }
+        const bool clean = stopping && q == cudaSuccess && status == POSPOP_OK;
+        running = stopping = false;
+        progress = true;
+        if (!clean) {
+          // flags raised before the grid left still count; the rest fail
+          for (size_t k = 0; k < active.size(); k++) {
+            Request *r = active[k];
+            if (__atomic_load_n(srv->g_hflags + r->gslot, __ATOMIC_ACQUIRE) == (uint32_t)r->id) {
+              if (r->result)
+                for (int j = 0; j < r->w; j++)
+                  r->result[j] = srv->g_hres[64 * (size_t)r->gslot + j];
+              r->rec.status = POSPOP_OK;
+            } else {
+              r->rec.status = q == cudaSuccess && status == POSPOP_ETIMEDOUT ? POSPOP_ETIMEDOUT
+                                                                            : POSPOP_ECUDA;
+              if (r->items_next < r->items_total)   // still queued for its other items
+                queue.erase(std::remove(queue.begin(), queue.end(), r), queue.end());
+            }
+            done_reqs.push_back(r);
+          }
+          active.clear();
+          reset_queue();
+        }
+      }
+    }
+    // 3. under the lock: completions, admission, newly admitted requests
+    std::vector<Request *> incoming;
+    bool stop_now = false, server_stop = false;
+    size_t load_bytes = 0;
+    {
+      std::unique_lock<std::mutex> lk(srv->mu);
+      const int64_t tnow = now_ns();
+      for (Request *r : done_reqs) complete(*srv, r, r->rec.status, tnow);
+      if (!done_reqs.empty()) srv->cv_done.notify_all();
+      if (admit(*srv, tnow)) progress = true;
+      load_bytes = srv->inflight_bytes;
+      incoming.assign(srv->admitted.begin(), srv->admitted.end());
+      srv->admitted.clear();
+      server_stop = srv->stop;
+      const bool work = !queue.empty() || !staging.empty() || !active.empty() ||
+                        !incoming.empty() || !srv->pending.empty() || srv->uploading > 0;
+      if (work) last_work = tnow;
+      if (server_stop && !work && !running) stop_now = true;
+      if (progress || work || running) last_activity = tnow;
+      if (!progress && !work && !running && !stop_now && tnow - last_activity > 200000)
+        srv->cv_loop.wait_for(lk, std::chrono::milliseconds(50));
+    }
+    // 4. newly admitted requests: item rows, flag cleared, into the queue
+    //    (host input once its copy into the pool has finished)
+    for (Request *r : incoming) {
+      const uint64_t rrows = serve_rows(r->dptr, r->nbytes);
+      if (load_bytes < light) {
+        const ServeTune &st = cls[request_class(r->nbytes, srv->levels)];
+        r->ir = serve_light_rows(*srv->ctx, shape, rrows,
+                                 std::min(st.light_rows ? st.light_rows : st.rows, st.rows));
+      } else {
+        r->ir = srv->srf_rows ? srv->srf_rows
+                              : std::max<uint32_t>(1, cls[request_class(r->nbytes, srv->levels)].rows);
+      }
+      r->items_total = (uint32_t)((rrows + r->ir - 1) / r->ir);
+      if (r->items_total == 0) {
+        if (r->result)
+          for (int j = 0; j < r->w; j++) r->result[j] = 0;
+        std::lock_guard<std::mutex> g(srv->mu);
+        complete(*srv, r, POSPOP_OK, now_ns());
+        srv->cv_done.notify_all();
+        continue;
+      }
+      __atomic_store_n(srv->g_hflags + r->gslot, ~(uint32_t)r->id, __ATOMIC_RELAXED);
+      staging.push_back(r);
+      progress = true;
+    }
+    for (size_t k = 0; k < staging.size();) {
+      Request *r = staging[k];
+      if (r->ev) {
+        const cudaError_t q = cudaEventQuery(r->ev);
+        if (q == cudaErrorNotReady) {
+          k++;
+          continue;
+        }
+        if (q != cudaSuccess) cudaGetLastError();
+      }
+      queue.insert(std::upper_bound(queue.begin(), queue.end(), rows_left(r), fits), r);
+      staging[k] = staging.back();
+      staging.pop_back();
+    }
+    // 5. the grid: launch it when there is work and none is on the device;
+    //    publish runs while the unclaimed work is below the target
+    if (!queue.empty() && !running && !stopping && active.empty() &&
+        tickets > kResTicketLimit - (1ull << 32))
+      reset_queue();   // the ticket numbers start again (nothing is on the device)
+    if (!queue.empty() && !running && !stopping) {
+      ResParams P;
+      P.hruns = srv->r_hruns_dev;
+      P.ctl = srv->r_hctl_dev;
+      P.druns = srv->r_druns;
+      P.idx = srv->r_idx;
+      P.st = srv->r_st;
+      P.counts = srv->g_dcounts;
+      P.done = srv->g_ddone;
+      P.host_res = srv->g_dres;
+      P.flags = srv->g_dflags;
+      P.C = kResRing;
+      P.B = kResIndex;
+      P.epoch = ++epoch;
+      P.wait_ns = wait_ns;
+      const Variant &v = resident_variant(shape);
+      void *args[] = {&P};
+      if (cudaLaunchKernel(v.fn, dim3(srv->r_grid), dim3(v.bs), args, 0, srv->r_stream) !=
+              cudaSuccess ||
+          cudaEventRecord(srv->r_done, srv->r_stream) != cudaSuccess) {
+        // no grid: every queued request fails
+        cudaGetLastError();
+        std::lock_guard<std::mutex> g(srv->mu);
+        srv->loop_error = POSPOP_ECUDA;
+        for (Request *r : queue) complete(*srv, r, POSPOP_ECUDA, now_ns());
+        queue.clear();
+        srv->cv_done.notify_all();
+      } else {
+        note_launches(1);
+        running = true;
+      }
+      progress = true;
+    }
+    if (running && !stopping && !queue.empty()) {
+      const uint64_t head = __atomic_load_n(&srv->r_hctl->head_seen, __ATOMIC_RELAXED);
+      while (!pubs.empty() && pubs.front().t1 <= head) {
+        pub_bytes -= (pubs.front().t1 - pubs.front().t0) * pubs.front().item_bytes;
+        pubs.pop_front();
+      }
+      uint64_t backlog = pub_bytes;   // less what the grid has taken of the first run
+      if (!pubs.empty() && head > pubs.front().t0)
+        backlog -= (head - pubs.front().t0) * pubs.front().item_bytes;
+      const uint64_t run0 = published;
+      const uint64_t copied = __atomic_load_n(&srv->r_hctl->copied_seen, __ATOMIC_RELAXED);
+      while (!queue.empty() && backlog < srv->srf_bytes) {
+        if (published - copied >= kResRing) break;   // the host ring is full
+        if (tickets >= kResTicketLimit) break;        // a reset first (above)
+        Request *r = queue.front();
+        const uint64_t item_bytes = (uint64_t)r->ir * 512u;
+        const uint64_t left = r->items_total - r->items_next;
+        uint64_t n = std::min<uint64_t>(
+            left, std::max<uint64_t>(1, (srv->srf_bytes - backlog + item_bytes - 1) / item_bytes));
+        n = std::min<uint64_t>(n, (1ull << kResNBits) - 1);
+        // unclaimed tickets stay within the 64-ticket index, with room to spare
+        const uint64_t room = (uint64_t)kResIndex * 32u;
+        if (tickets + n > head + room) {
+          if (tickets >= head + room) break;
+          n = head + room - tickets;
+        }
+        ResRun &run = srv->r_hruns[published & (kResRing - 1)];
+        run.ptr = r->dptr;
+        run.nbytes = r->nbytes;
+        run.key = 0;
+        run.left = 0;
+        run.w = r->w;
+        run.items = r->items_total;
+        run.item0 = r->items_next;
+        run.n = (uint32_t)n;
+        run.slot = r->gslot;
+        run.tag = (uint32_t)r->id;
+        run.rows = r->ir;
+        if (r->items_next == 0) {
+          r->rec.t_launch_ns = now_ns();   // its first run
+          active.push_back(r);
+        }
+        pubs.push_back(Pub{tickets, tickets + n, item_bytes});
+        pub_bytes += n * item_bytes;
+        backlog += n * item_bytes;
+        tickets += n;
+        published++;
+        r->items_next += (uint32_t)n;
+        // wholly published requests leave the queue; a split one has the
+        // fewest rows left and stays first
+        if (r->items_next == r->items_total) queue.erase(queue.begin());
+      }
+      if (published != run0) {
+        __atomic_store_n(&srv->r_hctl->published, (unsigned long long)published, __ATOMIC_RELEASE);
+        progress = true;
+      }
+    }
+    // 6. idle: tell the grid to leave (at once when the server is stopping)
+    if (running && !stopping && queue.empty() && staging.empty() && active.empty() &&
+        (server_stop || now_ns() - last_work > idle_ns)) {
+      __atomic_store_n(&srv->r_hctl->stop, (unsigned long long)epoch, __ATOMIC_RELEASE);
+      stopping = true;
+      progress = true;
+    }
+    if (stop_now) break;
+    if (!progress) std::this_thread::yield();
+  }
+}
+
 // The uploader: copies admitted host input into its pool range on the copy
 // stream, records the copy's event and hands the request to the loop.  A
 // pageable source makes cudaMemcpyAsync wait until the bytes are staged, so
@@ -948,6 +1243,13 @@ int request_ptr(pospop_server *srv, const void *bytes, size_t nbytes, const void
 // stopped, nothing of it is in flight).
 void free_server(pospop_server *srv) {
   for (Batch &x : srv->batches) free_batch(x);
+  if (srv->r_hruns) cudaFreeHost(srv->r_hruns);
+  if (srv->r_hctl) cudaFreeHost(srv->r_hctl);
+  if (srv->r_druns) cudaFree(srv->r_druns);
+  if (srv->r_idx) cudaFree(srv->r_idx);
+  if (srv->r_st) cudaFree(srv->r_st);
+  if (srv->r_done) cudaEventDestroy(srv->r_done);
+  if (srv->r_stream) cudaStreamDestroy(srv->r_stream);
   if (srv->g_dcounts) cudaFree(srv->g_dcounts);
   if (srv->g_ddone) cudaFree(srv->g_ddone);
   if (srv->g_hres) cudaFreeHost(srv->g_hres);
@@ -1012,6 +1314,36 @@ int create_server(size_t mem_budget, int max_inflight, int max_batches, bool poo
     srv->srf_bytes = c->tune.srf_bytes;
     srv->srf_launches = std::max(1, std::min(max_batches, (int)c->tune.srf_launches));
     srv->srf_rows = c->tune.srf_rows;
+    srv->r_variant = c->tune.serve_shape;
+  }
+  if (srv->mode == 3) {
+    // the queue's rings, control block and state; the grid fills every SM
+    const size_t rbytes = sizeof(ResRun) * kResRing;
+    int occ = 0;
+    const Variant &v = resident_variant(srv->r_variant);
+    if (cudaHostAlloc(&srv->r_hruns, rbytes, cudaHostAllocMapped) != cudaSuccess ||
+        cudaHostAlloc(&srv->r_hctl, sizeof(ResCtl), cudaHostAllocMapped) != cudaSuccess ||
+        cudaHostGetDevicePointer(reinterpret_cast<void **>(&srv->r_hruns_dev), srv->r_hruns, 0) !=
+            cudaSuccess ||
+        cudaHostGetDevicePointer(reinterpret_cast<void **>(&srv->r_hctl_dev), srv->r_hctl, 0) !=
+            cudaSuccess ||
+        cudaMalloc(&srv->r_druns, rbytes) != cudaSuccess ||
+        cudaMalloc(&srv->r_idx, sizeof(uint32_t) * kResIndex) != cudaSuccess ||
+        cudaMalloc(&srv->r_st, sizeof(ResState)) != cudaSuccess ||
+        cudaMemset(srv->r_druns, 0, rbytes) != cudaSuccess ||
+        cudaMemset(srv->r_idx, 0, sizeof(uint32_t) * kResIndex) != cudaSuccess ||
+        cudaMemset(srv->r_st, 0, sizeof(ResState)) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&srv->r_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&srv->r_done, cudaEventDisableTiming) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, v.fn, v.bs, 0) != cudaSuccess ||
+        occ < 1) {
+      cudaGetLastError();
+      free_server(srv);
+      return POSPOP_ENOMEM;
+    }
+    memset(srv->r_hruns, 0, rbytes);
+    memset(srv->r_hctl, 0, sizeof(ResCtl));
+    srv->r_grid = (unsigned)(c->sms * occ);
   }
   if (srv->mode >= 1) {
     // server-wide request slots: a request keeps one for its whole life
@@ -1051,7 +1383,9 @@ int create_server(size_t mem_budget, int max_inflight, int max_batches, bool poo
     free_server(srv);
     return POSPOP_ECUDA;
   }
-  srv->loop = std::thread(srv->mode >= 1 ? serve_loop_srf : serve_loop, srv);
+  srv->loop = std::thread(srv->mode == 3 ? serve_loop_resident
+                          : srv->mode >= 1 ? serve_loop_srf : serve_loop,
+                          srv);
   if (pooled) srv->uploader = std::thread(upload_loop, srv);
   *out = srv;
   return POSPOP_OK;

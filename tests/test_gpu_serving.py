@@ -45,11 +45,13 @@ def serve_tune(gpu, tmp_path):
     pp.pospopcnt_tune_load(str(saved))
 
 
-@pytest.fixture(params=(0, 1, 2), ids=("classes", "remaining", "remaining_by_class"))
+@pytest.fixture(params=(0, 1, 2, 3), ids=("classes", "remaining", "remaining_by_class",
+                                           "resident"))
 def mode(serve_tune, request):
     """Run a test under each schedule: size classes (`serve_mode 0`),
-    dispatch by remaining bytes (`serve_mode 1`) and the same per size class
-    of the bytes left (`serve_mode 2`)."""
+    dispatch by remaining bytes (`serve_mode 1`), the same per size class of
+    the bytes left (`serve_mode 2`) and the resident grid fed through a
+    device-side queue (`serve_mode 3`)."""
     serve_tune(f"serve_mode {request.param}")
     return request.param
 
@@ -196,7 +198,7 @@ def test_promoted_batches_equal_solo(gpu, pool, serve_tune):
         assert np.array_equal(results[k, :w[k]], solo[k, :w[k]]), k
 
 
-@pytest.mark.parametrize("srf_mode", (1, 2))
+@pytest.mark.parametrize("srf_mode", (1, 2, 3))
 @pytest.mark.parametrize("launch_bytes", (8 * MIB, 256 * MIB))
 def test_dispatch_by_remaining_bytes(gpu, orc, pool, serve_tune, launch_bytes, srf_mode):
     """serve_mode 1 and 2: requests dispatched smallest-remaining first in
@@ -228,7 +230,7 @@ def test_dispatch_by_remaining_bytes(gpu, orc, pool, serve_tune, launch_bytes, s
         assert np.array_equal(results[k, :w[k]], orc.bytes(int(w[k]), seg)), (launch_bytes, srf_mode, k)
 
 
-@pytest.mark.parametrize("srf_mode", (1, 2))
+@pytest.mark.parametrize("srf_mode", (1, 2, 3))
 def test_dispatch_by_remaining_bytes_host_input(gpu, orc, serve_tune, srf_mode):
     """serve_mode 1 and 2 on a pooled server: host input staged in the pool,
     counted over several launches, equal to the oracle; the pool is released."""
@@ -247,6 +249,67 @@ def test_dispatch_by_remaining_bytes_host_input(gpu, orc, serve_tune, srf_mode):
     for k, d in enumerate(data):
         w = (8, 16, 32, 64, 8)[k]
         assert np.array_equal(res[k, :w], orc.bytes(w, d)), k
+
+
+def test_resident_grid_stops_when_idle_and_restarts(gpu, orc, pool, serve_tune):
+    """serve_mode 3: the resident grid is told to leave after the idle time
+    (200 us here) and launched again for the next requests; every result of
+    both rounds equals the oracle's."""
+    import time
+    serve_tune("serve_mode 3", "serve_resident 200 200000")
+    host = pool.cpu().numpy()
+    srv = pp.pospop_server_create(1 << 30, 64, 2)
+    try:
+        for rnd in range(2):
+            n0 = pp.pospopcnt_launch_count()
+            w, nbytes, offs = _requests(40, 31 + rnd, 1, 4 * MIB, 256 * MIB)
+            res = np.zeros((40, 64), dtype=np.uint64)
+            for k in range(40):
+                pp.pospop_server_submit(srv, int(w[k]), pool.data_ptr() + int(offs[k]),
+                                        int(nbytes[k]), res[k])
+            assert pp.pospop_server_drain(srv, 10000) == pp.POSPOP_OK
+            recs = pp.pospop_server_poll(srv, 64, timeout_ms=100)
+            assert len(recs) == 40 and all(r.status == 0 for r in recs)
+            assert pp.pospopcnt_launch_count() > n0        # a grid was launched this round
+            for k in range(40):
+                seg = host[int(offs[k]):int(offs[k]) + int(nbytes[k])]
+                assert np.array_equal(res[k, :w[k]], orc.bytes(int(w[k]), seg)), (rnd, k)
+            time.sleep(0.02)                               # the grid leaves meanwhile
+    finally:
+        pp.pospop_server_destroy(srv)
+
+
+def test_resident_grid_wait_runs_out(gpu, orc, pool, serve_tune):
+    """serve_mode 3 with a 1 us limit on the grid's wait for a new run: the
+    grid keeps leaving on its own (its bounded wait runs out), the server
+    fails exactly the requests whose items were published but not counted
+    (POSPOP_ETIMEDOUT), every other request completes with the oracle's
+    counts, and with the normal limit the next requests all complete."""
+    serve_tune("serve_mode 3", "serve_resident 1000000 1")
+    host = pool.cpu().numpy()
+    n = 300
+    w, nbytes, offs = _requests(n, 41, 1, 2 * MIB, 256 * MIB)
+    srv = pp.pospop_server_create(1 << 30, 256, 2)
+    try:
+        results = np.zeros((n, 64), dtype=np.uint64)
+        recs = pp.pospop_server_run_trace(srv, (np.arange(n) * 20000).astype(np.int64), w,
+                                          pool.data_ptr() + offs, nbytes, results)
+        st = recs["status"]
+        assert set(np.unique(st).tolist()) <= {pp.POSPOP_OK, pp.POSPOP_ETIMEDOUT}
+        for k in np.nonzero(st == pp.POSPOP_OK)[0]:
+            seg = host[int(offs[k]):int(offs[k]) + int(nbytes[k])]
+            assert np.array_equal(results[k, :w[k]], orc.bytes(int(w[k]), seg)), k
+        serve_tune("serve_mode 3", "serve_resident 2000 200000")
+        w2, nb2, off2 = _requests(100, 42, 1, 2 * MIB, 256 * MIB)
+        res2 = np.zeros((100, 64), dtype=np.uint64)
+        recs2 = pp.pospop_server_run_trace(srv, (np.arange(100) * 2000).astype(np.int64), w2,
+                                           pool.data_ptr() + off2, nb2, res2)
+        assert (recs2["status"] == 0).all()
+        for k in range(100):
+            seg = host[int(off2[k]):int(off2[k]) + int(nb2[k])]
+            assert np.array_equal(res2[k, :w2[k]], orc.bytes(int(w2[k]), seg)), k
+    finally:
+        pp.pospop_server_destroy(srv)
 
 
 def test_lone_large_request(gpu, orc, pool, mode):
