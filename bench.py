@@ -902,11 +902,19 @@ def _serving(pp, synth, pool, pool_bytes, large_gbs, dev, loads=(0.3, 0.6, 0.9),
     mean = (hi - lo) / math.log((hi + 1) / lo)      # mean of the log-uniform size
     tune = {l.split()[0]: l.split()[1:] for l in pp.pospopcnt_tune_describe().splitlines()
             if l.startswith(("serve_mode", "serve_srf"))}
-    if tune.get("serve_mode", ["0"])[0] == "1":
+    mode = tune.get("serve_mode", ["0"])[0]
+    if mode in ("1", "2", "3"):
         b, nl, rows = tune["serve_srf"]
-        schedule = (f"dispatch by remaining bytes: smallest remaining first, {int(b) >> 20} MiB "
-                    f"of work items a launch, {min(8, int(nl))} launches in flight, "
-                    f"{rows} rows a work item under load")
+        rows = f"{rows} rows" if rows != "0" else "the class's rows"
+        if mode == "3":
+            schedule = (f"smallest remaining first through a device-side queue into one resident "
+                        f"grid, at most {int(b) >> 20} MiB unclaimed, {rows} a work item "
+                        f"under load")
+        else:
+            schedule = (f"dispatch by remaining bytes{' per size class' if mode == '2' else ''}: "
+                        f"smallest remaining first, {int(b) >> 20} MiB of work items a launch, "
+                        f"{min(8, int(nl))} launches in flight"
+                        f"{' per class' if mode == '2' else ''}, {rows} a work item under load")
     else:
         schedule = ("size classes below 1 MiB / 16 MiB / 128 MiB / above on prioritised "
                     "streams, 8 batch streams a class")
