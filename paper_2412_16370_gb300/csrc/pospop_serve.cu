@@ -4,8 +4,13 @@
 // Requests name device-resident input (any pointer, length and w).  A
 // request is ADMITTED when the input bytes of all admitted, unfinished
 // requests plus its own fit the server's device-memory budget and a slot is
-// free; admitted requests that are not yet on the GPU are gathered into one
-// batch as soon as one of the server's batch streams is free, so requests
+// free.  The tune entry serve_mode picks how admitted requests reach the
+// device: by size class (0, described here), or smallest remaining first in
+// launches (1), in launches per size class (2) or through a device-side
+// queue into one resident grid (3); serve_loop_srf and serve_loop_resident
+// below describe those.  Under the size classes, admitted requests that are
+// not yet on the GPU are gathered into one batch as soon as one of the
+// server's batch streams is free, so requests
 // that arrive while others run are counted in the next batch, overlapping on
 // the device with the batches already in flight.  Requests fall into size
 // classes (below 1 MiB, 16 MiB, 128 MiB, and above), each served by its own
