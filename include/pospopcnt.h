@@ -293,7 +293,9 @@ int pospopcnt_graph_destroy(void *graph);
  * `max_batches`) a launch takes work items of the smallest first, up to
  * <bytes> of them, so a large request is counted over several launches and
  * smaller arrivals overtake it at the next launch.  Each request keeps one
- * server-wide slot of counters until its last item is done.
+ * server-wide slot of counters until its last item is done.  Under load a
+ * request's work items have its size class's `serve_srf_class` rows, or
+ * else `serve_srf`'s <rows> (modes 2 and 3 likewise).
  *
  * `serve_mode 2`: the same, per size class of the bytes a request has left
  * (the classes below): a launch takes requests of one class only and runs

@@ -115,6 +115,13 @@ TuneTable default_tune() {
   t.srf_bytes = uint64_t(128) << 20;
   t.srf_launches = 5;
   t.srf_rows = 255;
+  // under load, 15- and 127-row items for requests below 1 MiB and 16 MiB
+  // (measured on GB300 with five launches: 0.9-load p50 49 against 62 us,
+  // p99 241-243 against 245-253 us)
+  t.srf_class_rows[0] = 15;
+  t.srf_class_rows[1] = 127;
+  t.srf_class_rows[2] = 0;
+  t.srf_class_rows[3] = 0;
   t.res_idle_us = 2000;
   t.res_wait_us = 200000;
   t.multi_rows = 1024;
@@ -166,6 +173,10 @@ TuneTable default_tune() {
 //                                  classes' prioritised streams; 3 = smallest remaining
 //                                  first through a device-side queue into one resident
 //                                  grid, serve_srf's <bytes> the queue's unclaimed work)
+//   serve_srf_class <r0> <r1> <r2> <r3>
+//                                 (serve_mode 1-3: rows per work item under load for
+//                                  requests of size class 0 .. 3, 0 .. 2^20; 0 takes
+//                                  serve_srf's rows)
 //   serve_resident <idle_us> <wait_us>
 //                                 (serve_mode 3: the host stops the resident grid after
 //                                  idle_us without work; the grid leaves by itself after
@@ -300,6 +311,11 @@ int parse_tune(const char *text, TuneTable *out, int *bad_line) {
       t.srf_bytes = (uint64_t)a[0];
       t.srf_launches = (uint32_t)a[1];
       t.srf_rows = (uint32_t)a[2];
+    } else if (strcmp(kind, "serve_srf_class") == 0) {
+      if (n != kServeClasses) return POSPOP_EINVAL;
+      for (int k = 0; k < kServeClasses; k++)
+        if (a[k] < 0 || a[k] > (1 << 20)) return POSPOP_EINVAL;
+      for (int k = 0; k < kServeClasses; k++) t.srf_class_rows[k] = (uint32_t)a[k];
     } else if (strcmp(kind, "serve_resident") == 0) {
       if (n != 2 || a[0] < 1 || a[0] > 10000000 || a[1] < 1 || a[1] > 10000000)
         return POSPOP_EINVAL;
@@ -427,9 +443,11 @@ std::string format_tune(const DevCtx &ctx, const TuneTable &t) {
   {
     const Variant &v = serve_variant(t.serve_shape);
     snprintf(line, sizeof line,
-             "serve_shape %d %d %d %d\nserve_mode %u\nserve_srf %llu %u %u\nserve_resident %u %u\n",
+             "serve_shape %d %d %d %d\nserve_mode %u\nserve_srf %llu %u %u\n"
+             "serve_srf_class %u %u %u %u\nserve_resident %u %u\n",
              v.bs, v.minb, v.depth, v.hint, t.serve_mode, (unsigned long long)t.srf_bytes,
-             t.srf_launches, t.srf_rows, t.res_idle_us, t.res_wait_us);
+             t.srf_launches, t.srf_rows, t.srf_class_rows[0], t.srf_class_rows[1],
+             t.srf_class_rows[2], t.srf_class_rows[3], t.res_idle_us, t.res_wait_us);
     s += line;
   }
   snprintf(line, sizeof line, "# multi <most item rows> <0 contiguous | 1 strided items>\nmulti %u %u\n",

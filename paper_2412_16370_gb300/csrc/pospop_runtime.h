@@ -78,6 +78,8 @@ struct TuneTable {
   uint64_t srf_bytes;           // serve_mode 1: bytes of work items per launch, at most
   uint32_t srf_launches;        // serve_mode 1: launches in flight, at most
   uint32_t srf_rows;            // serve_mode 1: rows per work item
+  uint32_t srf_class_rows[kServeClasses];   // serve_mode 1-3: rows per work item under
+                                            // load by size class (0: srf_rows)
   uint32_t res_idle_us;         // serve_mode 3: the host stops the resident grid after this long idle
   uint32_t res_wait_us;         // serve_mode 3: the grid leaves after this long without a new run
   uint32_t multi_rows;          // pospopcnt_multi: most work-item rows (wave-aligned, at least 8)

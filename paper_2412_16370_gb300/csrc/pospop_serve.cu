@@ -664,12 +664,16 @@ void serve_loop_srf(pospop_server *srv) {
     int shape;
     uint32_t strided;
     ServeTune cls[kServeClasses];
+    uint32_t load_rows[kServeClasses];
     uint64_t light;
     {
       std::lock_guard<std::mutex> g(srv->ctx->mu);
       shape = srv->ctx->tune.serve_shape;
       strided = srv->ctx->tune.serve_strided;
-      for (int k = 0; k < kServeClasses; k++) cls[k] = srv->ctx->tune.serve[k];
+      for (int k = 0; k < kServeClasses; k++) {
+        cls[k] = srv->ctx->tune.serve[k];
+        load_rows[k] = srv->ctx->tune.srf_class_rows[k];
+      }
       light = srv->ctx->tune.serve_light;
     }
     // 1. finished launches free their streams; flagged requests are done;
@@ -736,9 +740,11 @@ void serve_loop_srf(pospop_server *srv) {
         const ServeTune &st = cls[request_class(r->nbytes, srv->levels)];
         r->ir = serve_light_rows(*srv->ctx, shape, rrows,
                                  std::min(st.light_rows ? st.light_rows : st.rows, st.rows));
-      } else {   // srf_rows, or 0: the rows of the request's class under load
-        r->ir = srv->srf_rows ? srv->srf_rows
-                              : std::max<uint32_t>(1, cls[request_class(r->nbytes, srv->levels)].rows);
+      } else {   // the class's serve_srf_class rows, else srf_rows, else (0) its serve rows
+        const int k = request_class(r->nbytes, srv->levels);
+        r->ir = load_rows[k]     ? load_rows[k]
+                : srv->srf_rows  ? srv->srf_rows
+                                 : std::max<uint32_t>(1, cls[k].rows);
       }
       r->items_total = (uint32_t)((rrows + r->ir - 1) / r->ir);
       if (r->items_total == 0) {
@@ -918,12 +924,16 @@ void serve_loop_resident(pospop_server *srv) {
     bool progress = false;
     int shape;
     ServeTune cls[kServeClasses];
+    uint32_t load_rows[kServeClasses];
     uint64_t light;
     int64_t idle_ns, wait_ns;
     {
       std::lock_guard<std::mutex> g(srv->ctx->mu);
       shape = srv->r_variant;
-      for (int k = 0; k < kServeClasses; k++) cls[k] = srv->ctx->tune.serve[k];
+      for (int k = 0; k < kServeClasses; k++) {
+        cls[k] = srv->ctx->tune.serve[k];
+        load_rows[k] = srv->ctx->tune.srf_class_rows[k];
+      }
       light = srv->ctx->tune.serve_light;
       idle_ns = (int64_t)srv->ctx->tune.res_idle_us * 1000;
       wait_ns = (int64_t)srv->ctx->tune.res_wait_us * 1000;
@@ -1011,8 +1021,10 @@ void serve_loop_resident(pospop_server *srv) {
         r->ir = serve_light_rows(*srv->ctx, shape, rrows,
                                  std::min(st.light_rows ? st.light_rows : st.rows, st.rows));
       } else {
-        r->ir = srv->srf_rows ? srv->srf_rows
-                              : std::max<uint32_t>(1, cls[request_class(r->nbytes, srv->levels)].rows);
+        const int k = request_class(r->nbytes, srv->levels);
+        r->ir = load_rows[k]     ? load_rows[k]
+                : srv->srf_rows  ? srv->srf_rows
+                                 : std::max<uint32_t>(1, cls[k].rows);
       }
       r->items_total = (uint32_t)((rrows + r->ir - 1) / r->ir);
       if (r->items_total == 0) {
