@@ -905,7 +905,12 @@ def _serving(pp, synth, pool, pool_bytes, large_gbs, dev, loads=(0.3, 0.6, 0.9),
     mode = tune.get("serve_mode", ["0"])[0]
     if mode in ("1", "2", "3"):
         b, nl, rows = tune["serve_srf"]
-        rows = f"{rows} rows" if rows != "0" else "the class's rows"
+        per_class = tune.get("serve_srf_class", ["0"] * 4)
+        bounds = ("1 MiB", "16 MiB", "128 MiB")
+        extra = "; ".join(f"{r} rows below {bounds[k]}" for k, r in enumerate(per_class[:3])
+                          if r != "0")
+        rows = (f"{rows} rows" if rows != "0" else "the class's rows") + \
+            (f" ({extra})" if extra else "")
         if mode == "3":
             schedule = (f"smallest remaining first through a device-side queue into one resident "
                         f"grid, at most {int(b) >> 20} MiB unclaimed, {rows} a work item "
