@@ -295,7 +295,9 @@ int pospopcnt_graph_destroy(void *graph);
  * smaller arrivals overtake it at the next launch.  Each request keeps one
  * server-wide slot of counters until its last item is done.  Under load a
  * request's work items have its size class's `serve_srf_class` rows, or
- * else `serve_srf`'s <rows> (modes 2 and 3 likewise).
+ * else `serve_srf`'s <rows> (modes 2 and 3 likewise).  With `serve_srf_age`
+ * set, the longest-waiting request, once it has waited that long, takes up
+ * to half of the next launch ahead of the order (off by default).
  *
  * `serve_mode 2`: the same, per size class of the bytes a request has left
  * (the classes below): a launch takes requests of one class only and runs

@@ -122,6 +122,7 @@ TuneTable default_tune() {
   t.srf_class_rows[1] = 127;
   t.srf_class_rows[2] = 0;
   t.srf_class_rows[3] = 0;
+  t.srf_age_us = 0;
   t.res_idle_us = 2000;
   t.res_wait_us = 200000;
   t.multi_rows = 1024;
@@ -177,6 +178,9 @@ TuneTable default_tune() {
 //                                 (serve_mode 1-3: rows per work item under load for
 //                                  requests of size class 0 .. 3, 0 .. 2^20; 0 takes
 //                                  serve_srf's rows)
+//   serve_srf_age <us>            (serve_mode 1: 0 = off; else the longest-waiting
+//                                  request that has waited this long since it arrived
+//                                  takes up to half of the next launch, 1 .. 10^7)
 //   serve_resident <idle_us> <wait_us>
 //                                 (serve_mode 3: the host stops the resident grid after
 //                                  idle_us without work; the grid leaves by itself after
@@ -316,6 +320,9 @@ int parse_tune(const char *text, TuneTable *out, int *bad_line) {
       for (int k = 0; k < kServeClasses; k++)
         if (a[k] < 0 || a[k] > (1 << 20)) return POSPOP_EINVAL;
       for (int k = 0; k < kServeClasses; k++) t.srf_class_rows[k] = (uint32_t)a[k];
+    } else if (strcmp(kind, "serve_srf_age") == 0) {
+      if (n != 1 || a[0] < 0 || a[0] > 10000000) return POSPOP_EINVAL;
+      t.srf_age_us = (uint32_t)a[0];
     } else if (strcmp(kind, "serve_resident") == 0) {
       if (n != 2 || a[0] < 1 || a[0] > 10000000 || a[1] < 1 || a[1] > 10000000)
         return POSPOP_EINVAL;
@@ -444,10 +451,10 @@ std::string format_tune(const DevCtx &ctx, const TuneTable &t) {
     const Variant &v = serve_variant(t.serve_shape);
     snprintf(line, sizeof line,
              "serve_shape %d %d %d %d\nserve_mode %u\nserve_srf %llu %u %u\n"
-             "serve_srf_class %u %u %u %u\nserve_resident %u %u\n",
+             "serve_srf_class %u %u %u %u\nserve_srf_age %u\nserve_resident %u %u\n",
              v.bs, v.minb, v.depth, v.hint, t.serve_mode, (unsigned long long)t.srf_bytes,
              t.srf_launches, t.srf_rows, t.srf_class_rows[0], t.srf_class_rows[1],
-             t.srf_class_rows[2], t.srf_class_rows[3], t.res_idle_us, t.res_wait_us);
+             t.srf_class_rows[2], t.srf_class_rows[3], t.srf_age_us, t.res_idle_us, t.res_wait_us);
     s += line;
   }
   snprintf(line, sizeof line, "# multi <most item rows> <0 contiguous | 1 strided items>\nmulti %u %u\n",

@@ -80,6 +80,7 @@ struct TuneTable {
   uint32_t srf_rows;            // serve_mode 1: rows per work item
   uint32_t srf_class_rows[kServeClasses];   // serve_mode 1-3: rows per work item under
                                             // load by size class (0: srf_rows)
+  uint32_t srf_age_us;          // serve_mode 1: a request waiting this long takes half a launch (0: off)
   uint32_t res_idle_us;         // serve_mode 3: the host stops the resident grid after this long idle
   uint32_t res_wait_us;         // serve_mode 3: the grid leaves after this long without a new run
   uint32_t multi_rows;          // pospopcnt_multi: most work-item rows (wave-aligned, at least 8)

@@ -666,6 +666,7 @@ void serve_loop_srf(pospop_server *srv) {
     ServeTune cls[kServeClasses];
     uint32_t load_rows[kServeClasses];
     uint64_t light;
+    int64_t age_ns;
     {
       std::lock_guard<std::mutex> g(srv->ctx->mu);
       shape = srv->ctx->tune.serve_shape;
@@ -675,6 +676,7 @@ void serve_loop_srf(pospop_server *srv) {
         load_rows[k] = srv->ctx->tune.srf_class_rows[k];
       }
       light = srv->ctx->tune.serve_light;
+      age_ns = (int64_t)srv->ctx->tune.srf_age_us * 1000;
     }
     // 1. finished launches free their streams; flagged requests are done;
     //    a request whose launches all finished unflagged failed on the device
@@ -788,14 +790,11 @@ void serve_loop_srf(pospop_server *srv) {
         uint64_t budget = srv->srf_bytes;
         uint64_t items = 0;
         uint32_t n = 0;
-        size_t taken = 0;
-        for (size_t q = lo; q < hi; q++) {
-          Request *r = queue[q];
-          if (n == (uint32_t)kServeMax || budget == 0) break;
+        // one entry of this launch: up to `cap` bytes of r's next items
+        auto take_from = [&](Request *r, uint64_t cap) {
           const uint64_t item_bytes = (uint64_t)r->ir * 512u;
           const uint64_t left = r->items_total - r->items_next;
-          const uint64_t take =
-              std::min<uint64_t>(left, std::max<uint64_t>(1, budget / item_bytes));
+          const uint64_t take = std::min<uint64_t>(left, std::max<uint64_t>(1, cap / item_bytes));
           P.req[n] = ServeReq{r->dptr, (uint64_t)r->nbytes, r->w, r->items_total, nullptr,
                               r->items_next, r->gslot, (uint32_t)r->id, r->ir};
           P.item_start[n] = items;
@@ -810,11 +809,42 @@ void serve_loop_srf(pospop_server *srv) {
           b->reqs.push_back(r);
           if (r->ev && cudaStreamWaitEvent(b->s, r->ev, 0) != cudaSuccess) cudaGetLastError();
           n++;
+        };
+        // serve_srf_age (serve_mode 1): the longest-waiting request, once it
+        // has waited that long, takes up to half the launch first (it leaves
+        // its place in the queue and goes back by its rows left)
+        if (age_ns > 0 && !leveled && hi - lo > 1) {
+          const int64_t tnow = now_ns();
+          size_t oldest = hi;
+          for (size_t q = lo + 1; q < hi; q++)
+            if (tnow - queue[q]->rec.t_submit_ns > age_ns &&
+                (oldest == hi || queue[q]->rec.t_submit_ns < queue[oldest]->rec.t_submit_ns))
+              oldest = q;
+          if (oldest < hi) {
+            Request *r = queue[oldest];
+            queue.erase(queue.begin() + (std::ptrdiff_t)oldest);
+            hi--;
+            take_from(r, srv->srf_bytes / 2);
+            if (r->items_next < r->items_total)
+              queue.insert(std::upper_bound(queue.begin(), queue.end(), rows_left(r),
+                                            [](uint64_t k, const Request *x) {
+                                              return k < rows_left(x);
+                                            }),
+                           r);
+            hi = queue.size();   // (serve_mode 1: the run is the whole queue)
+          }
+        }
+        size_t taken = 0;
+        for (size_t q = lo; q < hi; q++) {
+          Request *r = queue[q];
+          if (n == (uint32_t)kServeMax || budget == 0) break;
+          take_from(r, budget);
           taken++;
           if (r->items_next < r->items_total) break;   // the budget is spent
         }
         // requests with every item dispatched leave the queue
-        Request *part = queue[lo + taken - 1]->items_next < queue[lo + taken - 1]->items_total
+        Request *part = taken > 0 && queue[lo + taken - 1]->items_next <
+                                         queue[lo + taken - 1]->items_total
                             ? queue[lo + taken - 1]
                             : nullptr;
         queue.erase(queue.begin() + (std::ptrdiff_t)lo,

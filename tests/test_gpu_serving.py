@@ -230,6 +230,29 @@ def test_dispatch_by_remaining_bytes(gpu, orc, pool, serve_tune, launch_bytes, s
         assert np.array_equal(results[k, :w[k]], orc.bytes(int(w[k]), seg)), (launch_bytes, srf_mode, k)
 
 
+def test_aged_requests_take_half_a_launch(gpu, orc, pool, serve_tune):
+    """serve_mode 1 with `serve_srf_age 1`: at almost every launch the
+    longest-waiting request takes up to half of it ahead of the smallest
+    remaining ones (its items then split across launches out of the queue's
+    order): every result still equals the oracle's."""
+    serve_tune("serve_mode 1", f"serve_srf {8 * MIB} 4 255", "serve_srf_age 1")
+    n = 400
+    w, nbytes, offs = _requests(n, 27, 1, 24 * MIB, 256 * MIB)
+    nbytes[::47] = 0
+    srv = pp.pospop_server_create(96 * MIB, 64, 4)
+    try:
+        results = np.zeros((n, 64), dtype=np.uint64)
+        recs = pp.pospop_server_run_trace(srv, (np.arange(n) * 1000).astype(np.int64), w,
+                                          pool.data_ptr() + offs, nbytes, results)
+    finally:
+        pp.pospop_server_destroy(srv)
+    assert (recs["status"] == 0).all()
+    host = pool.cpu().numpy()
+    for k in range(n):
+        seg = host[int(offs[k]):int(offs[k]) + int(nbytes[k])]
+        assert np.array_equal(results[k, :w[k]], orc.bytes(int(w[k]), seg)), k
+
+
 @pytest.mark.parametrize("srf_mode", (1, 2, 3))
 def test_dispatch_by_remaining_bytes_host_input(gpu, orc, serve_tune, srf_mode):
     """serve_mode 1 and 2 on a pooled server: host input staged in the pool,

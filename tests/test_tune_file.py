@@ -45,7 +45,7 @@ def test_per_width_and_every_width_entries(pp, tmp_path):
               "serve_strided 1", "serve_strided 0", "serve_order 1", "multi 8 0",
               "serve_promote 0", "serve_promote 250", "serve_shape 512 1 16 0",
               "serve_mode 1", "serve_mode 2", "serve_mode 0", "serve_srf 268435456 4 255", "serve_srf 512 1 1",
-              "serve_srf 134217728 4 0", "serve_srf_class 31 127 0 0", "serve_mode 3", "serve_resident 2000 200000", "serve_resident 1 1",
+              "serve_srf 134217728 4 0", "serve_srf_class 31 127 0 0", "serve_srf_age 150", "serve_srf_age 0", "serve_mode 3", "serve_resident 2000 200000", "serve_resident 1 1",
               "serve_shape 256 2 32 1",
               "multi 1048576 1",
               "stream 4 512 1 16 0 3 1   # trailing comment"]
@@ -86,7 +86,7 @@ def test_per_width_and_every_width_entries(pp, tmp_path):
     "serve_order 2", "serve_order", "multi 7 0", "multi 1048577 0", "multi 4096 2", "multi 4096",
     "serve_promote -1", "serve_promote 10000001", "serve_promote",
     "serve_shape 500 1 16 0", "serve_shape 512 1 16", "serve_shape 512 1 24 0",
-    "serve_mode 4", "serve_srf_class 1 2 3", "serve_srf_class 1 2 3 1048577", "serve_srf 511 1 1", "serve_srf 511 1 0", "serve_resident 0 5", "serve_resident 5", "serve_srf 1048576 4 -1", "serve_srf 268435456 0 255", "serve_srf 268435456 4",
+    "serve_mode 4", "serve_srf_age -1", "serve_srf_age 10000001", "serve_srf_class 1 2 3", "serve_srf_class 1 2 3 1048577", "serve_srf 511 1 1", "serve_srf 511 1 0", "serve_resident 0 5", "serve_resident 5", "serve_srf 1048576 4 -1", "serve_srf 268435456 0 255", "serve_srf 268435456 4",
 ])
 def test_malformed_line_is_reported_with_its_number(pp, tmp_path, bad):
     text = "# header\nstream 0 256 2 16 1 1 2\n\n" + bad + "\npdl 1\n"
