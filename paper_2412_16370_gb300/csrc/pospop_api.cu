@@ -1489,9 +1489,13 @@ int pospopcnt_multi(size_t n, const int *w, uint64_t *const *counts, const void 
     // against 7.13 TB/s for four single launches)
     const uint64_t wave = (uint64_t)c->sms * (uint64_t)c->occ_multi[vi];
     const uint64_t grid = std::min<uint64_t>((items + wpb - 1) / wpb, wave);
-    void *args[] = {&P};
-    if (launch_kernel(v.fn, dim3((unsigned)grid), dim3(v.bs), args,
-                      static_cast<cudaStream_t>(stream), t.pdl != 0) != cudaSuccess) {
+    // a launch of few counts takes the small parameter block
+    static thread_local ServeParamsSmall S;
+    const bool small = cnt <= (size_t)kServeSmall;
+    if (small) shrink_params(P, S);
+    void *args[] = {small ? static_cast<void *>(&S) : static_cast<void *>(&P)};
+    if (launch_kernel(small ? multi_small_variant(vi).fn : v.fn, dim3((unsigned)grid), dim3(v.bs),
+                      args, static_cast<cudaStream_t>(stream), t.pdl != 0) != cudaSuccess) {
       cudaGetLastError();
       return POSPOP_ECUDA;
     }

@@ -1,7 +1,9 @@
 // pospop_desc.cu -- the serving loop's counting kernel (and its add-into
 // form behind pospopcnt_multi): one launch counts up to kServeMax requests
-// of mixed width and size, passed by value in the kernel's parameter block (a __grid_constant__ struct of about 8 KiB, read
-// in place through the constant cache: no upload copy before the launch).
+// of mixed width and size, passed by value in the kernel's parameter block
+// (a __grid_constant__ struct, read in place through the constant cache: no
+// upload copy before the launch; about 14 KiB, or about 1 KiB in the form
+// for at most kServeSmall requests).
 //
 // A launch counts work items [item0, item0 + its items here) of each
 // request, so one request's items may be spread over several launches; its
@@ -46,8 +48,9 @@ __device__ __forceinline__ uint32_t find_request(const uint64_t *item_start, uin
 // added straight into its count's own counters (req.out), with no request
 // slots and no completion tracking; it waits for the previous kernel on the
 // stream (programmatic dependent launch) like the other counting kernels.
-template <int BS, int MINB, int DEPTH, int HINT, bool ADD = false>
-__global__ void __launch_bounds__(BS, MINB) serve_kernel(const __grid_constant__ ServeParams P) {
+template <int BS, int MINB, int DEPTH, int HINT, bool ADD = false, int N = kServeMax>
+__global__ void __launch_bounds__(BS, MINB)
+    serve_kernel(const __grid_constant__ ServeParamsT<N> P) {
   if (ADD) pdl_enter();
   constexpr unsigned WPB = BS / 32;
   const unsigned lane = threadIdx.x & 31u;
@@ -118,18 +121,28 @@ __global__ void __launch_bounds__(BS, MINB) serve_kernel(const __grid_constant__
 
 #define POSPOP_SERV(BS, MINB, D, H) \
   Variant{reinterpret_cast<const void *>(&serve_kernel<BS, MINB, D, H>), BS, MINB, D, H}
+#define POSPOP_SERV_S(BS, MINB, D, H)                                                        \
+  Variant{reinterpret_cast<const void *>(&serve_kernel<BS, MINB, D, H, false, kServeSmall>), \
+          BS, MINB, D, H}
 
 static const Variant kServe[] = {POSPOP_FAMILY(POSPOP_SERV)};
+static const Variant kServeSm[] = {POSPOP_FAMILY(POSPOP_SERV_S)};
 
 int serve_variant_count() { return (int)(sizeof(kServe) / sizeof(kServe[0])); }
 const Variant &serve_variant(int i) { return kServe[i]; }
+const Variant &serve_small_variant(int i) { return kServeSm[i]; }
 
 #define POSPOP_MULTI(BS, MINB, D, H) \
   Variant{reinterpret_cast<const void *>(&serve_kernel<BS, MINB, D, H, true>), BS, MINB, D, H}
+#define POSPOP_MULTI_S(BS, MINB, D, H)                                                      \
+  Variant{reinterpret_cast<const void *>(&serve_kernel<BS, MINB, D, H, true, kServeSmall>), \
+          BS, MINB, D, H}
 
 static const Variant kMulti[] = {POSPOP_FAMILY(POSPOP_MULTI)};
+static const Variant kMultiSm[] = {POSPOP_FAMILY(POSPOP_MULTI_S)};
 
 int multi_variant_count() { return (int)(sizeof(kMulti) / sizeof(kMulti[0])); }
 const Variant &multi_variant(int i) { return kMulti[i]; }
+const Variant &multi_small_variant(int i) { return kMultiSm[i]; }
 
 }  // namespace pospop

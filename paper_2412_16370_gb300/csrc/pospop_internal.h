@@ -82,7 +82,8 @@ struct ServeReq {
   uint32_t rows;                // rows of 512 B per work item of this request
 };
 
-struct ServeParams {
+template <int N>
+struct ServeParamsT {
   uint32_t n;                   // requests in this launch
   uint64_t total;               // work items in this launch
   unsigned long long *counts;   // 64 per request slot (device, zero between uses)
@@ -93,9 +94,32 @@ struct ServeParams {
                                 // (warps on neighbouring items read neighbouring rows);
                                 // 0: item k counts rows k * rows .. + rows - 1 (rows: the
                                 // request's item rows)
-  ServeReq req[kServeMax];
-  uint64_t item_start[kServeMax + 1];
+  ServeReq req[N];
+  uint64_t item_start[N + 1];
 };
+using ServeParams = ServeParamsT<kServeMax>;
+
+// Launches of at most kServeSmall requests go out with a parameter block of
+// that many entries (about 1 KiB instead of 14 KiB): the driver copies the
+// whole block into every launch, and a small block reaches the device
+// sooner.  The same kernel, instantiated for both sizes.
+constexpr int kServeSmall = 16;
+using ServeParamsSmall = ServeParamsT<kServeSmall>;
+
+inline void shrink_params(const ServeParams &P, ServeParamsSmall &S) {
+  S.n = P.n;
+  S.total = P.total;
+  S.counts = P.counts;
+  S.done = P.done;
+  S.host_res = P.host_res;
+  S.flags = P.flags;
+  S.strided = P.strided;
+  for (uint32_t k = 0; k < P.n; k++) {
+    S.req[k] = P.req[k];
+    S.item_start[k] = P.item_start[k];
+  }
+  S.item_start[P.n] = P.item_start[P.n];
+}
 
 // serve_mode 3: one resident grid fed through a device-side queue.  The host
 // publishes runs of a request's work items into a ring in mapped pinned
@@ -223,10 +247,13 @@ const Variant &roofline_variant(int i);
 
 int serve_variant_count();
 const Variant &serve_variant(int i);
+// the same serving kernels with the small parameter block (same order)
+const Variant &serve_small_variant(int i);
 // The serving kernel's add-into form (pospopcnt_multi): same launch shapes,
 // each count added into its own counters, no completion tracking.
 int multi_variant_count();
 const Variant &multi_variant(int i);
+const Variant &multi_small_variant(int i);
 // pospopcnt_multi for groups of large counts: the single-array kernel's
 // grid-stride schedule over the group's rows (same order as the stream
 // kernel table).

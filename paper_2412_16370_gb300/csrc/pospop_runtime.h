@@ -210,7 +210,7 @@ uint32_t serve_light_rows(const DevCtx &ctx, int variant, uint64_t rows, uint32_
                           uint32_t least = 0);
 // Launch serve variant v on the planned parameter block P (nothing if P
 // has no work items).
-int serve_launch(const Variant &v, const ServeParams &P, cudaStream_t stream);
+int serve_launch(int shape, const ServeParams &P, cudaStream_t stream);
 
 // Device address of the no-allocation batch's scratch array on the current
 // device (pospop_noalloc.cu); called once per device when its context is

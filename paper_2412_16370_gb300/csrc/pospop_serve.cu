@@ -151,16 +151,22 @@ uint32_t serve_light_rows(const DevCtx &ctx, int variant, uint64_t rows, uint32_
   return (uint32_t)std::min(m, std::max(least, want));
 }
 
-int serve_launch(const Variant &v, const ServeParams &P, cudaStream_t stream) {
+int serve_launch(int shape, const ServeParams &P, cudaStream_t stream) {
   // one work item per warp: blocks retire as their items finish, so a
   // smaller class's pending blocks can take the SM (the grid-stride loop in
   // the kernel covers any cap)
+  const Variant &v = serve_variant(shape);
   const uint64_t wpb = (uint64_t)v.bs / 32;
   uint64_t grid = (P.total + wpb - 1) / wpb;
   if (grid > kMaxServeGrid) grid = kMaxServeGrid;
   if (grid == 0) return POSPOP_OK;
-  void *args[] = {const_cast<ServeParams *>(&P)};
-  if (cudaLaunchKernel(v.fn, dim3((unsigned)grid), dim3(v.bs), args, 0, stream) != cudaSuccess) {
+  // a launch of few requests takes the small parameter block
+  static thread_local ServeParamsSmall S;
+  const bool small = P.n <= (uint32_t)kServeSmall;
+  if (small) shrink_params(P, S);
+  void *args[] = {small ? static_cast<void *>(&S) : const_cast<ServeParams *>(&P)};
+  const void *fn = small ? serve_small_variant(shape).fn : v.fn;
+  if (cudaLaunchKernel(fn, dim3((unsigned)grid), dim3(v.bs), args, 0, stream) != cudaSuccess) {
     cudaGetLastError();
     return POSPOP_ECUDA;
   }
@@ -276,7 +282,6 @@ int launch_batch(pospop_server &srv, Batch &b, const LoopTune &lt, size_t load_b
   // class's stream); all requests of a batch are of one class
   const int cls = b.reqs.empty() ? b.level : request_class(b.reqs[0]->nbytes, srv.levels);
   const uint32_t ir = batch_item_rows(srv, lt, cls, rows, load_bytes);
-  const Variant &v = serve_variant(lt.shape);
   // host input: the batch stream waits for the requests' copies into the pool
   for (const Request *r : b.reqs)
     if (r->ev && cudaStreamWaitEvent(b.s, r->ev, 0) != cudaSuccess) {
@@ -312,7 +317,7 @@ int launch_batch(pospop_server &srv, Batch &b, const LoopTune &lt, size_t load_b
     P.item_start[cnt] = items;
     P.total = items;
     if (items == 0) continue;
-    const int rc = serve_launch(v, P, b.s);
+    const int rc = serve_launch(lt.shape, P, b.s);
     if (rc != POSPOP_OK) return rc;
   }
   if (cudaEventRecord(b.done, b.s) != cudaSuccess) {
@@ -863,7 +868,7 @@ void serve_loop_srf(pospop_server *srv) {
         P.flags = srv->g_dflags;
         P.strided = strided;
         P.item_start[n] = items;
-        int rc = serve_launch(serve_variant(shape), P, b->s);
+        int rc = serve_launch(shape, P, b->s);
         if (rc == POSPOP_OK && cudaEventRecord(b->done, b->s) != cudaSuccess) rc = POSPOP_ECUDA;
         b->busy = true;
         if (rc != POSPOP_OK) {

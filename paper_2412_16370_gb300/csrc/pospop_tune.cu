@@ -282,7 +282,6 @@ extern "C" int pospopcnt_autotune(size_t max_bytes, const char *path) {
         {31, 63, 127}, {63, 127, 255}, {127, 255, 511}, {127, 255, 511}};
     const uint32_t light_set[] = {8, 16, 32, 63, 127, 0};   // 0: the class's `rows`
     const int sv = best.serve_shape;   // the server's launch shape
-    const Variant &v = serve_variant(sv);
     std::unique_ptr<ServeParams> P(new ServeParams());
     unsigned long long *dres = nullptr;
     unsigned int *ddone = nullptr, *dflags = nullptr;
@@ -313,7 +312,7 @@ extern "C" int pospopcnt_autotune(size_t max_bytes, const char *path) {
       }
       P->item_start[reqs.size()] = items;
       P->total = items;
-      return serve_launch(v, *P, tm.s);
+      return serve_launch(sv, *P, tm.s);
     };
     for (int k = 0; ok && k < kServeClasses; k++) {
       // requests of the class, at random places in the scratch buffer
