@@ -12,10 +12,10 @@
 // in it has been wholly counted (each worker takes one from the run's
 // `left` when it is done with the record), and a run's tickets sit in one
 // 8-byte key written after its other fields, so a warp that scans the ring
-// sees a run whole or not at all.  Every other warp claims one ticket at a time
-// (an atomic on `head`, taken only while a released ticket is left, so that
-// idle warps do not run ahead), finds its run from the 64-ticket index and
-// at most two warp-wide scans of the ring, and counts that work item with
+// sees a run whole or not at all.  Every other warp claims one ticket at a
+// time (an atomic on `head`, taken only while a released ticket is left, so
+// that idle warps do not run ahead), finds its run from the 64-ticket index
+// and at most three warp-wide scans of the ring, and counts that work item with
 // the paper's per-thread algorithm (Section 4) into the request's slot, as
 // the serving kernel does: the warp that finishes a request's last item
 // publishes its counts and raises its flag with the request's tag.
