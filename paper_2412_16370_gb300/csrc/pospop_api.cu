@@ -790,7 +790,11 @@ int launch_roofline_with(const DevCtx &ctx, const RoofTune &rt, const void *byte
   // 512 granules (bulk-copy staging)
   const uint64_t units = v.smem > 0 ? (P.G + 511) >> 9 : (P.G + 31) >> 5;
   uint64_t grid = (units + (v.bs / 32) - 1) / (v.bs / 32);
-  const uint64_t max_grid = (uint64_t)ctx.sms * cps;
+  uint64_t max_grid = (uint64_t)ctx.sms * cps;
+  // an input too small to give every warp of that grid 32 units runs in one
+  // wave of resident blocks instead (the waves pay only for large inputs)
+  const uint64_t wave = (uint64_t)ctx.sms * (uint64_t)std::max(1, ctx.occ_roof[rt.variant]);
+  if (max_grid > wave && units < max_grid * (v.bs / 32) * 32) max_grid = wave;
   if (grid > max_grid) grid = max_grid;
   if (grid < 1) grid = 1;
   void *args[] = {&P};
